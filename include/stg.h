@@ -1,0 +1,166 @@
+/*
+ * stg.h -- C ABI of the GB300 space-time Vanka-multigrid FGMRES solver.
+ *
+ * The solver follows M. Anselmann, M. Bause, "Efficiency of local Vanka smoother
+ * geometric multigrid preconditioning for space-time finite element methods to
+ * the Navier--Stokes equations":
+ *   - Sec. 2, Eq. (2.2): the dG(k)-in-time, (Q2)^d x P1disc-in-space slab problem
+ *     on I_n with Nitsche's method for Dirichlet data (Eq. (2.1));
+ *   - Sec. 3, Eq. (3.2): the unknown X_n = (v^{n,0}, p^{n,0}, ..., v^{n,k}, p^{n,k})
+ *     of the k+1 Gauss--Radau time nodes;
+ *   - Sec. 3, Eq. (3.3): the Newton/Oseen Jacobian J_n with (k+1) x (k+1)
+ *     saddle-point blocks [[D_ab, B_ab^T], [B_ab, 0]];
+ *   - Sec. 3: GMRES preconditioned by one geometric-multigrid V-cycle, a direct
+ *     solver on the coarsest mesh T_0 and the local Vanka smoother
+ *     S_K(d) = R_K d + omega J_K^{-1} R_K (b - J d) (Eq. (3.4)) applied through
+ *     the averaging loop (S0)-(S3).
+ *
+ * Conventions shared by every entry point:
+ *   - Vectors are caller-owned DEVICE buffers of doubles (e.g. torch tensors) in
+ *     the C-ABI order of X_n: time-node blocks a = 0..k; inside block a the R
+ *     velocity values (Q2 nodes numbered lexicographically with x fastest,
+ *     components interleaved: node*d + c), then the S pressure values (cells
+ *     numbered lexicographically with x fastest, d+1 P1disc coefficients
+ *     {1, xi_1, .., xi_d} per cell in the cell's reference coordinates).
+ *     Internally the library permutes to its own layout.
+ *   - All work is enqueued on the stream given to stg_setup; entry points that
+ *     return scalars to the host synchronise that stream.
+ *   - Errors are returned as a status; no call aborts.  stg_last_error gives a
+ *     text.  The context stays usable after STG_ENOCONV and STG_ESINGULAR.
+ *   - The context owns all device memory it allocates (freed by stg_destroy).
+ */
+#ifndef STG_H
+#define STG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stg_ctx stg_ctx;
+
+typedef enum {
+  STG_OK = 0,
+  STG_EINVAL = 1,     /* invalid argument (sizes, levels, null pointers)            */
+  STG_ENOMEM = 2,     /* device allocation failed                                    */
+  STG_ECUDA = 3,      /* a CUDA call or kernel launch failed                         */
+  STG_ESINGULAR = 4,  /* a zero pivot in a local J_K or a coarse block (cell id in   */
+                      /* stg_last_error)                                            */
+  STG_ENOCONV = 5,    /* FGMRES reached gmres_maxit; x and rel_res are still written */
+  STG_ETIMEOUT = 6    /* a device-side wait reached its iteration limit              */
+} stg_status;
+
+enum { STG_OSEEN = 0, STG_NEWTON = 1 };                 /* Sec. 3: terms of D_ab        */
+enum { STG_VANKA_AVERAGED = 0, STG_VANKA_COLOURED = 1 }; /* (S0)-(S3) / successive       */
+enum { STG_F64 = 0, STG_F32 = 1, STG_BF16 = 2 };        /* storage/arithmetic precision */
+
+/* Structured box mesh hierarchy (Sec. 2: nested partitions T_0..T_L, h_l = h_{l-1}/2).
+ * nx, ny (, nz) are the FINEST level's cells per direction; level l has
+ * n/2^(n_levels-1-l) cells per direction, so every n must be divisible by
+ * 2^(n_levels-1).  Bit 2*dir+side of dirichlet_faces marks a Dirichlet face
+ * (side 0 = low, 1 = high); the other faces carry the do-nothing condition
+ * (Sec. 1). */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int nx, ny, nz;          /* finest-level cells (nz ignored for dim = 2) */
+  int n_levels;            /* >= 1; level 0 is solved directly */
+  double x0, x1, y0, y1, z0, z1;
+  unsigned dirichlet_faces;
+} stg_mesh;
+
+typedef struct {
+  int linearisation;       /* STG_NEWTON (default) adds ((v . grad) w, psi) to D_ab   */
+  int smoother;            /* STG_VANKA_AVERAGED (default, (S0)-(S3)) | COLOURED     */
+  int nu1, nu2;            /* pre/post smoothing steps J_max (paper: 4; default 4)   */
+  double omega;            /* under-relaxation of Eq. (3.4) (paper: 0.7)             */
+  double gamma1, gamma2;   /* Nitsche penalties of Eq. (2.1) (paper: 35, 35)         */
+  int factor_prec;         /* storage of J_K^{-1}: STG_F64 | STG_F32 | STG_BF16       */
+  int vcycle_prec;         /* vectors/operators inside the V-cycle: STG_F64 | STG_F32 */
+  int gmres_restart;       /* FGMRES restart length (default 30)                      */
+  int gmres_maxit;         /* total inner iterations (default 200)                    */
+  double gmres_rtol;       /* stop at ||b - J x|| <= max(rtol ||b||, atol)            */
+  double gmres_atol;       /* (defaults 1e-8 and 0; the paper's absolute 1e-9: set    */
+                           /*  rtol = 0, atol = 1e-9)                                  */
+  int use_graph;           /* capture the V-cycle in a CUDA graph (default 1)         */
+} stg_options;
+
+/* Fills the defaults listed above.  Returns STG_EINVAL for a null pointer. */
+stg_status stg_options_default(stg_options* opt);
+
+/* Builds the level hierarchy, assembles J_l on every level (Eq. (3.3); coarse
+ * operators rediscretised with w injected at the coarse Q2 nodes), inverts
+ * every local J_K on levels l >= 1 (Eq. (3.4)) and factors J_0.
+ *   k      dG(k) degree, 0 <= k <= 4 (dim 2) or 0 <= k <= 2 (dim 3)
+ *   nu     viscosity; tau the slab length t_n - t_{n-1}
+ *   w      DEVICE doubles [(k+1) * R]: the linearisation velocity at the Q2
+ *          nodes of the finest level for each Radau node, in the velocity
+ *          part of the C-ABI order (block a holds R values); read during the
+ *          call only, caller-owned
+ *   stream a cudaStream_t (NULL = legacy default stream)
+ *   out    receives the new context (NULL on failure)
+ * Returns STG_EINVAL (bad mesh/k/options), STG_ENOMEM, STG_ECUDA or
+ * STG_ESINGULAR (a local J_K or the coarse system has a zero pivot). */
+stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const double* w,
+                     const stg_options* opt, void* stream, stg_ctx** out);
+
+/* Re-assembles and re-factors every level for a new linearisation velocity w
+ * (same layout as in stg_setup); allocates nothing. */
+stg_status stg_update_linearisation(stg_ctx* ctx, const double* w);
+
+/* y = J x on the finest level (Eq. (3.3)); x, y DEVICE doubles of length N. */
+stg_status stg_apply_jacobian(stg_ctx* ctx, const double* x, double* y);
+
+/* y = J_l x on level `level` (0 = coarsest); vectors in that level's C-ABI order. */
+stg_status stg_apply_level_jacobian(stg_ctx* ctx, int level, const double* x, double* y);
+
+/* x = V(b): one V-cycle on the finest level with initial guess 0 (Sec. 3),
+ * nu1 pre- and nu2 post-smoothing steps on levels >= 1, the direct solve on
+ * level 0.  b, x DEVICE doubles of length N. */
+stg_status stg_vcycle(stg_ctx* ctx, const double* b, double* x);
+
+/* `sweeps` smoothing steps on level `level` >= 1 for J_l x = b, updating x in
+ * place ((S0)-(S3) for STG_VANKA_AVERAGED).  Runs in the V-cycle precision. */
+stg_status stg_smooth(stg_ctx* ctx, int level, int sweeps, const double* b, double* x);
+
+/* Grid transfer (nested FE spaces; time nodes are not coarsened):
+ * stg_prolongate: x_fine += P x_coarse; stg_restrict: b_coarse = P^T r_fine.
+ * `level` is the FINE level (>= 1); vectors in the levels' C-ABI orders. */
+stg_status stg_prolongate(stg_ctx* ctx, int level, const double* x_coarse, double* x_fine);
+stg_status stg_restrict(stg_ctx* ctx, int level, const double* r_fine, double* b_coarse);
+
+/* x = J_0^{-1} b on the coarsest level (Sec. 3: direct solver on T_0).  With
+ * Dirichlet data on the whole boundary J_0 is singular (one constant-pressure
+ * mode per Radau node); the solution then has the pressure coefficient 0 of
+ * cell 0 equal to 0 for every Radau node.  b must be consistent. */
+stg_status stg_coarse_solve(stg_ctx* ctx, const double* b, double* x);
+
+/* Flexible GMRES, right-preconditioned by one V-cycle (Sec. 3).  x holds the
+ * initial guess on entry and the solution on exit; iters (total inner
+ * iterations) and rel_res (||b - J x|| / ||b||, recomputed in FP64) are host
+ * pointers, may be NULL, and are written even on STG_ENOCONV. */
+stg_status stg_gmres_solve(stg_ctx* ctx, const double* b, double* x, int* iters, double* rel_res);
+
+/* Sizes of level `level`: space-time DoFs N_l = (k+1)(R+S), cells, and the
+ * local patch size (k+1)(R^ + S^) (21(k+1) in 2D, 85(k+1) in 3D).  Host
+ * pointers, each may be NULL. */
+stg_status stg_get_sizes(const stg_ctx* ctx, int level, long long* n_dofs, long long* n_cells,
+                         int* n_patch);
+
+/* Copies J_K^{-1} of cell `cell` (cell number as in the C-ABI order) of level
+ * `level` >= 1 to the HOST buffer out[n_patch * n_patch], row-major, in the
+ * paper's local order dof(K, mu): time node a first, then the 3^d Q2 nodes
+ * (x fastest) times d components, then the d+1 pressure coefficients.  The
+ * values are those stored for the smoother (rounded to factor_prec). */
+stg_status stg_get_local_inverse(const stg_ctx* ctx, int level, long long cell, double* out);
+
+/* Text of the last error of this context (or of the last failed stg_setup
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* stg_last_error(const stg_ctx* ctx);
+
+/* Frees all device memory and the context.  NULL is accepted. */
+void stg_destroy(stg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STG_H */

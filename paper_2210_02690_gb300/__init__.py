@@ -1,0 +1,262 @@
+"""GB300-native space-time Vanka-multigrid GMRES solver (Python binding of libstg.so).
+
+The solver (Anselmann & Bause, Sec. 3) preconditions flexible GMRES with one
+geometric-multigrid V-cycle whose smoother is the local Vanka operator of
+Eq. (3.4) applied through the averaging loop (S0)-(S3), for the Newton/Oseen
+Jacobian (Eq. (3.3)) of the dG(k)-in-time, (Q2)^d x P1disc-in-space slab
+problem of Eq. (2.2).  All arithmetic runs in the CUDA library (include/stg.h);
+this module only marshals arguments: torch provides device memory and a
+stream.  There is no CPU fallback: every call fails loudly when libstg.so is
+missing or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libstg.so")
+
+STG_OK, STG_EINVAL, STG_ENOMEM, STG_ECUDA, STG_ESINGULAR, STG_ENOCONV, STG_ETIMEOUT = range(7)
+STG_OSEEN, STG_NEWTON = 0, 1
+STG_VANKA_AVERAGED, STG_VANKA_COLOURED = 0, 1
+STG_F64, STG_F32, STG_BF16 = 0, 1, 2
+PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16}
+
+EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg_apply_jacobian",
+            "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
+            "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_last_error",
+            "stg_destroy")
+
+
+class StgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"stg status {status}: {msg}")
+        self.status = status
+
+
+class stg_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("z0", ctypes.c_double),
+                ("z1", ctypes.c_double), ("dirichlet_faces", ctypes.c_uint)]
+
+
+class stg_options(ctypes.Structure):
+    _fields_ = [("linearisation", ctypes.c_int), ("smoother", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("gamma1", ctypes.c_double),
+                ("gamma2", ctypes.c_double), ("factor_prec", ctypes.c_int), ("vcycle_prec", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
+                ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libstg.so and declares the signatures of include/stg.h."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, D, I, LL = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "stg_options_default": (I, [ctypes.POINTER(stg_options)]),
+        "stg_setup": (I, [ctypes.POINTER(stg_mesh), I, D, D, P, ctypes.POINTER(stg_options), P,
+                          ctypes.POINTER(P)]),
+        "stg_update_linearisation": (I, [P, P]),
+        "stg_apply_jacobian": (I, [P, P, P]),
+        "stg_apply_level_jacobian": (I, [P, I, P, P]),
+        "stg_vcycle": (I, [P, P, P]),
+        "stg_smooth": (I, [P, I, I, P, P]),
+        "stg_prolongate": (I, [P, I, P, P]),
+        "stg_restrict": (I, [P, I, P, P]),
+        "stg_coarse_solve": (I, [P, P, P]),
+        "stg_gmres_solve": (I, [P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stg_get_sizes": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(I)]),
+        "stg_get_local_inverse": (I, [P, I, LL, P]),
+        "stg_last_error": (ctypes.c_char_p, [P]),
+        "stg_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def make_mesh(spec) -> stg_mesh:
+    """stg_mesh from a stg_inputs.MeshSpec-like object (dim, n, lo, hi, n_levels, dirichlet)."""
+    n = list(spec.n) + [1] * (3 - len(spec.n))
+    lo = list(spec.lo) + [0.0] * (3 - len(spec.lo))
+    hi = list(spec.hi) + [1.0] * (3 - len(spec.hi))
+    return stg_mesh(spec.dim, n[0], n[1], n[2], spec.n_levels, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2],
+                    spec.dirichlet)
+
+
+def make_options(**kw) -> stg_options:
+    lib = load_library()
+    o = stg_options()
+    lib.stg_options_default(ctypes.byref(o))
+    for key, val in kw.items():
+        if key in ("factor_prec", "vcycle_prec") and isinstance(val, str):
+            val = PREC[val]
+        if key == "smoother" and isinstance(val, str):
+            val = {"averaged": STG_VANKA_AVERAGED, "coloured": STG_VANKA_COLOURED}[val]
+        if key == "linearisation" and isinstance(val, str):
+            val = {"oseen": STG_OSEEN, "newton": STG_NEWTON}[val]
+        setattr(o, key, val)
+    return o
+
+
+def _check(lib, ctx, status: int):
+    if status not in (STG_OK, STG_ENOCONV):
+        msg = lib.stg_last_error(ctx)
+        raise StgError(status, msg.decode() if msg else "")
+    return status
+
+
+class Solver:
+    """One slab problem on one GPU: wraps an stg_ctx and a private CUDA stream.
+
+    All tensors are float64 CUDA tensors in the C-ABI order of X_n.  Each call
+    orders itself after the caller's current stream and makes the caller's
+    stream wait for it, so it composes with ordinary torch code.
+    """
+
+    def __init__(self, spec, k: int, nu: float, tau: float, w, **options):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2210_02690_gb300 needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.lib = load_library()
+        self.spec, self.k, self.nu, self.tau = spec, k, nu, tau
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.mesh = make_mesh(spec)
+        self.opts = make_options(**options)
+        w = self._dev(w)
+        ctx = ctypes.c_void_p()
+        self._enter()
+        st = self.lib.stg_setup(ctypes.byref(self.mesh), k, nu, tau, ctypes.c_void_p(w.data_ptr()),
+                                ctypes.byref(self.opts), ctypes.c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(ctx))
+        self._leave()
+        if st != STG_OK:
+            msg = self.lib.stg_last_error(None)
+            raise StgError(st, msg.decode() if msg else "")
+        self.ctx = ctx
+
+    # -- stream plumbing
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _leave(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _dev(self, a):
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+        a = a.to(device=self.device, dtype=t.float64).contiguous()
+        return a
+
+    @staticmethod
+    def _p(a):
+        return ctypes.c_void_p(a.data_ptr())
+
+    def _call(self, fn, *args):
+        self._enter()
+        try:
+            return _check(self.lib, self.ctx, fn(self.ctx, *args))
+        finally:
+            self._leave()
+
+    def sizes(self, level: int = -1):
+        level = self.spec.n_levels - 1 if level < 0 else level
+        nd, nc, npch = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        _check(self.lib, self.ctx, self.lib.stg_get_sizes(self.ctx, level, ctypes.byref(nd), ctypes.byref(nc),
+                                                          ctypes.byref(npch)))
+        return nd.value, nc.value, npch.value
+
+    def update_linearisation(self, w):
+        w = self._dev(w)
+        self._call(self.lib.stg_update_linearisation, self._p(w))
+
+    def apply_jacobian(self, x, level: int = -1):
+        level = self.spec.n_levels - 1 if level < 0 else level
+        x = self._dev(x)
+        y = self.torch.empty_like(x)
+        self._call(self.lib.stg_apply_level_jacobian, level, self._p(x), self._p(y))
+        return y
+
+    def vcycle(self, b, out=None):
+        b = self._dev(b)
+        x = self.torch.empty_like(b) if out is None else out
+        self._call(self.lib.stg_vcycle, self._p(b), self._p(x))
+        return x
+
+    def smooth(self, level: int, sweeps: int, b, x):
+        b = self._dev(b)
+        x = self._dev(x).clone()
+        self._call(self.lib.stg_smooth, level, sweeps, self._p(b), self._p(x))
+        return x
+
+    def prolongate(self, level: int, xc, xf):
+        xc = self._dev(xc)
+        xf = self._dev(xf).clone()
+        self._call(self.lib.stg_prolongate, level, self._p(xc), self._p(xf))
+        return xf
+
+    def restrict(self, level: int, rf):
+        rf = self._dev(rf)
+        nd, _, _ = self.sizes(level - 1)
+        bc = self.torch.empty(nd, dtype=self.torch.float64, device=self.device)
+        self._call(self.lib.stg_restrict, level, self._p(rf), self._p(bc))
+        return bc
+
+    def coarse_solve(self, b):
+        b = self._dev(b)
+        x = self.torch.empty_like(b)
+        self._call(self.lib.stg_coarse_solve, self._p(b), self._p(x))
+        return x
+
+    def gmres_solve(self, b, x0=None, out=None):
+        """Returns (x, total inner iterations, relative residual, converged)."""
+        b = self._dev(b)
+        if out is not None:
+            x = out
+            if x0 is None:
+                x.zero_()
+            else:
+                x.copy_(self._dev(x0))
+        else:
+            x = self.torch.zeros_like(b) if x0 is None else self._dev(x0).clone()
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        st = self._call(self.lib.stg_gmres_solve, self._p(b), self._p(x), ctypes.byref(its), ctypes.byref(rel))
+        return x, its.value, rel.value, st == STG_OK
+
+    def local_inverse(self, level: int, cell: int) -> np.ndarray:
+        n = self.sizes(level)[2]
+        out = np.zeros((n, n))
+        self.stream.synchronize()
+        _check(self.lib, self.ctx, self.lib.stg_get_local_inverse(self.ctx, level, cell,
+                                                                  out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.stg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

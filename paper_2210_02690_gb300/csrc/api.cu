@@ -1,0 +1,803 @@
+// C-ABI of the solver: context, level hierarchy, V-cycle and flexible GMRES (Sec. 3).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "coarse.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace stg {
+
+// ------------------------------------------------------------------ geometry
+Geom make_geom(const stg_mesh& m, int level, int k) {
+  Geom g{};
+  g.dim = m.dim;
+  g.k = k;
+  g.nt = k + 1;
+  const int f = 1 << (m.n_levels - 1 - level);
+  const int nf[3] = {m.nx, m.ny, m.dim == 3 ? m.nz : 1};
+  const double lo[3] = {m.x0, m.y0, m.z0}, hi[3] = {m.x1, m.y1, m.z1};
+  for (int e = 0; e < 3; ++e) {
+    if (e < m.dim) {
+      g.n[e] = nf[e] / f;
+      g.nn[e] = 2 * g.n[e] + 1;
+      g.lo[e] = lo[e];
+      g.h[e] = (hi[e] - lo[e]) / g.n[e];
+    } else {
+      g.n[e] = 1;
+      g.nn[e] = 1;
+      g.lo[e] = 0.0;
+      g.h[e] = 1.0;
+    }
+  }
+  g.dirichlet = m.dirichlet_faces;
+  g.NV = g.nt * g.dim;
+  g.NP = g.nt * (g.dim + 1);
+  g.nloc = g.dim == 2 ? 9 : 27;
+  g.npatch = g.nloc * g.NV + g.NP;
+  g.n_nodes = (long long)g.nn[0] * g.nn[1] * g.nn[2];
+  g.n_cells = (long long)g.n[0] * g.n[1] * g.n[2];
+  g.nvel = g.n_nodes * g.NV;
+  g.npres = g.n_cells * g.NP;
+  g.N = g.nvel + g.npres;
+  g.coff[0] = 0;
+  for (int c = 0; c < 8; ++c) {
+    long long cnt = 1;
+    for (int e = 0; e < 3; ++e) {
+      const int p = (c >> e) & 1;
+      int ce;
+      if (e < g.dim)
+        ce = (g.n[e] - p + 1) / 2;
+      else
+        ce = p ? 0 : 1;
+      g.ccount[c][e] = ce;
+      cnt *= ce;
+    }
+    if (c >= (1 << g.dim)) cnt = 0;
+    g.coff[c + 1] = g.coff[c] + cnt;
+  }
+  return g;
+}
+
+// ------------------------------------------------------------------ time basis
+namespace {
+using Poly = std::vector<double>;  // monomial coefficients, low order first
+Poly pmul(const Poly& a, const Poly& b) {
+  Poly r(a.size() + b.size() - 1, 0.0);
+  for (size_t i = 0; i < a.size(); ++i)
+    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
+  return r;
+}
+Poly pder(const Poly& a) {
+  Poly r(a.size() > 1 ? a.size() - 1 : 1, 0.0);
+  for (size_t i = 1; i < a.size(); ++i) r[i - 1] = a[i] * (double)i;
+  return r;
+}
+double pint01(const Poly& a) {
+  double s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] / (double)(i + 1);
+  return s;
+}
+double legendre(int n, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0, p1 = x;
+  for (int i = 1; i < n; ++i) {
+    const double p2 = ((2.0 * i + 1.0) * x * p1 - i * p0) / (i + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+}  // namespace
+
+TimeData time_basis(int k) {
+  // right Radau points: roots of P_k - P_{k+1} on (-1, 1], mapped to [0, 1]
+  auto f = [k](double x) { return legendre(k, x) - legendre(k + 1, x); };
+  std::vector<double> x;
+  const int ns = 4000;
+  for (int i = 0; i < ns; ++i) {
+    double a = -1.0 + 2.0 * i / ns, b = -1.0 + 2.0 * (i + 1) / ns;
+    if (i == ns - 1) break;  // the root x = 1 is added exactly below
+    double fa = f(a), fb = f(b);
+    if (fa == 0.0) {
+      x.push_back(a);
+      continue;
+    }
+    if (fa * fb < 0.0) {
+      for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (a + b), fm = f(m);
+        if (fa * fm <= 0.0) {
+          b = m;
+        } else {
+          a = m;
+          fa = fm;
+        }
+      }
+      x.push_back(0.5 * (a + b));
+    }
+  }
+  x.push_back(1.0);
+  if ((int)x.size() != k + 1) throw Error{STG_EINVAL, "Radau root search failed"};
+  TimeData td{};
+  std::vector<Poly> chi(k + 1);
+  for (int a = 0; a <= k; ++a) {
+    td.c[a] = 0.5 * (x[a] + 1.0);
+  }
+  for (int a = 0; a <= k; ++a) {
+    Poly p{1.0};
+    for (int b = 0; b <= k; ++b)
+      if (b != a) p = pmul(p, Poly{-td.c[b] / (td.c[a] - td.c[b]), 1.0 / (td.c[a] - td.c[b])});
+    chi[a] = p;
+    td.w[a] = pint01(p);
+    td.jump[a] = p[0];
+  }
+  for (int a = 0; a <= k; ++a)
+    for (int b = 0; b <= k; ++b) td.T[a][b] = pint01(pmul(pder(chi[b]), chi[a])) + chi[a][0] * chi[b][0];
+  return td;
+}
+
+}  // namespace stg
+
+using namespace stg;
+
+// ------------------------------------------------------------------ context
+struct LevelBufs {
+  Geom g{};
+  int* rowptr = nullptr;
+  int* colidx = nullptr;
+  long long nnzb = 0;
+  double *vv = nullptr, *vp = nullptr, *pv = nullptr;
+  float *vv32 = nullptr, *vp32 = nullptr, *pv32 = nullptr;
+  void* jinv = nullptr;
+  double* w = nullptr;
+  void *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
+};
+
+struct stg_ctx {
+  stg_mesh mesh{};
+  stg_options opt{};
+  int k = 0;
+  double nu = 0, tau = 0;
+  cudaStream_t st = nullptr;
+  TimeData td{};
+  std::vector<LevelBufs> lv;
+  CoarseSolver coarse;
+  double *cb64 = nullptr, *cx64 = nullptr;
+  int* status = nullptr;
+  void* inv_scratch = nullptr;
+  // FGMRES (finest level, internal layout, FP64)
+  double *V = nullptr, *Z = nullptr, *wv = nullptr, *rv = nullptr, *partial = nullptr, *hd = nullptr;
+  double *vin = nullptr, *vout = nullptr, *tmp_a = nullptr, *tmp_b = nullptr;
+  double* hh = nullptr;  // pinned host
+  cudaGraphExec_t graph = nullptr;
+  std::vector<void*> owned;
+  std::string err;
+  bool pure_dirichlet = false;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+template <typename T>
+T* dalloc(stg_ctx* c, long long n) {
+  T* p = nullptr;
+  const size_t bytes = sizeof(T) * (size_t)(n > 0 ? n : 1);
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{STG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+  }
+  c->owned.push_back(p);
+  return p;
+}
+
+size_t fsize(int prec) { return prec == STG_F64 ? 8 : (prec == STG_F32 ? 4 : 2); }
+
+void build_pattern(stg_ctx* c, LevelBufs& L) {
+  const Geom& g = L.g;
+  std::vector<int> rowptr(g.n_nodes + 1, 0);
+  std::vector<int> colidx;
+  long long nnz = 0;
+  for (int iz = 0; iz < g.nn[2]; ++iz)
+    for (int iy = 0; iy < g.nn[1]; ++iy)
+      for (int ix = 0; ix < g.nn[0]; ++ix) {
+        int xl, xh, yl, yh, zl, zh;
+        stencil_range(ix, g.nn[0], xl, xh);
+        stencil_range(iy, g.nn[1], yl, yh);
+        stencil_range(iz, g.nn[2], zl, zh);
+        for (int jz = zl; jz <= zh; ++jz)
+          for (int jy = yl; jy <= yh; ++jy)
+            for (int jx = xl; jx <= xh; ++jx) colidx.push_back((int)node_id(g, jx, jy, jz));
+        nnz += (long long)(xh - xl + 1) * (yh - yl + 1) * (zh - zl + 1);
+        if (nnz > 2147483647LL) throw Error{STG_EINVAL, "level too large for 32-bit block indices"};
+        rowptr[node_id(g, ix, iy, iz) + 1] = (int)nnz;
+      }
+  L.nnzb = nnz;
+  L.rowptr = dalloc<int>(c, g.n_nodes + 1);
+  L.colidx = dalloc<int>(c, nnz);
+  STG_CUDA_OK(cudaMemcpy(L.rowptr, rowptr.data(), sizeof(int) * rowptr.size(), cudaMemcpyHostToDevice));
+  STG_CUDA_OK(cudaMemcpy(L.colidx, colidx.data(), sizeof(int) * colidx.size(), cudaMemcpyHostToDevice));
+}
+
+bool vc64(const stg_ctx* c) { return c->opt.vcycle_prec == STG_F64; }
+
+// Assemble every level, invert the local matrices, factor the coarse system.
+void linearise(stg_ctx* c, const double* w_cabi) {
+  const int nl = (int)c->lv.size();
+  LevelBufs& F = c->lv[nl - 1];
+  w_to_internal(F.g, w_cabi, F.w, c->st);
+  for (int l = nl - 1; l > 0; --l) inject_w(c->lv[l - 1].g, c->lv[l].g, c->lv[l].w, c->lv[l - 1].w, c->st);
+  AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, c->opt.linearisation == STG_NEWTON ? 1 : 0};
+  STG_CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
+  for (int l = 0; l < nl; ++l) {
+    LevelBufs& L = c->lv[l];
+    assemble_level(L.g, c->td, cf, L.w, L.rowptr, L.vv, L.nnzb, L.vp, L.pv, c->st);
+    if (!vc64(c)) {
+      convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, c->st);
+      const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
+      convert(nvp, L.vp, L.vp32, c->st);
+      convert(nvp, L.pv, L.pv32, c->st);
+    }
+    if (l == 0) continue;
+    const int fp = c->opt.factor_prec;
+    const int cf32 = fp != STG_F64 && invert_scratch_bytes(L.g, 0) > 0 ? 1 : 0;
+    if (fp == STG_F64)
+      invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, (double*)L.jinv, 0, c->status, c->inv_scratch, c->st);
+    else if (fp == STG_F32)
+      invert_patches<float>(L.g, L.rowptr, L.vv, L.vp, L.pv, (float*)L.jinv, cf32, c->status, c->inv_scratch,
+                            c->st);
+    else
+      invert_patches<__nv_bfloat16>(L.g, L.rowptr, L.vv, L.vp, L.pv, (__nv_bfloat16*)L.jinv, cf32, c->status,
+                                    c->inv_scratch, c->st);
+  }
+  LevelBufs& C0 = c->lv[0];
+  c->coarse.factor(C0.rowptr, C0.colidx, C0.vv, C0.vp, C0.pv, c->st);
+  int hs[4];
+  STG_CUDA_OK(cudaMemcpyAsync(hs, c->status, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  STG_CUDA_OK(cudaStreamSynchronize(c->st));
+  if (hs[0]) throw Error{STG_ESINGULAR, "singular local matrix J_K of cell " + std::to_string(hs[0] - 1)};
+  const int cs = c->coarse.read_status(c->st);
+  if (cs > 0) throw Error{STG_ESINGULAR, "singular block in the coarse solver (block " + std::to_string(cs - 1) + ")"};
+  if (cs < 0) throw Error{STG_ECUDA, "coarse matrix coupling outside the slab block structure"};
+}
+
+template <typename VT>
+struct Ops;
+template <>
+struct Ops<double> {
+  static const double* vv(const LevelBufs& L) { return L.vv; }
+  static const double* vp(const LevelBufs& L) { return L.vp; }
+  static const double* pv(const LevelBufs& L) { return L.pv; }
+};
+template <>
+struct Ops<float> {
+  static const float* vv(const LevelBufs& L) { return L.vv32; }
+  static const float* vp(const LevelBufs& L) { return L.vp32; }
+  static const float* pv(const LevelBufs& L) { return L.pv32; }
+};
+
+template <typename VT>
+void residual(stg_ctx* c, const LevelBufs& L, const VT* x, const VT* b, VT* r) {
+  apply_operator<VT, VT>(L.g, L.rowptr, L.colidx, Ops<VT>::vv(L), Ops<VT>::vp(L), Ops<VT>::pv(L), x, b, r, c->st);
+}
+
+template <typename VT, typename FT>
+void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
+  LevelBufs& L = c->lv[l];
+  const Geom& g = L.g;
+  VT* b = (VT*)L.b;
+  VT* x = (VT*)L.x;
+  VT* r = (VT*)L.r;
+  VT* z = (VT*)L.z;
+  const FT* jinv = (const FT*)L.jinv;
+  const int ncol = 1 << g.dim;
+  for (int s = 0; s < sweeps; ++s) {
+    if (c->opt.smoother == STG_VANKA_AVERAGED) {
+      const VT* res = b;
+      if (!(x_zero && s == 0)) {
+        residual<VT>(c, L, x, b, r);
+        res = r;
+      }
+      for (int col = 0; col < ncol; ++col) vanka_colour<VT, FT>(g, col, jinv, res, z, (VT)1, c->st);
+      vanka_update<VT>(g, x, z, c->opt.omega, c->st);
+    } else {
+      for (int col = 0; col < ncol; ++col) {
+        const VT* res = b;
+        if (!(x_zero && s == 0 && col == 0)) {
+          residual<VT>(c, L, x, b, r);
+          res = r;
+        }
+        vanka_colour<VT, FT>(g, col, jinv, res, x, (VT)c->opt.omega, c->st);
+      }
+    }
+  }
+}
+
+template <typename VT>
+void coarse_level(stg_ctx* c) {
+  LevelBufs& L = c->lv[0];
+  if (std::is_same<VT, double>::value) {
+    c->coarse.solve((const double*)L.b, (double*)L.x, c->st);
+  } else {
+    convert(L.g.N, (const float*)L.b, c->cb64, c->st);
+    c->coarse.solve(c->cb64, c->cx64, c->st);
+    convert(L.g.N, c->cx64, (float*)L.x, c->st);
+  }
+}
+
+template <typename VT, typename FT>
+void vcycle_level(stg_ctx* c, int l) {
+  if (l == 0) {
+    coarse_level<VT>(c);
+    return;
+  }
+  LevelBufs& L = c->lv[l];
+  LevelBufs& Lc = c->lv[l - 1];
+  STG_CUDA_OK(cudaMemsetAsync(L.x, 0, sizeof(VT) * L.g.N, c->st));
+  smooth_level<VT, FT>(c, l, c->opt.nu1, true);
+  residual<VT>(c, L, (const VT*)L.x, (const VT*)L.b, (VT*)L.r);
+  restrict_res<VT>(Lc.g, L.g, (const VT*)L.r, (VT*)Lc.b, c->st);
+  vcycle_level<VT, FT>(c, l - 1);
+  prolongate_add<VT>(Lc.g, L.g, (const VT*)Lc.x, (VT*)L.x, c->st);
+  smooth_level<VT, FT>(c, l, c->opt.nu2, false);
+}
+
+// V-cycle from c->vin (FP64 internal) to c->vout (FP64 internal)
+void vcycle_body(stg_ctx* c) {
+  LevelBufs& F = c->lv.back();
+  const int top = (int)c->lv.size() - 1;
+  if (vc64(c)) {
+    STG_CUDA_OK(cudaMemcpyAsync(F.b, c->vin, sizeof(double) * F.g.N, cudaMemcpyDeviceToDevice, c->st));
+    vcycle_level<double, double>(c, top);
+    STG_CUDA_OK(cudaMemcpyAsync(c->vout, F.x, sizeof(double) * F.g.N, cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    convert(F.g.N, c->vin, (float*)F.b, c->st);
+    if (c->opt.factor_prec == STG_F32)
+      vcycle_level<float, float>(c, top);
+    else
+      vcycle_level<float, __nv_bfloat16>(c, top);
+    convert(F.g.N, (const float*)F.x, c->vout, c->st);
+  }
+}
+
+void run_vcycle(stg_ctx* c) {
+  if (c->opt.use_graph) {
+    if (!c->graph) {
+      cudaGraph_t graph = nullptr;
+      STG_CUDA_OK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+      try {
+        vcycle_body(c);
+      } catch (...) {
+        cudaStreamEndCapture(c->st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      STG_CUDA_OK(cudaStreamEndCapture(c->st, &graph));
+      const cudaError_t e = cudaGraphInstantiate(&c->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      STG_CUDA_OK(e);
+    }
+    STG_CUDA_OK(cudaGraphLaunch(c->graph, c->st));
+  } else {
+    vcycle_body(c);
+  }
+}
+
+template <typename VT>
+void level_to_internal(stg_ctx* c, int l, const double* in, VT* out) {
+  cabi_to_internal<VT>(c->lv[l].g, in, out, c->st);
+}
+
+void apply_fine64(stg_ctx* c, const double* x, double* y) {
+  const LevelBufs& F = c->lv.back();
+  apply_operator<double, double>(F.g, F.rowptr, F.colidx, F.vv, F.vp, F.pv, x, nullptr, y, c->st);
+}
+
+double dot_host(stg_ctx* c, const double* a, const double* b) {
+  const long long n = c->lv.back().g.N;
+  multi_dot(n, 1, a, n, b, c->partial, c->hd, c->st);
+  STG_CUDA_OK(cudaMemcpyAsync(c->hh, c->hd, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  STG_CUDA_OK(cudaStreamSynchronize(c->st));
+  return c->hh[0];
+}
+
+// Flexible GMRES(m), right preconditioned by one V-cycle; b, x internal FP64.
+stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double* rel_out) {
+  const long long n = c->lv.back().g.N;
+  const int m = c->opt.gmres_restart;
+  const double bnorm = std::sqrt(dot_host(c, b, b));
+  const double tol = std::max(c->opt.gmres_rtol * bnorm, c->opt.gmres_atol);
+  int its = 0;
+  double beta = 0.0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  for (;;) {
+    apply_fine64(c, x, c->rv);
+    axpby(n, 1.0, b, -1.0, c->rv, c->st);  // r = b - J x
+    beta = std::sqrt(dot_host(c, c->rv, c->rv));
+    if (beta <= tol || its >= c->opt.gmres_maxit || bnorm == 0.0) break;
+    axpby(n, 1.0 / beta, c->rv, 0.0, c->V, c->st);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = c->V + (long long)j * n;
+      double* zj = c->Z + (long long)j * n;
+      STG_CUDA_OK(cudaMemcpyAsync(c->vin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+      run_vcycle(c);
+      STG_CUDA_OK(cudaMemcpyAsync(zj, c->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+      apply_fine64(c, zj, c->wv);
+      // classical Gram-Schmidt, twice
+      multi_dot(n, j + 1, c->V, n, c->wv, c->partial, c->hd, c->st);
+      multi_axpy_sub(n, j + 1, c->V, n, c->hd, c->wv, c->st);
+      multi_dot(n, j + 1, c->V, n, c->wv, c->partial, c->hd + 32, c->st);
+      multi_axpy_sub(n, j + 1, c->V, n, c->hd + 32, c->wv, c->st);
+      multi_dot(n, 1, c->wv, n, c->wv, c->partial, c->hd + 64, c->st);
+      STG_CUDA_OK(cudaMemcpyAsync(c->hh, c->hd, sizeof(double) * 65, cudaMemcpyDeviceToHost, c->st));
+      STG_CUDA_OK(cudaStreamSynchronize(c->st));
+      for (int i = 0; i <= j; ++i) Hc(i, j) = c->hh[i] + c->hh[32 + i];
+      const double hn = std::sqrt(std::max(c->hh[64], 0.0));
+      Hc(j + 1, j) = hn;
+      if (hn > 0.0) axpby(n, 1.0 / hn, c->wv, 0.0, c->V + (long long)(j + 1) * n, c->st);
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+        Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+        Hc(i, j) = t;
+      }
+      const double rho = std::hypot(Hc(j, j), Hc(j + 1, j));
+      cs[j] = rho > 0 ? Hc(j, j) / rho : 1.0;
+      sn[j] = rho > 0 ? Hc(j + 1, j) / rho : 0.0;
+      Hc(j, j) = rho;
+      Hc(j + 1, j) = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++its;
+      jend = j + 1;
+      if (std::fabs(gv[j + 1]) <= tol || its >= c->opt.gmres_maxit || rho == 0.0 || hn == 0.0) break;
+    }
+    for (int i = jend - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int l = i + 1; l < jend; ++l) s -= Hc(i, l) * y[l];
+      y[i] = Hc(i, i) != 0.0 ? s / Hc(i, i) : 0.0;
+    }
+    STG_CUDA_OK(cudaMemcpyAsync(c->hd + 96, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, c->st));
+    multi_axpy_add(n, jend, c->Z, n, c->hd + 96, x, c->st);
+  }
+  if (iters_out) *iters_out = its;
+  if (rel_out) *rel_out = bnorm > 0 ? beta / bnorm : 0.0;
+  return beta <= tol || bnorm == 0.0 ? STG_OK : STG_ENOCONV;
+}
+
+stg_status fail(stg_ctx* c, const Error& e) {
+  if (c)
+    c->err = e.msg;
+  else
+    g_setup_error = e.msg;
+  return e.st;
+}
+
+stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
+  if (!m || !o) throw Error{STG_EINVAL, "null mesh or options"};
+  if (m->dim != 2 && m->dim != 3) throw Error{STG_EINVAL, "dim must be 2 or 3"};
+  if (m->n_levels < 1 || m->n_levels > 12) throw Error{STG_EINVAL, "n_levels must be in 1..12"};
+  if (k < 0 || k > (m->dim == 2 ? 4 : 2)) throw Error{STG_EINVAL, "k out of range (2D: 0..4, 3D: 0..2)"};
+  const int f = 1 << (m->n_levels - 1);
+  const int n[3] = {m->nx, m->ny, m->dim == 3 ? m->nz : f};
+  for (int e = 0; e < m->dim; ++e)
+    if (n[e] < f || n[e] % f) throw Error{STG_EINVAL, "cells per direction must be a positive multiple of 2^(n_levels-1)"};
+  const double lo[3] = {m->x0, m->y0, m->z0}, hi[3] = {m->x1, m->y1, m->z1};
+  for (int e = 0; e < m->dim; ++e)
+    if (!(hi[e] > lo[e])) throw Error{STG_EINVAL, "empty domain"};
+  if (o->vcycle_prec == STG_F64 && o->factor_prec != STG_F64)
+    throw Error{STG_EINVAL, "an FP64 V-cycle needs FP64 local inverses"};
+  if (o->vcycle_prec == STG_F32 && o->factor_prec == STG_F64)
+    throw Error{STG_EINVAL, "an FP32 V-cycle takes FP32 or BF16 local inverses"};
+  if (o->vcycle_prec != STG_F64 && o->vcycle_prec != STG_F32) throw Error{STG_EINVAL, "bad vcycle_prec"};
+  if (o->nu1 < 0 || o->nu2 < 0) throw Error{STG_EINVAL, "negative smoothing steps"};
+  if (o->gmres_restart < 1 || o->gmres_restart > 30) throw Error{STG_EINVAL, "gmres_restart must be in 1..30"};
+  if (o->smoother != STG_VANKA_AVERAGED && o->smoother != STG_VANKA_COLOURED) throw Error{STG_EINVAL, "bad smoother"};
+  return STG_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+stg_status stg_options_default(stg_options* o) {
+  if (!o) return STG_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->linearisation = STG_NEWTON;
+  o->smoother = STG_VANKA_AVERAGED;
+  o->nu1 = 4;
+  o->nu2 = 4;
+  o->omega = 0.7;
+  o->gamma1 = 35.0;
+  o->gamma2 = 35.0;
+  o->factor_prec = STG_F64;
+  o->vcycle_prec = STG_F64;
+  o->gmres_restart = 30;
+  o->gmres_maxit = 200;
+  o->gmres_rtol = 1e-8;
+  o->gmres_atol = 0.0;
+  o->use_graph = 1;
+  return STG_OK;
+}
+
+stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const double* w, const stg_options* opt,
+                     void* stream, stg_ctx** out) {
+  if (!out) return STG_EINVAL;
+  *out = nullptr;
+  stg_ctx* c = nullptr;
+  try {
+    validate(mesh, k, opt);
+    if (!w) throw Error{STG_EINVAL, "null linearisation velocity"};
+    c = new (std::nothrow) stg_ctx();
+    if (!c) throw Error{STG_ENOMEM, "host allocation failed"};
+    c->mesh = *mesh;
+    c->opt = *opt;
+    c->k = k;
+    c->nu = nu;
+    c->tau = tau;
+    c->st = (cudaStream_t)stream;
+    c->td = time_basis(k);
+    c->pure_dirichlet = mesh->dirichlet_faces == (1u << (2 * mesh->dim)) - 1u;
+    upload_fe_tables();
+    const int nl = mesh->n_levels;
+    c->lv.resize(nl);
+    size_t scratch = 0;
+    const bool f64 = vc64(c);
+    const size_t vts = f64 ? 8 : 4;
+    for (int l = 0; l < nl; ++l) {
+      LevelBufs& L = c->lv[l];
+      L.g = make_geom(*mesh, l, k);
+      const Geom& g = L.g;
+      build_pattern(c, L);
+      L.vv = dalloc<double>(c, L.nnzb * g.NV * g.NV);
+      const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * (g.dim + 1);
+      L.vp = dalloc<double>(c, nvp);
+      L.pv = dalloc<double>(c, nvp);
+      if (!f64) {
+        L.vv32 = dalloc<float>(c, L.nnzb * g.NV * g.NV);
+        L.vp32 = dalloc<float>(c, nvp);
+        L.pv32 = dalloc<float>(c, nvp);
+      }
+      L.w = dalloc<double>(c, g.nvel);
+      L.b = dalloc<char>(c, (long long)vts * g.N);
+      L.x = dalloc<char>(c, (long long)vts * g.N);
+      L.r = dalloc<char>(c, (long long)vts * g.N);
+      L.z = dalloc<char>(c, (long long)vts * g.N);
+      STG_CUDA_OK(cudaMemset(L.z, 0, vts * g.N));
+      STG_CUDA_OK(cudaMemset(L.x, 0, vts * g.N));
+      if (l > 0) {
+        L.jinv = dalloc<char>(c, (long long)fsize(opt->factor_prec) * patch_stride(g.npatch) * g.n_cells);
+        const int cf32 = opt->factor_prec != STG_F64 && invert_scratch_bytes(g, 0) > 0 ? 1 : 0;
+        scratch = std::max(scratch, invert_scratch_bytes(g, cf32));
+      }
+    }
+    if (scratch) c->inv_scratch = dalloc<char>(c, (long long)scratch);
+    c->coarse.init(c->lv[0].g, c->pure_dirichlet);
+    c->cb64 = dalloc<double>(c, c->lv[0].g.N);
+    c->cx64 = dalloc<double>(c, c->lv[0].g.N);
+    c->status = dalloc<int>(c, 4);
+    const long long n = c->lv.back().g.N;
+    const int m = opt->gmres_restart;
+    c->V = dalloc<double>(c, (long long)(m + 1) * n);
+    c->Z = dalloc<double>(c, (long long)m * n);
+    c->wv = dalloc<double>(c, n);
+    c->rv = dalloc<double>(c, n);
+    c->vin = dalloc<double>(c, n);
+    c->vout = dalloc<double>(c, n);
+    c->tmp_a = dalloc<double>(c, n);
+    c->tmp_b = dalloc<double>(c, n);
+    c->partial = dalloc<double>(c, (long long)dot_partial_doubles());
+    c->hd = dalloc<double>(c, 160);
+    STG_CUDA_OK(cudaMallocHost(&c->hh, sizeof(double) * 160));
+    linearise(c, w);
+    *out = c;
+    return STG_OK;
+  } catch (const Error& e) {
+    g_setup_error = e.msg;
+    if (c) stg_destroy(c);
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    g_setup_error = "host allocation failed";
+    if (c) stg_destroy(c);
+    return STG_ENOMEM;
+  }
+}
+
+stg_status stg_update_linearisation(stg_ctx* c, const double* w) {
+  if (!c || !w) return STG_EINVAL;
+  try {
+    linearise(c, w);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_apply_level_jacobian(stg_ctx* c, int level, const double* x, double* y) {
+  if (!c || !x || !y || level < 0 || level >= (int)c->lv.size()) return STG_EINVAL;
+  try {
+    const LevelBufs& L = c->lv[level];
+    cabi_to_internal<double>(L.g, x, c->tmp_a, c->st);
+    apply_operator<double, double>(L.g, L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->tmp_a, nullptr, c->tmp_b, c->st);
+    internal_to_cabi<double>(L.g, c->tmp_b, y, c->st);
+    STG_CUDA_OK(cudaGetLastError());
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_apply_jacobian(stg_ctx* c, const double* x, double* y) {
+  if (!c) return STG_EINVAL;
+  return stg_apply_level_jacobian(c, (int)c->lv.size() - 1, x, y);
+}
+
+stg_status stg_vcycle(stg_ctx* c, const double* b, double* x) {
+  if (!c || !b || !x) return STG_EINVAL;
+  try {
+    const Geom& g = c->lv.back().g;
+    cabi_to_internal<double>(g, b, c->vin, c->st);
+    run_vcycle(c);
+    internal_to_cabi<double>(g, c->vout, x, c->st);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_smooth(stg_ctx* c, int level, int sweeps, const double* b, double* x) {
+  if (!c || !b || !x || level < 1 || level >= (int)c->lv.size() || sweeps < 0) return STG_EINVAL;
+  try {
+    LevelBufs& L = c->lv[level];
+    if (vc64(c)) {
+      cabi_to_internal<double>(L.g, b, (double*)L.b, c->st);
+      cabi_to_internal<double>(L.g, x, (double*)L.x, c->st);
+      smooth_level<double, double>(c, level, sweeps, false);
+      internal_to_cabi<double>(L.g, (const double*)L.x, x, c->st);
+    } else {
+      cabi_to_internal<float>(L.g, b, (float*)L.b, c->st);
+      cabi_to_internal<float>(L.g, x, (float*)L.x, c->st);
+      if (c->opt.factor_prec == STG_F32)
+        smooth_level<float, float>(c, level, sweeps, false);
+      else
+        smooth_level<float, __nv_bfloat16>(c, level, sweeps, false);
+      internal_to_cabi<float>(L.g, (const float*)L.x, x, c->st);
+    }
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_prolongate(stg_ctx* c, int level, const double* xc, double* xf) {
+  if (!c || !xc || !xf || level < 1 || level >= (int)c->lv.size()) return STG_EINVAL;
+  try {
+    const Geom& gc = c->lv[level - 1].g;
+    const Geom& gf = c->lv[level].g;
+    cabi_to_internal<double>(gc, xc, c->tmp_a, c->st);
+    cabi_to_internal<double>(gf, xf, c->tmp_b, c->st);
+    prolongate_add<double>(gc, gf, c->tmp_a, c->tmp_b, c->st);
+    internal_to_cabi<double>(gf, c->tmp_b, xf, c->st);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_restrict(stg_ctx* c, int level, const double* rf, double* bc) {
+  if (!c || !rf || !bc || level < 1 || level >= (int)c->lv.size()) return STG_EINVAL;
+  try {
+    const Geom& gc = c->lv[level - 1].g;
+    const Geom& gf = c->lv[level].g;
+    cabi_to_internal<double>(gf, rf, c->tmp_a, c->st);
+    restrict_res<double>(gc, gf, c->tmp_a, c->tmp_b, c->st);
+    internal_to_cabi<double>(gc, c->tmp_b, bc, c->st);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_coarse_solve(stg_ctx* c, const double* b, double* x) {
+  if (!c || !b || !x) return STG_EINVAL;
+  try {
+    const Geom& g = c->lv[0].g;
+    cabi_to_internal<double>(g, b, c->cb64, c->st);
+    c->coarse.solve(c->cb64, c->cx64, c->st);
+    internal_to_cabi<double>(g, c->cx64, x, c->st);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_gmres_solve(stg_ctx* c, const double* b, double* x, int* iters, double* rel_res) {
+  if (!c || !b || !x) return STG_EINVAL;
+  try {
+    const Geom& g = c->lv.back().g;
+    cabi_to_internal<double>(g, b, c->tmp_a, c->st);
+    cabi_to_internal<double>(g, x, c->tmp_b, c->st);
+    const stg_status s = fgmres(c, c->tmp_a, c->tmp_b, iters, rel_res);
+    internal_to_cabi<double>(g, c->tmp_b, x, c->st);
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    if (s == STG_ENOCONV) c->err = "FGMRES reached gmres_maxit";
+    return s;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_get_sizes(const stg_ctx* c, int level, long long* n_dofs, long long* n_cells, int* n_patch) {
+  if (!c || level < 0 || level >= (int)c->lv.size()) return STG_EINVAL;
+  const Geom& g = c->lv[level].g;
+  if (n_dofs) *n_dofs = g.N;
+  if (n_cells) *n_cells = g.n_cells;
+  if (n_patch) *n_patch = g.npatch;
+  return STG_OK;
+}
+
+stg_status stg_get_local_inverse(const stg_ctx* cc, int level, long long cell, double* out) {
+  stg_ctx* c = const_cast<stg_ctx*>(cc);
+  if (!c || !out || level < 1 || level >= (int)c->lv.size()) return STG_EINVAL;
+  const Geom& g = c->lv[level].g;
+  if (cell < 0 || cell >= g.n_cells) return STG_EINVAL;
+  try {
+    const int n = g.npatch;
+    const int cx = (int)(cell % g.n[0]), cy = (int)((cell / g.n[0]) % g.n[1]);
+    const int cz = (int)(cell / ((long long)g.n[0] * g.n[1]));
+    const long long p = patch_of_cell(g, cx, cy, cz);
+    const size_t fs = fsize(c->opt.factor_prec);
+    std::vector<unsigned char> raw((size_t)n * n * fs);
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    STG_CUDA_OK(cudaMemcpy(raw.data(), (const char*)c->lv[level].jinv + (size_t)p * patch_stride(n) * fs,
+                           raw.size(), cudaMemcpyDeviceToHost));
+    auto val = [&](int col, int row) -> double {
+      const size_t i = (size_t)col * n + row;
+      if (c->opt.factor_prec == STG_F64) return ((const double*)raw.data())[i];
+      if (c->opt.factor_prec == STG_F32) return ((const float*)raw.data())[i];
+      unsigned int bits = (unsigned int)((const unsigned short*)raw.data())[i] << 16;
+      float f;
+      std::memcpy(&f, &bits, 4);
+      return f;
+    };
+    // paper order: a-major; nodes x comps; then pressure coefficients
+    const int d = g.dim, blk = g.nloc * d + d + 1;
+    auto gpu_index = [&](int mu) {
+      const int a = mu / blk, r = mu % blk;
+      if (r < g.nloc * d) {
+        const int i = r / d, comp = r % d;
+        return i * g.NV + a * d + comp;
+      }
+      return g.nloc * g.NV + a * (d + 1) + (r - g.nloc * d);
+    };
+    for (int r = 0; r < n; ++r)
+      for (int col = 0; col < n; ++col) out[(size_t)r * n + col] = val(gpu_index(col), gpu_index(r));
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+const char* stg_last_error(const stg_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
+
+void stg_destroy(stg_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->coarse.release();
+  for (void* p : c->owned) cudaFree(p);
+  if (c->hh) cudaFreeHost(c->hh);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// Jacobian assembly on one structured level (Sec. 3, Eq. (3.3) with D_ab and B_ab).
+//
+// For the linearisation velocity w_a at Radau node a, the space-time block of
+// test (a, i, c) and trial (b, j, e) is
+//   T_ab M_ij delta_ce + delta_ab tau w_a [ (w_a . grad phi_j, phi_i) delta_ce
+//       + (Newton) phi_i phi_j d_e w_a,c + nu (grad phi_j, grad phi_i) delta_ce
+//       + Nitsche terms of A_h and B_GammaD (Eq. (2.1)) on Dirichlet faces ],
+// the velocity-pressure blocks delta_ab tau w_a [ -(xi_m, d_c phi_i) + <xi_m, phi_i n_c> ],
+// the pressure-velocity blocks delta_ab tau w_a [ (xi_m, d_e phi_j) - <phi_j n_e, xi_m> ].
+// T_ab is the time-derivative plus jump matrix of the Radau-Lagrange basis.
+// One CTA per cell; cells of one colour share no Q2 node, so a colour's cells
+// add into disjoint BCSR blocks and the launches need no atomics.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace stg {
+
+// 1D Q2 Lagrange values / derivatives at five points: the three Gauss points and xi = -1, +1.
+__constant__ double c_L1[5][3];
+__constant__ double c_D1[5][3];
+__constant__ double c_X[5];
+__constant__ double c_GW[3];
+
+void upload_fe_tables() {
+  const double g = std::sqrt(0.6);
+  const double X[5] = {-g, 0.0, g, -1.0, 1.0};
+  double L1[5][3], D1[5][3];
+  for (int p = 0; p < 5; ++p) {
+    const double x = X[p];
+    L1[p][0] = x * (x - 1.0) / 2.0;
+    L1[p][1] = 1.0 - x * x;
+    L1[p][2] = x * (x + 1.0) / 2.0;
+    D1[p][0] = x - 0.5;
+    D1[p][1] = -2.0 * x;
+    D1[p][2] = x + 0.5;
+  }
+  const double GW[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_L1, L1, sizeof(L1)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_D1, D1, sizeof(D1)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_X, X, sizeof(X)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_GW, GW, sizeof(GW)));
+}
+
+namespace {
+
+template <int DIM>
+struct Pow3 { static constexpr int v = DIM == 2 ? 9 : 27; };
+
+// Value and physical gradient of local Q2 function i at point multi-index p.
+template <int DIM>
+__device__ __forceinline__ void basis_at(const Geom& g, const int* p, int i, double& v, double* grad) {
+  int l[3] = {i % 3, (i / 3) % 3, i / 9};
+  v = 1.0;
+  for (int e = 0; e < DIM; ++e) v *= c_L1[p[e]][l[e]];
+  for (int e = 0; e < DIM; ++e) {
+    double d = 2.0 / g.h[e] * c_D1[p[e]][l[e]];
+    for (int f = 0; f < DIM; ++f)
+      if (f != e) d *= c_L1[p[f]][l[f]];
+    grad[e] = d;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
+                                                      const double* __restrict__ w,
+                                                      const int* __restrict__ rowptr, double* __restrict__ vv,
+                                                      double* __restrict__ vp, double* __restrict__ pv) {
+  constexpr int NQ = Pow3<DIM>::v;
+  constexpr int NL = NQ;
+  __shared__ double phi[NQ][NL];
+  __shared__ double dphi[NQ][NL][DIM];
+  __shared__ double qwd[NQ];
+  __shared__ double wq[5][NQ][DIM];
+  __shared__ double gw[5][NQ][DIM][DIM];
+
+  const int nt = g.nt, NV = g.NV, NP = g.NP;
+  int cx, cy, cz;
+  patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
+  const int cc[3] = {cx, cy, cz};
+  const long long cell = cell_id(g, cx, cy, cz);
+
+  for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x) {
+    const int q = t / NL, i = t % NL;
+    int p[3] = {q % 3, (q / 3) % 3, q / 9};
+    double v, gr[3];
+    basis_at<DIM>(g, p, i, v, gr);
+    phi[q][i] = v;
+    for (int e = 0; e < DIM; ++e) dphi[q][i][e] = gr[e];
+    if (i == 0) {
+      double wt = 1.0;
+      for (int e = 0; e < DIM; ++e) wt *= c_GW[p[e]] * g.h[e] / 2.0;
+      qwd[q] = wt;
+    }
+  }
+  __syncthreads();
+  // w_a and grad w_a at the quadrature points
+  for (int t = threadIdx.x; t < nt * NQ * DIM; t += blockDim.x) {
+    const int a = t / (NQ * DIM), q = (t / DIM) % NQ, c = t % DIM;
+    double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < NL; ++i) {
+      const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
+      const double wi = w[nd * NV + a * DIM + c];
+      v += phi[q][i] * wi;
+      for (int e = 0; e < DIM; ++e) gr[e] += dphi[q][i][e] * wi;
+    }
+    wq[a][q][c] = v;
+    for (int e = 0; e < DIM; ++e) gw[a][q][c][e] = gr[e];
+  }
+  __syncthreads();
+
+  // Dirichlet faces of this cell (bit f = 2*dir + side)
+  unsigned faces = 0;
+  for (int e = 0; e < DIM; ++e) {
+    if (cc[e] == 0 && (g.dirichlet >> (2 * e) & 1u)) faces |= 1u << (2 * e);
+    if (cc[e] == g.n[e] - 1 && (g.dirichlet >> (2 * e + 1) & 1u)) faces |= 1u << (2 * e + 1);
+  }
+
+  // ---- velocity-velocity blocks
+  const long long nvv = (long long)NL * NL * NV * NV;
+  for (long long t = threadIdx.x; t < nvv; t += blockDim.x) {
+    const int s = (int)(t % NV), r = (int)((t / NV) % NV);
+    const int j = (int)((t / (NV * NV)) % NL), i = (int)(t / ((long long)NV * NV * NL));
+    const int a = r / DIM, c = r % DIM, b = s / DIM, e = s % DIM;
+    double val = 0.0;
+    if (c == e) {
+      double m = 0.0;
+      for (int q = 0; q < NQ; ++q) m += qwd[q] * phi[q][i] * phi[q][j];
+      val += td.T[a][b] * m;
+    }
+    if (a == b) {
+      double sp = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        double term = 0.0;
+        if (c == e) {
+          double conv = 0.0, visc = 0.0;
+          for (int f = 0; f < DIM; ++f) {
+            conv += wq[a][q][f] * dphi[q][j][f];
+            visc += dphi[q][j][f] * dphi[q][i][f];
+          }
+          term += conv * phi[q][i] + cf.nu * visc;
+        }
+        if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
+        sp += qwd[q] * term;
+      }
+      if (faces) {
+        for (int f = 0; f < 2 * DIM; ++f) {
+          if (!(faces >> f & 1u)) continue;
+          const int e0 = f >> 1, s0 = f & 1;
+          const double ns = s0 ? 1.0 : -1.0, hf = g.h[e0];
+          double fdet = 1.0;
+          for (int d = 0; d < DIM; ++d)
+            if (d != e0) fdet *= g.h[d] / 2.0;
+          double acc = 0.0;
+          for (int fq = 0; fq < NQ / 3; ++fq) {
+            int p[3], o = 0, rem = fq;
+            double wt = fdet;
+            for (int d = 0; d < DIM; ++d) {
+              if (d == e0) {
+                p[d] = 3 + s0;
+              } else {
+                p[d] = (o == 0) ? rem % 3 : rem / 3;
+                wt *= c_GW[p[d]];
+                ++o;
+              }
+            }
+            double vi, vj, gi[3], gj[3];
+            basis_at<DIM>(g, p, i, vi, gi);
+            basis_at<DIM>(g, p, j, vj, gj);
+            const double dni = ns * gi[e0], dnj = ns * gj[e0];
+            double term = 0.0;
+            if (c == e) term += -cf.nu * dnj * vi - cf.nu * vj * dni + cf.gamma1 * cf.nu / hf * vj * vi;
+            if (c == e0 && e == e0) term += cf.gamma2 / hf * vj * vi;
+            acc += wt * term;
+          }
+          sp += acc;
+        }
+      }
+      val += cf.tau * td.w[a] * sp;
+    }
+    const int li[3] = {i % 3, (i / 3) % 3, i / 9}, lj[3] = {j % 3, (j / 3) % 3, j / 9};
+    const long long slot = bcsr_slot(g, rowptr, 2 * cx + li[0], 2 * cy + li[1], 2 * cz + li[2], 2 * cx + lj[0],
+                                      2 * cy + lj[1], 2 * cz + lj[2]);
+    vv[slot * NV * NV + (long long)r * NV + s] += val;
+  }
+
+  // ---- velocity-pressure [cell][i][a][c][m] and pressure-velocity [cell][a][m][i][c]
+  const int nvp = NL * nt * DIM * (DIM + 1);
+  for (int t = threadIdx.x; t < nvp; t += blockDim.x) {
+    const int m = t % (DIM + 1), c = (t / (DIM + 1)) % DIM, a = (t / ((DIM + 1) * DIM)) % nt;
+    const int i = t / ((DIM + 1) * DIM * nt);
+    double vol = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      const double xi = m == 0 ? 1.0 : c_X[(m == 1) ? q % 3 : (m == 2 ? (q / 3) % 3 : q / 9)];
+      vol += qwd[q] * xi * dphi[q][i][c];
+    }
+    double bnd = 0.0;
+    for (int f = 0; f < 2 * DIM; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      if (c != e0) continue;
+      const double ns = s0 ? 1.0 : -1.0;
+      double fdet = 1.0;
+      for (int d = 0; d < DIM; ++d)
+        if (d != e0) fdet *= g.h[d] / 2.0;
+      for (int fq = 0; fq < NQ / 3; ++fq) {
+        int p[3], o = 0, rem = fq;
+        double wt = fdet;
+        for (int d = 0; d < DIM; ++d) {
+          if (d == e0) {
+            p[d] = 3 + s0;
+          } else {
+            p[d] = (o == 0) ? rem % 3 : rem / 3;
+            wt *= c_GW[p[d]];
+            ++o;
+          }
+        }
+        double vi, gi[3];
+        basis_at<DIM>(g, p, i, vi, gi);
+        const double xi = m == 0 ? 1.0 : c_X[p[m - 1]];
+        bnd += wt * xi * vi * ns;
+      }
+    }
+    const double s = cf.tau * td.w[a];
+    vp[(((cell * NL + i) * nt + a) * DIM + c) * (DIM + 1) + m] = s * (-vol + bnd);
+    pv[((cell * nt + a) * (DIM + 1) + m) * (long long)NL * DIM + i * DIM + c] = s * (vol - bnd);
+  }
+  (void)NP;
+}
+
+}  // namespace
+
+void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
+                    double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st) {
+  STG_CUDA_OK(cudaMemsetAsync(vv, 0, sizeof(double) * nnzb * g.NV * g.NV, st));
+  for (int col = 0; col < (1 << g.dim); ++col) {
+    const long long cnt = g.coff[col + 1] - g.coff[col];
+    if (cnt == 0) continue;
+    if (g.dim == 2)
+      assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, vv, vp, pv);
+    else
+      assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, vv, vp, pv);
+    STG_LAUNCH_OK();
+  }
+}
+
+}  // namespace stg

@@ -1,0 +1,50 @@
+// Coarse-level direct solver: interior elimination per cell column plus block
+// cyclic reduction over the vertex planes (FP64).  See coarse.cu.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace stg {
+
+struct CoarseView {
+  Geom g;
+  int pin, nsi, nsv, mV, mI;
+  double *AII, *AIV, *AVI, *D, *L, *U;
+  int* status;  // [0]: 1 + first singular block, [1]: unexpected coupling
+};
+
+struct CrLevel {
+  long long stride;
+  int n_odd, n_left, n_right, n_bright;
+  double **oD, **oL, **oU, **oGL, **oGU, **ob, **ot;
+  double **lD, **lL, **lGU, **lGL, **lT, **lb, **lt, **sL;
+  double **rD, **rU, **rGL, **rGU, **rT, **rb, **rt, **sU;
+  double **bx, **bt, **bGL, **bxl, **bGU, **bxr, **bx2;
+};
+
+struct CoarseSolver {
+  CoarseView v{};
+  double *W = nullptr, *C = nullptr, *GL = nullptr, *GU = nullptr, *TL = nullptr;
+  double *bV = nullptr, *tV = nullptr, *xV = nullptr, *bI = nullptr, *gI = nullptr, *cI = nullptr, *xI = nullptr;
+  double **d_AII = nullptr, **d_AIV = nullptr, **d_AVI = nullptr, **d_W = nullptr, **d_C = nullptr;
+  double **d_bI = nullptr, **d_gI = nullptr, **d_cI = nullptr, **d_xVs = nullptr, **d_xI = nullptr;
+  double **d_top = nullptr, **d_topb = nullptr, **d_topx = nullptr;
+  std::vector<CrLevel> levels;
+  std::vector<void*> owned;
+
+  void init(const Geom& g, bool pure_dirichlet);
+  void release();
+  // factor J_0 given in the internal level layout (FP64)
+  void factor(const int* rowptr, const int* colidx, const double* vv, const double* vp, const double* pv,
+              cudaStream_t st);
+  // x = J_0^{-1} b, both in the internal level layout (FP64)
+  void solve(const double* b, double* x, cudaStream_t st);
+  // 0 = ok, > 0: 1 + singular block, -1: coupling outside the block structure (synchronises)
+  int read_status(cudaStream_t st);
+};
+
+void copy_ptrs(double* const* src, double* const* dst, int batch, long long n, cudaStream_t st);
+
+}  // namespace stg

@@ -1,0 +1,139 @@
+// Internal definitions shared by the sm_103a kernels of the space-time Vanka
+// multigrid solver (geometry of one structured level, data layout, helpers).
+//
+// Internal data layout of one level (differs from the C-ABI order of X_n,
+// Eq. (3.2); the entry points permute at the boundary):
+//   vector  = [velocity | pressure]
+//   velocity: node-major, NV = (k+1)*dim values per Q2 node, index a*dim + c
+//   pressure: cell-major, NP = (k+1)*(dim+1) values per cell, index a*(dim+1) + m
+//   Jvv     : block-CSR over Q2 nodes, dense NV x NV blocks (row (a,c), col (b,e)),
+//             the columns of a row ordered (z, y, x) lexicographically over the
+//             tensor-product stencil of the node
+//   Jvp     : per cell and local node: [cell][i][a][c][m]   (time-diagonal)
+//   Jpv     : per cell: [cell][a][m][i][c]                  (time-diagonal)
+//   patch   : local order [3^d nodes x NV | NP]; npatch = (k+1)(3^d d + d + 1)
+//   J_K^{-1}: one column-major npatch x npatch matrix per cell, cells ordered by
+//             colour (colour = sum_e (c_e & 1) 2^e) and lexicographically inside
+//             a colour
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "stg.h"
+
+namespace stg {
+
+struct Geom {
+  int dim, k, nt;
+  int n[3];             // cells per direction (1 beyond dim)
+  int nn[3];            // Q2 nodes per direction (1 beyond dim)
+  double lo[3], h[3];
+  unsigned dirichlet;   // bit 2*dir+side
+  int NV, NP, nloc, npatch;
+  long long n_nodes, n_cells, nvel, npres, N;
+  // cells of each colour: count per direction and offset of the colour's first patch
+  int ccount[8][3];
+  long long coff[9];
+};
+
+Geom make_geom(const stg_mesh& m, int level, int k);
+
+// ------------------------------------------------------------------ conversions
+template <typename D, typename S>
+__device__ __forceinline__ D cvt(S x) { return static_cast<D>(x); }
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, float>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16, double>(double x) { return __double2bfloat16(x); }
+
+// ------------------------------------------------------------------ index helpers
+__host__ __device__ __forceinline__ long long node_id(const Geom& g, int ix, int iy, int iz) {
+  return ix + (long long)g.nn[0] * (iy + (long long)g.nn[1] * iz);
+}
+__host__ __device__ __forceinline__ long long cell_id(const Geom& g, int cx, int cy, int cz) {
+  return cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz);
+}
+// Range of Q2 node indices coupled to node index i along one direction:
+// a vertex line (even i) touches two cells, an interior line (odd i) one.
+__host__ __device__ __forceinline__ void stencil_range(int i, int nn, int& lo, int& hi) {
+  const int r = (i & 1) ? 1 : 2;
+  lo = i - r < 0 ? 0 : i - r;
+  hi = i + r > nn - 1 ? nn - 1 : i + r;
+}
+// Position of column node (jx,jy,jz) in the BCSR row of node (ix,iy,iz).
+__host__ __device__ __forceinline__ long long bcsr_slot(const Geom& g, const int* rowptr, int ix, int iy,
+                                                        int iz, int jx, int jy, int jz) {
+  int xl, xh, yl, yh, zl, zh;
+  stencil_range(ix, g.nn[0], xl, xh);
+  stencil_range(iy, g.nn[1], yl, yh);
+  stencil_range(iz, g.nn[2], zl, zh);
+  const int wx = xh - xl + 1, wy = yh - yl + 1;
+  return (long long)rowptr[node_id(g, ix, iy, iz)] + ((long long)(jz - zl) * wy + (jy - yl)) * wx + (jx - xl);
+}
+// Cell of patch index p (patches ordered by colour, then lexicographically).
+__host__ __device__ __forceinline__ void patch_cell(const Geom& g, long long p, int& cx, int& cy, int& cz) {
+  int col = 0;
+  while (col < (1 << g.dim) - 1 && p >= g.coff[col + 1]) ++col;
+  long long li = p - g.coff[col];
+  const int* c = g.ccount[col];
+  const int jx = (int)(li % c[0]);
+  li /= c[0];
+  const int jy = (int)(li % c[1]);
+  const int jz = (int)(li / c[1]);
+  cx = 2 * jx + (col & 1);
+  cy = g.dim > 1 ? 2 * jy + ((col >> 1) & 1) : 0;
+  cz = g.dim > 2 ? 2 * jz + ((col >> 2) & 1) : 0;
+}
+__host__ __device__ __forceinline__ long long patch_of_cell(const Geom& g, int cx, int cy, int cz) {
+  const int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+  const int* c = g.ccount[col];
+  return g.coff[col] + (cx >> 1) + (long long)c[0] * ((cy >> 1) + (long long)c[1] * (cz >> 1));
+}
+// Global internal index of local patch entry mu of cell (cx,cy,cz).
+__host__ __device__ __forceinline__ long long patch_dof(const Geom& g, int cx, int cy, int cz, int mu) {
+  const int vel = g.nloc * g.NV;
+  if (mu < vel) {
+    const int i = mu / g.NV, v = mu - i * g.NV;
+    const int lx = i % 3, ly = (i / 3) % 3, lz = i / 9;
+    return node_id(g, 2 * cx + lx, 2 * cy + ly, 2 * cz + lz) * g.NV + v;
+  }
+  return g.nvel + cell_id(g, cx, cy, cz) * g.NP + (mu - vel);
+}
+// Number of cells sharing Q2 node (ix,iy,iz): the static multiplicity p of (S2).
+__host__ __device__ __forceinline__ int node_multiplicity(const Geom& g, int ix, int iy, int iz) {
+  int m = 1;
+  if (!(ix & 1) && ix > 0 && ix < g.nn[0] - 1) m *= 2;
+  if (g.dim > 1 && !(iy & 1) && iy > 0 && iy < g.nn[1] - 1) m *= 2;
+  if (g.dim > 2 && !(iz & 1) && iz > 0 && iz < g.nn[2] - 1) m *= 2;
+  return m;
+}
+
+inline long long patch_stride(int npatch) { return ((long long)npatch * npatch + 31) / 32 * 32; }
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  stg_status st;
+  std::string msg;
+};
+
+#define STG_CUDA_OK(call)                                                                      \
+  do {                                                                                         \
+    cudaError_t e__ = (call);                                                                  \
+    if (e__ != cudaSuccess)                                                                    \
+      throw ::stg::Error{STG_ECUDA, std::string(#call) + " at " + __FILE__ + ":" +               \
+                                        std::to_string(__LINE__) + ": " + cudaGetErrorString(e__)}; \
+  } while (0)
+
+#define STG_LAUNCH_OK() STG_CUDA_OK(cudaGetLastError())
+
+inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace stg

@@ -1,0 +1,84 @@
+// Host-side launchers of the solver kernels (one declaration per kernel family).
+#pragma once
+
+#include "common.cuh"
+
+namespace stg {
+
+// Radau-Lagrange time basis on [0,1] (Sec. 3): nodes c_a, weights w_a,
+// T_ab = int chi_b' chi_a + chi_a(0) chi_b(0), jump vector chi_a(0).
+struct TimeData {
+  double T[5][5];
+  double w[5];
+  double c[5];
+  double jump[5];
+};
+TimeData time_basis(int k);
+
+struct AsmCoef {
+  double nu, tau, gamma1, gamma2;
+  int newton;
+};
+
+// ---- assembly (assemble.cu)
+void upload_fe_tables();
+void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
+                    double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
+
+// ---- operators, smoother and transfers (vanka.cu, transfer.cu)
+// out = b - J x (has_b) or out = J x; MT = operator precision, VT = vector precision
+template <typename MT, typename VT>
+void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const MT* vv, const MT* vp, const MT* pv,
+                    const VT* x, const VT* b, VT* out, cudaStream_t st);
+
+// Local inverses J_K^{-1} of every cell (gather from the assembled J, Gauss-Jordan
+// with partial pivoting in CT precision, stored as FT). status[0] receives the
+// first singular cell + 1 (0 = none).
+size_t invert_scratch_bytes(const Geom& g, int compute_f32);
+template <typename FT>
+void invert_patches(const Geom& g, const int* rowptr, const double* vv, const double* vp, const double* pv,
+                    FT* jinv, int compute_f32, int* status, void* scratch, cudaStream_t st);
+
+// One colour phase of the smoother: y_K = J_K^{-1} R_K r for all cells of colour
+// `colour`; accumulate (averaged mode: z += y) or apply (coloured mode: z += omega y).
+template <typename VT, typename FT>
+void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st);
+
+// d += omega z / p (p = static multiplicity of (S2)); z = 0.
+template <typename VT>
+void vanka_update(const Geom& g, VT* d, VT* z, double omega, cudaStream_t st);
+
+template <typename VT>
+void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaStream_t st);
+template <typename VT>
+void restrict_res(const Geom& gc, const Geom& gf, const VT* rf, VT* bc, cudaStream_t st);
+
+// C-ABI order <-> internal layout
+template <typename VT>
+void cabi_to_internal(const Geom& g, const double* in, VT* out, cudaStream_t st);
+template <typename VT>
+void internal_to_cabi(const Geom& g, const VT* in, double* out, cudaStream_t st);
+// velocity-only (k+1) x R C-ABI block -> internal node-major velocity
+void w_to_internal(const Geom& g, const double* in, double* out, cudaStream_t st);
+// coarse velocity at node 2g of the fine level (injection)
+void inject_w(const Geom& gc, const Geom& gf, const double* wf, double* wc, cudaStream_t st);
+
+template <typename D, typename S>
+void convert(long long n, const S* in, D* out, cudaStream_t st);
+
+// ---- BLAS-1 in FP64 (krylov.cu)
+// h[i] = <V_i, w>, i < m, V row-major (m x n, leading dim ldv); partial sums per block -> h.
+void multi_dot(long long n, int m, const double* V, long long ldv, const double* w, double* partial, double* h,
+               cudaStream_t st);
+// w -= sum_i h[i] V_i (h on the device)
+void multi_axpy_sub(long long n, int m, const double* V, long long ldv, const double* h, double* w,
+                    cudaStream_t st);
+// x += sum_i y[i] Z_i
+void multi_axpy_add(long long n, int m, const double* Z, long long ldz, const double* y, double* x,
+                    cudaStream_t st);
+// y = a x + b y
+void axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st);
+
+size_t dot_partial_doubles();
+
+}  // namespace stg

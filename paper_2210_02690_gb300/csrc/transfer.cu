@@ -1,0 +1,260 @@
+// Grid transfer between nested levels and layout permutations.
+//
+// The V-cycle of Sec. 3 works on nested meshes (Sec. 2, h_l = h_{l-1}/2); the
+// transfers are those of the nested spaces: prolongation P maps a coarse
+// (Q2)^d x P1disc function to its coefficients on the fine mesh, restriction
+// is P^T.  Along one direction a fine Q2 node at coarse reference coordinate
+// -1/2 (+1/2) takes the coarse cell's nodal values with weights (3/8, 3/4,
+// -1/8) ((-1/8, 3/4, 3/8)); nodes on coarse nodes take weight 1.  A child
+// cell with offset s in {-1/2, +1/2}^d gets c0 + sum_e s_e c_e and c_e / 2.
+// Time nodes are not coarsened.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace stg {
+namespace {
+
+// Coarse node indices and weights feeding fine node index f along one direction.
+__device__ __forceinline__ int prolong_1d(int f, int* idx, double* w) {
+  if (!(f & 1)) {
+    idx[0] = f >> 1;
+    w[0] = 1.0;
+    return 1;
+  }
+  const int cc = f >> 2;
+  idx[0] = 2 * cc;
+  idx[1] = 2 * cc + 1;
+  idx[2] = 2 * cc + 2;
+  if ((f & 3) == 1) {
+    w[0] = 0.375;
+    w[1] = 0.75;
+    w[2] = -0.125;
+  } else {
+    w[0] = -0.125;
+    w[1] = 0.75;
+    w[2] = 0.375;
+  }
+  return 3;
+}
+
+// Fine node indices and weights of row c of P^T along one direction (nnf fine nodes).
+__device__ __forceinline__ int restrict_1d(int c, int nnf, int* idx, double* w) {
+  int n = 0;
+  auto add = [&](int f, double wt) {
+    if (f >= 0 && f < nnf) {
+      idx[n] = f;
+      w[n] = wt;
+      ++n;
+    }
+  };
+  add(2 * c, 1.0);
+  if (c & 1) {
+    add(2 * c - 1, 0.75);
+    add(2 * c + 1, 0.75);
+  } else {
+    add(2 * c - 1, 0.375);
+    add(2 * c + 1, 0.375);
+    add(2 * c - 3, -0.125);
+    add(2 * c + 3, -0.125);
+  }
+  return n;
+}
+
+template <typename VT>
+__global__ void prolong_vel(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gf.nvel) return;
+  const int NV = gf.NV;
+  const long long node = t / NV;
+  const int v = (int)(t - node * NV);
+  const int f[3] = {(int)(node % gf.nn[0]), (int)((node / gf.nn[0]) % gf.nn[1]),
+                    (int)(node / ((long long)gf.nn[0] * gf.nn[1]))};
+  int ix[3][3], n[3];
+  double w[3][3];
+  for (int e = 0; e < 3; ++e) n[e] = prolong_1d(f[e], ix[e], w[e]);
+  double acc = 0.0;
+  for (int c = 0; c < n[2]; ++c)
+    for (int b = 0; b < n[1]; ++b)
+      for (int a = 0; a < n[0]; ++a)
+        acc += w[0][a] * w[1][b] * w[2][c] * (double)xc[node_id(gc, ix[0][a], ix[1][b], ix[2][c]) * NV + v];
+  xf[t] += (VT)acc;
+}
+
+template <typename VT>
+__global__ void prolong_pres(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gf.npres) return;
+  const int d = gf.dim;
+  const long long K = t / gf.NP;
+  const int q = (int)(t - K * gf.NP);
+  const int a = q / (d + 1), m = q % (d + 1);
+  const int f[3] = {(int)(K % gf.n[0]), (int)((K / gf.n[0]) % gf.n[1]), (int)(K / ((long long)gf.n[0] * gf.n[1]))};
+  const long long Kc = cell_id(gc, f[0] >> 1, f[1] >> 1, f[2] >> 1);
+  const VT* c = xc + gc.nvel + Kc * gc.NP + a * (d + 1);
+  double val;
+  if (m == 0) {
+    val = (double)c[0];
+    for (int e = 0; e < d; ++e) val += ((f[e] & 1) ? 0.5 : -0.5) * (double)c[e + 1];
+  } else {
+    val = 0.5 * (double)c[m];
+  }
+  xf[gf.nvel + t] += (VT)val;
+}
+
+template <typename VT>
+__global__ void restrict_vel(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.nvel) return;
+  const int NV = gc.NV;
+  const long long node = t / NV;
+  const int v = (int)(t - node * NV);
+  const int c[3] = {(int)(node % gc.nn[0]), (int)((node / gc.nn[0]) % gc.nn[1]),
+                    (int)(node / ((long long)gc.nn[0] * gc.nn[1]))};
+  int ix[3][5], n[3];
+  double w[3][5];
+  for (int e = 0; e < 3; ++e) n[e] = restrict_1d(c[e], gf.nn[e], ix[e], w[e]);
+  double acc = 0.0;
+  for (int z = 0; z < n[2]; ++z)
+    for (int y = 0; y < n[1]; ++y)
+      for (int x = 0; x < n[0]; ++x)
+        acc += w[0][x] * w[1][y] * w[2][z] * (double)rf[node_id(gf, ix[0][x], ix[1][y], ix[2][z]) * NV + v];
+  bc[t] = (VT)acc;
+}
+
+template <typename VT>
+__global__ void restrict_pres(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.npres) return;
+  const int d = gc.dim;
+  const long long K = t / gc.NP;
+  const int q = (int)(t - K * gc.NP);
+  const int a = q / (d + 1), m = q % (d + 1);
+  const int c[3] = {(int)(K % gc.n[0]), (int)((K / gc.n[0]) % gc.n[1]), (int)(K / ((long long)gc.n[0] * gc.n[1]))};
+  double acc = 0.0;
+  const int nch = 1 << d;
+  for (int o = 0; o < nch; ++o) {
+    const int fx = 2 * c[0] + (o & 1), fy = d > 1 ? 2 * c[1] + ((o >> 1) & 1) : 0;
+    const int fz = d > 2 ? 2 * c[2] + ((o >> 2) & 1) : 0;
+    const VT* f = rf + gf.nvel + cell_id(gf, fx, fy, fz) * gf.NP + a * (d + 1);
+    if (m == 0) {
+      acc += (double)f[0];
+    } else {
+      const double s = ((o >> (m - 1)) & 1) ? 0.5 : -0.5;
+      acc += s * (double)f[0] + 0.5 * (double)f[m];
+    }
+  }
+  bc[gc.nvel + t] = (VT)acc;
+}
+
+__device__ __forceinline__ long long cabi_index(const Geom& g, long long t) {
+  const long long R = (long long)g.dim * g.n_nodes, S = (long long)(g.dim + 1) * g.n_cells;
+  if (t < g.nvel) {
+    const long long node = t / g.NV;
+    const int v = (int)(t - node * g.NV);
+    const int a = v / g.dim, c = v % g.dim;
+    return a * (R + S) + node * g.dim + c;
+  }
+  const long long u = t - g.nvel;
+  const long long cell = u / g.NP;
+  const int q = (int)(u - cell * g.NP);
+  const int a = q / (g.dim + 1), m = q % (g.dim + 1);
+  return a * (R + S) + R + cell * (g.dim + 1) + m;
+}
+
+template <typename VT>
+__global__ void to_internal_kernel(Geom g, const double* __restrict__ in, VT* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N) return;
+  out[t] = (VT)in[cabi_index(g, t)];
+}
+
+template <typename VT>
+__global__ void to_cabi_kernel(Geom g, const VT* __restrict__ in, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N) return;
+  out[cabi_index(g, t)] = (double)in[t];
+}
+
+__global__ void w_to_internal_kernel(Geom g, const double* __restrict__ in, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nvel) return;
+  const long long node = t / g.NV;
+  const int v = (int)(t - node * g.NV);
+  const int a = v / g.dim, c = v % g.dim;
+  out[t] = in[a * (long long)g.dim * g.n_nodes + node * g.dim + c];
+}
+
+__global__ void inject_w_kernel(Geom gc, Geom gf, const double* __restrict__ wf, double* __restrict__ wc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.nvel) return;
+  const long long node = t / gc.NV;
+  const int v = (int)(t - node * gc.NV);
+  const int c[3] = {(int)(node % gc.nn[0]), (int)((node / gc.nn[0]) % gc.nn[1]),
+                    (int)(node / ((long long)gc.nn[0] * gc.nn[1]))};
+  wc[t] = wf[node_id(gf, 2 * c[0], 2 * c[1], 2 * c[2]) * gf.NV + v];
+}
+
+template <typename D, typename S>
+__global__ void convert_kernel(long long n, const S* __restrict__ in, D* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = cvt<D>(in[t]);
+}
+
+}  // namespace
+
+template <typename VT>
+void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaStream_t st) {
+  prolong_vel<VT><<<grid_for(gf.nvel, 256), 256, 0, st>>>(gc, gf, xc, xf);
+  prolong_pres<VT><<<grid_for(gf.npres, 256), 256, 0, st>>>(gc, gf, xc, xf);
+  STG_LAUNCH_OK();
+}
+
+template <typename VT>
+void restrict_res(const Geom& gc, const Geom& gf, const VT* rf, VT* bc, cudaStream_t st) {
+  restrict_vel<VT><<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, rf, bc);
+  restrict_pres<VT><<<grid_for(gc.npres, 256), 256, 0, st>>>(gc, gf, rf, bc);
+  STG_LAUNCH_OK();
+}
+
+template <typename VT>
+void cabi_to_internal(const Geom& g, const double* in, VT* out, cudaStream_t st) {
+  to_internal_kernel<VT><<<grid_for(g.N, 256), 256, 0, st>>>(g, in, out);
+  STG_LAUNCH_OK();
+}
+
+template <typename VT>
+void internal_to_cabi(const Geom& g, const VT* in, double* out, cudaStream_t st) {
+  to_cabi_kernel<VT><<<grid_for(g.N, 256), 256, 0, st>>>(g, in, out);
+  STG_LAUNCH_OK();
+}
+
+void w_to_internal(const Geom& g, const double* in, double* out, cudaStream_t st) {
+  w_to_internal_kernel<<<grid_for(g.nvel, 256), 256, 0, st>>>(g, in, out);
+  STG_LAUNCH_OK();
+}
+
+void inject_w(const Geom& gc, const Geom& gf, const double* wf, double* wc, cudaStream_t st) {
+  inject_w_kernel<<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, wf, wc);
+  STG_LAUNCH_OK();
+}
+
+template <typename D, typename S>
+void convert(long long n, const S* in, D* out, cudaStream_t st) {
+  if (n <= 0) return;
+  convert_kernel<D, S><<<grid_for(n, 256), 256, 0, st>>>(n, in, out);
+  STG_LAUNCH_OK();
+}
+
+template void prolongate_add<double>(const Geom&, const Geom&, const double*, double*, cudaStream_t);
+template void prolongate_add<float>(const Geom&, const Geom&, const float*, float*, cudaStream_t);
+template void restrict_res<double>(const Geom&, const Geom&, const double*, double*, cudaStream_t);
+template void restrict_res<float>(const Geom&, const Geom&, const float*, float*, cudaStream_t);
+template void cabi_to_internal<double>(const Geom&, const double*, double*, cudaStream_t);
+template void cabi_to_internal<float>(const Geom&, const double*, float*, cudaStream_t);
+template void internal_to_cabi<double>(const Geom&, const double*, double*, cudaStream_t);
+template void internal_to_cabi<float>(const Geom&, const float*, double*, cudaStream_t);
+template void convert<float, double>(long long, const double*, float*, cudaStream_t);
+template void convert<double, float>(long long, const float*, double*, cudaStream_t);
+template void convert<__nv_bfloat16, double>(long long, const double*, __nv_bfloat16*, cudaStream_t);
+
+}  // namespace stg

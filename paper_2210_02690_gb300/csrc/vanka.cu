@@ -1,0 +1,416 @@
+// Operator application, local inverses and the local Vanka smoother (Sec. 3).
+//
+// Eq. (3.4): S_K(d) = R_K d + omega J_K^{-1} R_K (b - J d), with J_K the
+// restriction of the assembled J to the (k+1)(R^+S^) DoFs of cell K.  The
+// averaging loop (S0)-(S3) equals d <- d + omega (sum_K E_K J_K^{-1} R_K r) / p
+// with r = b - J d and p the number of cells sharing a DoF.  The sum is
+// accumulated colour by colour: cells of one colour share no velocity DoF and
+// pressure DoFs belong to one cell, so one colour's scatters never collide
+// (no atomics, deterministic order).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace stg {
+namespace {
+
+template <typename T>
+struct AccT { using type = T; };
+template <>
+struct AccT<__nv_bfloat16> { using type = float; };
+
+// ------------------------------------------------------------------ J x, b - J x
+template <int DIM, typename MT, typename VT>
+__global__ void __launch_bounds__(256) op_vel_rows(Geom g, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ colidx, const MT* __restrict__ vv,
+                                                   const MT* __restrict__ vp, const VT* __restrict__ x,
+                                                   const VT* __restrict__ b, VT* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nvel) return;
+  const int NV = g.NV;
+  const long long node = t / NV;
+  const int r = (int)(t - node * NV);
+  VT acc = 0;
+  const int b0 = rowptr[node], b1 = rowptr[node + 1];
+  for (int blk = b0; blk < b1; ++blk) {
+    const MT* vals = vv + (long long)blk * NV * NV + (long long)r * NV;
+    const VT* xc = x + (long long)colidx[blk] * NV;
+    for (int s = 0; s < NV; ++s) acc += (VT)vals[s] * xc[s];
+  }
+  const int ix = (int)(node % g.nn[0]);
+  const int iy = (int)((node / g.nn[0]) % g.nn[1]);
+  const int iz = (int)(node / ((long long)g.nn[0] * g.nn[1]));
+  const int a = r / DIM, c = r % DIM;
+  const int id[3] = {ix, iy, iz};
+  int clo[3], chi[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e >= DIM) {
+      clo[e] = chi[e] = 0;
+    } else if (id[e] & 1) {
+      clo[e] = chi[e] = (id[e] - 1) / 2;
+    } else {
+      clo[e] = id[e] / 2 - 1 < 0 ? 0 : id[e] / 2 - 1;
+      chi[e] = id[e] / 2 > g.n[e] - 1 ? g.n[e] - 1 : id[e] / 2;
+    }
+  }
+  for (int cz = clo[2]; cz <= chi[2]; ++cz)
+    for (int cy = clo[1]; cy <= chi[1]; ++cy)
+      for (int cx = clo[0]; cx <= chi[0]; ++cx) {
+        const int il = (ix - 2 * cx) + 3 * (iy - 2 * cy) + 9 * (iz - 2 * cz);
+        const long long K = cell_id(g, cx, cy, cz);
+        const MT* q = vp + (((K * g.nloc + il) * g.nt + a) * DIM + c) * (DIM + 1);
+        const VT* p = x + g.nvel + K * g.NP + a * (DIM + 1);
+        for (int m = 0; m <= DIM; ++m) acc += (VT)q[m] * p[m];
+      }
+  out[t] = b ? b[t] - acc : acc;
+}
+
+template <int DIM, typename MT, typename VT>
+__global__ void __launch_bounds__(256) op_pres_rows(Geom g, const MT* __restrict__ pv, const VT* __restrict__ x,
+                                                    const VT* __restrict__ b, VT* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.npres) return;
+  const long long K = t / g.NP;
+  const int q = (int)(t - K * g.NP);
+  const int a = q / (DIM + 1), m = q % (DIM + 1);
+  const int cx = (int)(K % g.n[0]);
+  const int cy = (int)((K / g.n[0]) % g.n[1]);
+  const int cz = (int)(K / ((long long)g.n[0] * g.n[1]));
+  const MT* row = pv + ((K * g.nt + a) * (DIM + 1) + m) * (long long)g.nloc * DIM;
+  VT acc = 0;
+  for (int i = 0; i < g.nloc; ++i) {
+    const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
+    const VT* xv = x + nd * g.NV + a * DIM;
+    for (int e = 0; e < DIM; ++e) acc += (VT)row[i * DIM + e] * xv[e];
+  }
+  out[g.nvel + t] = b ? b[g.nvel + t] - acc : acc;
+}
+
+// ------------------------------------------------------------------ local inverses
+// Gather J_K from the assembled operator, then in-place Gauss-Jordan inversion
+// with partial pivoting (row interchanges, first maximal pivot as in LAPACK's
+// i_amax, columns swapped back at the end).  A in shared memory, or in global
+// scratch when it does not fit (SCR != nullptr).
+template <typename CT, typename FT>
+__global__ void __launch_bounds__(256) invert_kernel(Geom g, long long p0, const int* __restrict__ rowptr,
+                                                     const double* __restrict__ vv,
+                                                     const double* __restrict__ vp,
+                                                     const double* __restrict__ pv, FT* __restrict__ jinv,
+                                                     long long stride, int* status, int equil, CT* scratch) {
+  const int n = g.npatch, NV = g.NV, nloc = g.nloc, dim = g.dim, nt = g.nt;
+  const long long p = p0 + blockIdx.x;
+  int cx, cy, cz;
+  patch_cell(g, p, cx, cy, cz);
+  const long long cell = cell_id(g, cx, cy, cz);
+  extern __shared__ unsigned char smem_raw[];
+  CT* A;
+  CT* tail;
+  if (scratch) {
+    A = scratch + (long long)blockIdx.x * n * n;
+    tail = (CT*)smem_raw;
+  } else {
+    A = (CT*)smem_raw;
+    tail = A + n * n;
+  }
+  CT* colj = tail;
+  CT* rs = colj + n;
+  CT* cs = rs + n;
+  int* perm = (int*)(cs + n);
+  __shared__ int s_piv, s_fail;
+  __shared__ CT s_pval;
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  for (int t = tid; t < n * n; t += nth) A[t] = 0;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  const int nvv = nloc * nloc * NV * NV;
+  for (int t = tid; t < nvv; t += nth) {
+    const int s = t % NV, r = (t / NV) % NV, j = (t / (NV * NV)) % nloc, i = t / (NV * NV * nloc);
+    const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9,
+                                     2 * cx + j % 3, 2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+    A[(i * NV + r) * n + j * NV + s] = (CT)vv[slot * NV * NV + r * NV + s];
+  }
+  const int nvp = nloc * nt * dim * (dim + 1);
+  const int voff = nloc * NV;
+  for (int t = tid; t < nvp; t += nth) {
+    const int m = t % (dim + 1), c = (t / (dim + 1)) % dim, a = (t / ((dim + 1) * dim)) % nt;
+    const int i = t / ((dim + 1) * dim * nt);
+    const int vrow = i * NV + a * dim + c, prow = voff + a * (dim + 1) + m;
+    A[vrow * n + prow] = (CT)vp[(((cell * nloc + i) * nt + a) * dim + c) * (dim + 1) + m];
+    A[prow * n + vrow] = (CT)pv[((cell * nt + a) * (dim + 1) + m) * (long long)nloc * dim + i * dim + c];
+  }
+  __syncthreads();
+
+  // optional equilibration: A' = Dr A Dc with Dr = 1/max|row|, then Dc = 1/max|col of Dr A|
+  for (int i = tid; i < n; i += nth) {
+    rs[i] = 1;
+    cs[i] = 1;
+  }
+  __syncthreads();
+  if (equil) {
+    for (int i = tid; i < n; i += nth) {
+      CT mx = 0;
+      for (int l = 0; l < n; ++l) mx = fmax(mx, fabs(A[i * n + l]));
+      rs[i] = mx > 0 ? (CT)1 / mx : (CT)1;
+    }
+    __syncthreads();
+    for (int l = tid; l < n; l += nth) {
+      CT mx = 0;
+      for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(A[i * n + l] * rs[i]));
+      cs[l] = mx > 0 ? (CT)1 / mx : (CT)1;
+    }
+    __syncthreads();
+    for (int t = tid; t < n * n; t += nth) A[t] *= rs[t / n] * cs[t % n];
+    __syncthreads();
+  }
+
+  for (int j = 0; j < n; ++j) {
+    if (tid < 32) {
+      CT best = -1;
+      int bi = n;
+      for (int i = j + tid; i < n; i += 32) {
+        const CT v = fabs(A[i * n + j]);
+        if (v > best || (v == best && i < bi)) {
+          best = v;
+          bi = i;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const CT ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        const CT pv_ = bi < n ? A[bi * n + j] : (CT)0;
+        s_pval = pv_;
+        if (!(fabs(pv_) > 0) || isinf(pv_)) s_fail = 1;
+        perm[j] = bi;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const int pr = s_piv;
+    if (pr != j)
+      for (int l = tid; l < n; l += nth) {
+        const CT tmp = A[j * n + l];
+        A[j * n + l] = A[pr * n + l];
+        A[pr * n + l] = tmp;
+      }
+    __syncthreads();
+    for (int i = tid; i < n; i += nth) colj[i] = A[i * n + j];
+    __syncthreads();
+    const CT inv = (CT)1 / s_pval;
+    for (int l = tid; l < n; l += nth) A[j * n + l] = (l == j ? (CT)1 : A[j * n + l]) * inv;
+    __syncthreads();
+    for (int t = tid; t < n * n; t += nth) {
+      const int i = t / n, l = t - i * n;
+      if (i == j) continue;
+      A[t] = (l == j ? (CT)0 : A[t]) - colj[i] * A[j * n + l];
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) atomicCAS(status, 0, (int)(cell + 1));
+    for (int t = tid; t < n * n; t += nth) jinv[p * stride + t] = cvt<FT>((CT)0);
+    return;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const int pj = perm[j];
+    if (pj != j)
+      for (int i = tid; i < n; i += nth) {
+        const CT tmp = A[i * n + j];
+        A[i * n + j] = A[i * n + pj];
+        A[i * n + pj] = tmp;
+      }
+    __syncthreads();
+  }
+  // A^{-1} = Dc A'^{-1} Dr, stored column-major
+  for (int t = tid; t < n * n; t += nth) {
+    const int col = t / n, row = t - col * n;
+    jinv[p * stride + t] = cvt<FT>(A[row * n + col] * cs[row] * rs[col]);
+  }
+}
+
+// ------------------------------------------------------------------ smoother
+template <typename VT, typename FT, int RPL>
+__global__ void __launch_bounds__(256) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
+                                                           long long stride, const VT* __restrict__ r,
+                                                           VT* __restrict__ z, VT scale) {
+  using AT = typename AccT<VT>::type;
+  const int n = g.npatch;
+  const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long li = (long long)blockIdx.x * wpb + wid;
+  const long long cnt = g.coff[colour + 1] - g.coff[colour];
+  extern __shared__ unsigned char smem_raw[];
+  VT* rl = reinterpret_cast<VT*>(smem_raw) + wid * n;
+  if (li >= cnt) return;
+  const long long p = g.coff[colour] + li;
+  const int* cc = g.ccount[colour];
+  long long rem = li;
+  const int jx = (int)(rem % cc[0]);
+  rem /= cc[0];
+  const int jy = (int)(rem % cc[1]);
+  const int jz = (int)(rem / cc[1]);
+  const int cx = 2 * jx + (colour & 1), cy = 2 * jy + ((colour >> 1) & 1), cz = 2 * jz + ((colour >> 2) & 1);
+  long long gi[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    gi[t] = row < n ? patch_dof(g, cx, cy, cz, row) : 0;
+    if (row < n) rl[row] = r[gi[t]];
+  }
+  __syncwarp();
+  const FT* A = jinv + p * stride;
+  AT acc[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) acc[t] = 0;
+#pragma unroll 2
+  for (int col = 0; col < n; ++col) {
+    const AT rc = (AT)rl[col];
+    const FT* Ac = A + (long long)col * n;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int row = lane + 32 * t;
+      if (row < n) acc[t] += cvt<AT>(Ac[row]) * rc;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int row = lane + 32 * t;
+    if (row < n) z[gi[t]] += scale * (VT)acc[t];
+  }
+}
+
+template <typename VT>
+__global__ void vanka_update_kernel(Geom g, VT* __restrict__ d, VT* __restrict__ z, double omega) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N) return;
+  int mult = 1;
+  if (t < g.nvel) {
+    const long long node = t / g.NV;
+    const int ix = (int)(node % g.nn[0]);
+    const int iy = (int)((node / g.nn[0]) % g.nn[1]);
+    const int iz = (int)(node / ((long long)g.nn[0] * g.nn[1]));
+    mult = node_multiplicity(g, ix, iy, iz);
+  }
+  d[t] += (VT)omega * z[t] / (VT)mult;
+  z[t] = 0;
+}
+
+}  // namespace
+
+template <typename MT, typename VT>
+void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const MT* vv, const MT* vp, const MT* pv,
+                    const VT* x, const VT* b, VT* out, cudaStream_t st) {
+  if (g.dim == 2) {
+    op_vel_rows<2, MT, VT><<<grid_for(g.nvel, 256), 256, 0, st>>>(g, rowptr, colidx, vv, vp, x, b, out);
+    op_pres_rows<2, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
+  } else {
+    op_vel_rows<3, MT, VT><<<grid_for(g.nvel, 256), 256, 0, st>>>(g, rowptr, colidx, vv, vp, x, b, out);
+    op_pres_rows<3, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
+  }
+  STG_LAUNCH_OK();
+}
+
+size_t invert_scratch_bytes(const Geom& g, int compute_f32) {
+  const int n = g.npatch;
+  const size_t cs = compute_f32 ? sizeof(float) : sizeof(double);
+  const size_t full = (size_t)n * n * cs + (size_t)3 * n * cs + (size_t)n * sizeof(int) + 64;
+  if (full <= 200 * 1024) return 0;
+  const long long chunk = g.n_cells < 1024 ? g.n_cells : 1024;
+  return cs * n * n * chunk;
+}
+
+template <typename FT>
+void invert_patches(const Geom& g, const int* rowptr, const double* vv, const double* vp, const double* pv,
+                    FT* jinv, int compute_f32, int* status, void* scratch, cudaStream_t st) {
+  const int n = g.npatch;
+  const long long stride = patch_stride(n);
+  const int threads = n <= 63 ? 128 : 256;
+  auto launch = [&](auto tag) {
+    using CT = decltype(tag);
+    const size_t tail = (size_t)3 * n * sizeof(CT) + (size_t)n * sizeof(int) + 64;
+    const size_t full = (size_t)n * n * sizeof(CT) + tail;
+    // the attribute is a per-function maximum: never set it below the 48 KB default
+    STG_CUDA_OK(cudaFuncSetAttribute(invert_kernel<CT, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(full <= 200 * 1024 ? full : tail, 48 * 1024)));
+    if (full <= 200 * 1024) {
+      invert_kernel<CT, FT><<<(unsigned)g.n_cells, threads, full, st>>>(g, 0, rowptr, vv, vp, pv, jinv, stride,
+                                                                        status, compute_f32, (CT*)nullptr);
+      STG_LAUNCH_OK();
+    } else {
+      // matrix too large for shared memory: caller-provided global scratch, in chunks
+      if (!scratch) throw Error{STG_EINVAL, "local inverse needs scratch memory"};
+      const long long chunk = g.n_cells < 1024 ? g.n_cells : 1024;
+      for (long long p0 = 0; p0 < g.n_cells; p0 += chunk) {
+        const long long cnt = g.n_cells - p0 < chunk ? g.n_cells - p0 : chunk;
+        invert_kernel<CT, FT><<<(unsigned)cnt, threads, tail, st>>>(g, p0, rowptr, vv, vp, pv, jinv, stride,
+                                                                    status, compute_f32, (CT*)scratch);
+        STG_LAUNCH_OK();
+      }
+    }
+  };
+  if (compute_f32)
+    launch(float{});
+  else
+    launch(double{});
+}
+
+template <typename VT, typename FT>
+void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st) {
+  const long long cnt = g.coff[colour + 1] - g.coff[colour];
+  if (cnt == 0) return;
+  const int n = g.npatch;
+  const long long stride = patch_stride(n);
+  const int threads = 256, wpb = threads / 32;
+  const size_t sm = (size_t)wpb * n * sizeof(VT);
+  const unsigned grid = grid_for(cnt, wpb);
+#define STG_VC(RPL)                                                                                     \
+  vanka_colour_kernel<VT, FT, RPL><<<grid, threads, sm, st>>>(g, colour, jinv, stride, r, z, scale)
+  if (n <= 32)
+    STG_VC(1);
+  else if (n <= 64)
+    STG_VC(2);
+  else if (n <= 96)
+    STG_VC(3);
+  else if (n <= 128)
+    STG_VC(4);
+  else if (n <= 192)
+    STG_VC(6);
+  else
+    STG_VC(8);
+#undef STG_VC
+  STG_LAUNCH_OK();
+}
+
+template <typename VT>
+void vanka_update(const Geom& g, VT* d, VT* z, double omega, cudaStream_t st) {
+  vanka_update_kernel<VT><<<grid_for(g.N, 256), 256, 0, st>>>(g, d, z, omega);
+  STG_LAUNCH_OK();
+}
+
+// explicit instantiations
+template void apply_operator<double, double>(const Geom&, const int*, const int*, const double*, const double*,
+                                             const double*, const double*, const double*, double*, cudaStream_t);
+template void apply_operator<float, float>(const Geom&, const int*, const int*, const float*, const float*,
+                                           const float*, const float*, const float*, float*, cudaStream_t);
+template void invert_patches<double>(const Geom&, const int*, const double*, const double*, const double*, double*,
+                                     int, int*, void*, cudaStream_t);
+template void invert_patches<float>(const Geom&, const int*, const double*, const double*, const double*, float*,
+                                    int, int*, void*, cudaStream_t);
+template void invert_patches<__nv_bfloat16>(const Geom&, const int*, const double*, const double*, const double*,
+                                            __nv_bfloat16*, int, int*, void*, cudaStream_t);
+template void vanka_colour<double, double>(const Geom&, int, const double*, const double*, double*, double,
+                                           cudaStream_t);
+template void vanka_colour<float, float>(const Geom&, int, const float*, const float*, float*, float, cudaStream_t);
+template void vanka_colour<float, __nv_bfloat16>(const Geom&, int, const __nv_bfloat16*, const float*, float*,
+                                                 float, cudaStream_t);
+template void vanka_update<double>(const Geom&, double*, double*, double, cudaStream_t);
+template void vanka_update<float>(const Geom&, float*, float*, double, cudaStream_t);
+
+}  // namespace stg

@@ -1,0 +1,221 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on small meshes.
+
+Tolerances (FP64 form): operators, transfers and other fixed-order sums agree
+to a few ulps (1e-13 relative); results that pass through the local inverses
+J_K^{-1} carry their rounding amplified by cond(J_K) (up to ~1e4 on these
+meshes), so local inverses, sweeps and V-cycles are held to 1e-11 relative;
+FGMRES solutions at rtol 1e-12 agree to 1e-8 relative.
+"""
+import numpy as np
+import pytest
+
+import stg_inputs as si
+from oracle import fgmres, multigrid, vanka
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OUT2 = si.FACE_XLO | si.FACE_YLO | si.FACE_YHI
+
+CASES = {
+    # name: (spec, k, newton)
+    "channel_k1_newton": (si.MeshSpec(2, (12, 8), (0.0, 0.0), (2.2, 0.41), 3, OUT2), 1, True),
+    "square_k0_dirichlet": (si.MeshSpec(2, (8, 8), (0.0, 0.0), (1.0, 1.0), 3, si.ALL2), 0, False),
+    "square_k2_dirichlet": (si.MeshSpec(2, (6, 4), (0.0, 0.0), (1.0, 0.7), 2, si.ALL2), 2, True),
+    "rect_k1_ragged": (si.MeshSpec(2, (10, 6), (0.3, -0.2), (1.3, 0.5), 2, si.FACE_XLO | si.FACE_YHI), 1, True),
+    "cube_k0": (si.MeshSpec(3, (4, 4, 2), (0.0,) * 3, (1.0, 1.0, 0.5), 2, si.ALL3), 0, True),
+    "cube_k1_outflow": (si.MeshSpec(3, (2, 4, 2), (0.0,) * 3, (0.5, 1.0, 0.5), 2, si.ALL3 & ~si.FACE_XHI), 1, True),
+}
+NU, TAU = 1e-3, 0.01
+
+
+def _w(spec, k):
+    if spec.dirichlet == OUT2:
+        return si.channel_w(spec, k)
+    return si.fourier_w(spec, k)
+
+
+_cache = {}
+
+
+def pair(name, **opts):
+    key = (name, tuple(sorted(opts.items())))
+    if key in _cache:
+        return _cache[key]
+    from paper_2210_02690_gb300 import Solver
+    import oracle
+
+    spec, k, newton = CASES[name]
+    w = _w(spec, k)
+    o = dict(nu1=2, nu2=2)
+    o.update(opts)
+    gpu = Solver(spec, k, NU, TAU, torch.from_numpy(w.ravel()).cuda(),
+                 linearisation="newton" if newton else "oseen", **o)
+    smoother = {0: "averaged", 1: "coloured"}[o.get("smoother", 0)] if isinstance(o.get("smoother", 0), int) \
+        else o["smoother"]
+    ref = oracle.Hierarchy(spec, k, NU, TAU, w, newton=newton, nu1=o["nu1"], nu2=o["nu2"], smoother=smoother)
+    _cache[key] = (gpu, ref)
+    return gpu, ref
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+def consistent_rhs(ref, seed=7):
+    xs = si.reference_solution(ref.spec, ref.k, seed=seed)
+    return ref.apply(xs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jacobian_every_level(name):
+    gpu, ref = pair(name)
+    for lvl, lev in enumerate(ref.levels):
+        x = si.random_vector(lev.N, 11 + lvl)
+        y = cpu(gpu.apply_jacobian(torch.from_numpy(x).cuda(), level=lvl))
+        assert rel(y, ref.J[lvl] @ x) < 1e-13, lvl
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_local_inverses(name):
+    gpu, ref = pair(name)
+    for lvl in range(1, len(ref.levels)):
+        n_cells = ref.levels[lvl].n_cells
+        for cell in sorted({0, n_cells // 3, n_cells - 1}):
+            g = gpu.local_inverse(lvl, cell)
+            assert rel(g, ref.jinv[lvl][cell]) < 1e-11, (lvl, cell)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_transfers(name):
+    gpu, ref = pair(name)
+    for lvl in range(1, len(ref.levels)):
+        xc = si.random_vector(ref.levels[lvl - 1].N, 3)
+        xf = si.random_vector(ref.levels[lvl].N, 4)
+        p = cpu(gpu.prolongate(lvl, torch.from_numpy(xc).cuda(), torch.from_numpy(xf).cuda()))
+        assert rel(p, xf + ref.P[lvl] @ xc) < 1e-14
+        r = cpu(gpu.restrict(lvl, torch.from_numpy(xf).cuda()))
+        assert rel(r, ref.P[lvl].T @ xf) < 1e-14
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve(name):
+    gpu, ref = pair(name)
+    lev0 = ref.levels[0]
+    xs = si.reference_solution(ref.spec, ref.k, seed=5, level=0)
+    b = ref.J[0] @ xs
+    x = cpu(gpu.coarse_solve(torch.from_numpy(b).cuda()))
+    assert rel(ref.J[0] @ x, b) < 1e-11
+    if ref.singular:
+        x = multigrid.normalise_pressure(lev0, x)
+    assert rel(x, ref.coarse_solve(b) if not ref.singular else multigrid.normalise_pressure(lev0, ref.coarse_solve(b))) < 1e-9
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_smoother_sweeps(name):
+    gpu, ref = pair(name)
+    lvl = len(ref.levels) - 1
+    lev = ref.levels[lvl]
+    b = si.random_vector(lev.N, 21)
+    d0 = si.random_vector(lev.N, 22)
+    d = cpu(gpu.smooth(lvl, 3, torch.from_numpy(b).cuda(), torch.from_numpy(d0).cuda()))
+    d_ref = vanka.sweep_averaged(ref.J[lvl], lev, ref.jinv[lvl], b, d0, 0.7, 3)
+    assert rel(d, d_ref) < 1e-11
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle(name):
+    gpu, ref = pair(name)
+    b = consistent_rhs(ref)
+    x = cpu(gpu.vcycle(torch.from_numpy(b).cuda()))
+    x_ref = ref.vcycle(b)
+    if ref.singular:
+        x, x_ref = multigrid.normalise_pressure(ref.fine, x), multigrid.normalise_pressure(ref.fine, x_ref)
+    assert rel(x, x_ref) < 1e-11
+
+
+def test_vcycle_coloured_smoother():
+    gpu, ref = pair("channel_k1_newton", smoother=1)
+    b = consistent_rhs(ref)
+    assert rel(cpu(gpu.vcycle(torch.from_numpy(b).cuda())), ref.vcycle(b)) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["channel_k1_newton", "square_k0_dirichlet", "cube_k1_outflow"])
+def test_fgmres(name):
+    gpu, ref = pair(name, gmres_rtol=1e-12)
+    b = consistent_rhs(ref)
+    x, its, relres, ok = gpu.gmres_solve(torch.from_numpy(b).cuda())
+    x = cpu(x)
+    x_ref, its_ref, rel_ref, ok_ref = fgmres.fgmres(ref.apply, ref.vcycle, b, rtol=1e-12)
+    assert ok and ok_ref and relres <= 1e-12
+    assert abs(its - its_ref) <= 1
+    assert rel(ref.apply(x), b) < 2e-12
+    if ref.singular:
+        x, x_ref = multigrid.normalise_pressure(ref.fine, x), multigrid.normalise_pressure(ref.fine, x_ref)
+    assert rel(x, x_ref) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [("f32", "f32"), ("f32", "bf16")])
+def test_reduced_precision_forms_converge(prec):
+    vprec, fprec = prec
+    gpu64, ref = pair("channel_k1_newton")
+    gpu, _ = pair("channel_k1_newton", vcycle_prec=vprec, factor_prec=fprec)
+    b = consistent_rhs(ref)
+    x64, its64, _, ok64 = gpu64.gmres_solve(torch.from_numpy(b).cuda())
+    x, its, relres, ok = gpu.gmres_solve(torch.from_numpy(b).cuda())
+    assert ok64 and ok and relres <= 1e-8
+    assert rel(ref.apply(cpu(x)), b) <= 1.01e-8
+    if fprec == "f32":
+        assert its <= its64 + 1
+        v = cpu(gpu.vcycle(torch.from_numpy(b).cuda()))
+        assert rel(v, ref.vcycle(b)) < 1e-4
+
+
+def test_zero_rhs_and_single_level():
+    from paper_2210_02690_gb300 import Solver
+    import oracle
+
+    spec = si.MeshSpec(2, (4, 2), (0.0, 0.0), (1.0, 0.5), 1, OUT2)
+    w = si.channel_w(spec, 1)
+    gpu = Solver(spec, 1, NU, TAU, torch.from_numpy(w.ravel()).cuda())
+    ref = oracle.Hierarchy(spec, 1, NU, TAU, w, newton=True)
+    n = ref.fine.N
+    x, its, relres, ok = gpu.gmres_solve(torch.zeros(n, dtype=torch.float64).cuda())
+    assert ok and its == 0 and float(x.abs().max()) == 0.0
+    b = si.random_vector(n, 1)
+    v = cpu(gpu.vcycle(torch.from_numpy(b).cuda()))
+    assert rel(ref.J[0] @ v, b) < 1e-11
+    gpu.close()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2210_02690_gb300 import Solver, StgError
+
+    spec = si.MeshSpec(2, (6, 4), (0.0, 0.0), (1.0, 1.0), 3, si.ALL2)  # 6 not divisible by 4
+    with pytest.raises(StgError) as e:
+        Solver(spec, 1, NU, TAU, torch.zeros(2 * 13 * 9 * 2, dtype=torch.float64).cuda())
+    assert e.value.status == 1
+    spec = si.MeshSpec(2, (4, 4), (0.0, 0.0), (1.0, 1.0), 2, si.ALL2)
+    with pytest.raises(StgError):
+        Solver(spec, 5, NU, TAU, torch.zeros(6 * 2 * 81, dtype=torch.float64).cuda())
+    with pytest.raises(StgError):
+        Solver(spec, 1, NU, TAU, torch.zeros(2 * 2 * 81, dtype=torch.float64).cuda(), factor_prec="f32")
+
+
+def test_update_linearisation_matches_fresh_setup():
+    from paper_2210_02690_gb300 import Solver
+
+    spec, k, newton = CASES["channel_k1_newton"]
+    w1 = _w(spec, k)
+    w2 = si.fourier_w(spec, k, seed=99)
+    a = Solver(spec, k, NU, TAU, torch.from_numpy(w1.ravel()).cuda(), nu1=2, nu2=2)
+    b_ = Solver(spec, k, NU, TAU, torch.from_numpy(w2.ravel()).cuda(), nu1=2, nu2=2)
+    a.update_linearisation(torch.from_numpy(w2.ravel()).cuda())
+    rhs = torch.from_numpy(si.random_vector(si.n_dofs(2, spec.n, k), 3)).cuda()
+    assert torch.equal(a.vcycle(rhs), b_.vcycle(rhs))
+    a.close()
+    b_.close()
