@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the space-time Vanka-multigrid FGMRES solver on GB300.
+
+Workload (default): the 2D channel [0, 2.2] x [0, 0.41] with 704 x 128 quads and
+four levels (88 x 16 coarse), Q2/P1disc, dG(1), nu = 1e-3, tau = 0.005, the
+Newton Jacobian at a seeded smooth linearisation velocity, V(2,2) averaged
+Vanka with omega = 0.7, FGMRES(30) to a relative residual of 1e-8.
+
+One step = one linearised solve on data resident in HBM:
+  stg_update_linearisation(w)  (assembly of every level, all local inverses
+                                J_K^{-1}, coarse factorisation)
+  stg_gmres_solve(b)           (FGMRES preconditioned by V-cycles)
+The headline form stores J_K^{-1} and runs the V-cycle in FP32 with FGMRES,
+residuals and the coarse solve in FP64; the all-FP64 form is measured on the
+same inputs for the time-to-tolerance comparison.
+
+value = Vanka-smoothed space-time DoFs per second over the whole job: the
+DoFs smoothed by all V-cycles of a step (iterations x sum over levels >= 1 of
+(nu1 + nu2) N_l) times steps times ranks, divided by the slowest rank's time.
+With several GPUs each rank solves its own seeded replica (no collective on
+the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import stg_inputs as si  # noqa: E402
+
+METRIC = "Vanka-smoothed space-time DoFs/s; FGMRES time-to-1e-8 (FP32/batched vs FP64)"
+UNIT = "smoothed space-time DoF/s"
+WORKLOAD = "channel704_k1"
+CPU_SAMPLE_FACTOR = 2     # cpu_baseline: 352 x 64 channel, same four-level hierarchy
+REF_STEP_FACTOR = 4       # --impl reference: 176 x 32 channel per step
+
+
+def describe(cfg, spec) -> str:
+    return (f"2D channel [0,2.2]x[0,0.41], {spec.n[0]}x{spec.n[1]} quads, {spec.n_levels} levels "
+            f"(coarse {spec.cells(0)[0]}x{spec.cells(0)[1]}), Q2/P1disc, dG({cfg['k']}), Newton Jacobian at seeded "
+            f"smooth w, nu={cfg['nu']}, tau={cfg['tau']}, inflow/walls Dirichlet (Nitsche), do-nothing outflow, "
+            f"V({cfg['nu1']},{cfg['nu2']}) averaged Vanka omega=0.7, FGMRES(30) rtol 1e-8")
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def oracle_step_cli(factor: int, repeats: int) -> None:
+    """Runs the oracle's full step on the channel scaled down by `factor` (child process)."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from oracle import fgmres
+
+    cfg = si.WORKLOADS[WORKLOAD]
+    spec = si.scaled(cfg["spec"], factor)
+    times, its_all = [], []
+    for r in range(repeats):
+        w = si.channel_w(spec, cfg["k"], seed=si.BASE_SEED + r)
+        t0 = time.perf_counter()
+        h = oracle.Hierarchy(spec, cfg["k"], cfg["nu"], cfg["tau"], w, newton=cfg["newton"], nu1=cfg["nu1"],
+                             nu2=cfg["nu2"])
+        b = h.apply(si.reference_solution(spec, cfg["k"]))
+        x, its, rel, ok = fgmres.fgmres(h.apply, h.vcycle, b)
+        times.append(time.perf_counter() - t0)
+        its_all.append(its)
+    sm = si.smoothed_dofs_per_cycle(spec, cfg["k"], cfg["nu1"], cfg["nu2"])
+    print(json.dumps({"times": times, "iters": its_all, "smoothed_per_cycle": sm, "cells": list(spec.n),
+                      "n_dofs": si.n_dofs(2, spec.n, cfg["k"])}))
+
+
+def run_oracle(factor: int, repeats: int, timeout: float = 900.0) -> dict:
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-step", str(factor), str(repeats)],
+                         capture_output=True, text=True, env=env, timeout=timeout, cwd=ROOT)
+    if out.returncode:
+        raise RuntimeError("oracle run failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_steps(solver, w, b, x, steps: int, torch) -> tuple:
+    """Runs `steps` steps on the solver's stream; returns (ms, iterations of the last step)."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    its = 0
+    torch.cuda.synchronize()
+    ev0.record(solver.stream)
+    for _ in range(steps):
+        solver.update_linearisation(w)
+        _, its, rel, ok = solver.gmres_solve(b, out=x)
+        if not ok:
+            raise RuntimeError(f"FGMRES did not converge (rel {rel:.2e})")
+    ev1.record(solver.stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), its
+
+
+def gpu_arm(args) -> None:
+    import torch
+
+    from paper_2210_02690_gb300 import Solver
+
+    world, rank, local = dist_setup()
+    cfg = si.WORKLOADS[WORKLOAD]
+    spec, k = cfg["spec"], cfg["k"]
+    seed = si.BASE_SEED + rank
+    w_np = si.channel_w(spec, k, seed=seed)
+    xs_np = si.reference_solution(spec, k, seed=seed + 1)
+    opts = dict(nu1=cfg["nu1"], nu2=cfg["nu2"], linearisation="newton")
+    w = torch.from_numpy(w_np.ravel()).cuda()
+    forms = {"f32": dict(vcycle_prec="f32", factor_prec="f32"), "f64": dict(vcycle_prec="f64", factor_prec="f64")}
+    n_dofs = si.n_dofs(2, spec.n, k)
+    per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
+    results = {}
+    main = None
+    for name in ("f32", "f64"):
+        solver = Solver(spec, k, cfg["nu"], cfg["tau"], w, **opts, **forms[name])
+        b = solver.apply_jacobian(torch.from_numpy(xs_np).cuda())
+        x = torch.zeros_like(b)
+        timed_steps(solver, w, b, x, args.warmup, torch)
+        steps = args.steps if name == "f32" else max(3, args.steps // 2)
+        if name == "f32":
+            solver.profile(True)
+            launches0 = solver.kernel_launches()
+        barrier(world)
+        with ClockSampler(local) as clk:
+            ms, its = timed_steps(solver, w, b, x, steps, torch)
+        barrier(world)
+        clocks = clk.summary()
+        ms_max = max_over_ranks(world, ms)
+        # split of one step: setup and solve alone
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(solver.stream)
+        solver.update_linearisation(w)
+        e[1].record(solver.stream)
+        _, its_s, rel_s, _ = solver.gmres_solve(b, out=x)
+        e[2].record(solver.stream)
+        torch.cuda.synchronize()
+        res = {"ms_per_step": ms_max / steps, "iters": its, "steps": steps, "setup_ms": e[0].elapsed_time(e[1]),
+               "time_to_tol_ms": e[1].elapsed_time(e[2]), "rel_res": rel_s, "clocks": clocks,
+               "value": per_cycle * its * steps * world / (ms_max * 1e-3)}
+        if name == "f32":
+            pms, plaunch, ppatch = solver.profile_read()
+            res["gpu_launches"] = solver.kernel_launches() - launches0
+            res["colour_kernel"] = (pms, plaunch, ppatch)
+            solver.profile(False)
+            # end to end through the public API: pinned host inputs, copies inside the timed region
+            w_h = torch.from_numpy(w_np.ravel()).pin_memory()
+            b_h = b.cpu().pin_memory()
+            x_h = torch.empty_like(b_h).pin_memory()
+            w_d, b_d = torch.empty_like(w), torch.empty_like(b)
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                w_d.copy_(w_h, non_blocking=True)
+                b_d.copy_(b_h, non_blocking=True)
+                solver.update_linearisation(w_d)
+                solver.gmres_solve(b_d, out=x)
+                x_h.copy_(x, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            e2e_ms = max_over_ranks(world, e0.elapsed_time(e1))
+            res["e2e"] = {"value": per_cycle * its * steps * world / (e2e_ms * 1e-3), "unit": UNIT,
+                          "h2d_bytes_per_step": int(w_h.numel() * 8 + b_h.numel() * 8),
+                          "d2h_bytes_per_step": int(x_h.numel() * 8),
+                          "ms_per_step": e2e_ms / steps, "wall_s": time.perf_counter() - t0}
+            main = solver
+            results[name] = res
+        else:
+            results[name] = res
+            solver.close()
+    r32 = results["f32"]
+    pms, plaunch, ppatch = r32["colour_kernel"]
+    npatch = 21 * (k + 1)
+    # algorithmic bytes of one colour-kernel launch: each patch streams its J_K^{-1}
+    # (npatch^2 FP32 values), gathers npatch residual values and reads+writes npatch values of z
+    bytes_per_patch = npatch * npatch * 4 + 3 * npatch * 4
+    avg_ms = pms / max(plaunch, 1)
+    per_launch_bytes = bytes_per_patch * ppatch / max(plaunch, 1)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "vanka_colour_kernel<float,float,2> (finest level)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+                "launches": plaunch, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+    if rank != 0:
+        if main:
+            main.close()
+        return
+    out = {
+        "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world, "steps": r32["steps"],
+        "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 factors + f32 V-cycle; f64 FGMRES/residuals/coarse solve",
+        "data": "synthetic (seeded Poiseuille + curl perturbation w, N(0,1) x*, b = J x*)",
+        "config": {"workload": f"{WORKLOAD}: " + describe(cfg, spec), "n_dofs": n_dofs,
+                   "smoothed_dofs_per_vcycle": per_cycle, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (FP32 J_K^{-1} of the finest level: "
+                         f"{spec.n[0] * spec.n[1] * npatch * npatch * 4 / 1e6:.0f} MB)",
+                   "step": "update_linearisation (assembly + local inverses + coarse factorisation) + FGMRES to 1e-8"},
+        "fgmres_iters": r32["iters"], "rel_res": r32["rel_res"], "setup_ms": r32["setup_ms"],
+        "time_to_tol_ms": r32["time_to_tol_ms"],
+        "f64_form": {k_: results["f64"][k_] for k_ in ("value", "ms_per_step", "iters", "setup_ms", "time_to_tol_ms",
+                                                        "rel_res")},
+        "speedup_time_to_tol_f32_vs_f64": results["f64"]["time_to_tol_ms"] / r32["time_to_tol_ms"],
+        "speedup_step_f32_vs_f64": results["f64"]["ms_per_step"] / r32["ms_per_step"],
+        "roofline": roofline, "e2e": r32["e2e"], "gpu_launches": r32["gpu_launches"], "clocks": r32["clocks"],
+    }
+    if main:
+        main.close()
+    if world == 1 and not args.no_cpu_baseline:
+        o = run_oracle(CPU_SAMPLE_FACTOR, 1)
+        t = sum(o["times"])
+        out["cpu_baseline"] = {"value": o["smoothed_per_cycle"] * sum(o["iters"]) / t, "unit": UNIT, "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"oracle full step (assembly, LAPACK local inverses, coarse LU, FGMRES to "
+                                         f"1e-8) on the same channel at {o['cells'][0]}x{o['cells'][1]} quads "
+                                         f"({o['n_dofs']} DoFs, 4 levels), 1 thread, {t:.1f} s"}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- reference arm
+def reference_arm(args) -> None:
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = si.WORKLOADS[WORKLOAD]
+    o = run_oracle(REF_STEP_FACTOR, args.warmup + args.steps, timeout=3600)
+    times = o["times"][args.warmup:]
+    its = o["iters"][args.warmup:]
+    t = sum(times)
+    value = o["smoothed_per_cycle"] * sum(its) / t
+    sample = (f"oracle full step on the same channel at {o['cells'][0]}x{o['cells'][1]} quads ({o['n_dofs']} DoFs, "
+              f"4 levels) per step, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: " + describe(cfg, cfg["spec"]), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--oracle-step":
+        oracle_step_cli(int(sys.argv[2]), int(sys.argv[3]))
+        return
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

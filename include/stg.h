@@ -152,6 +152,20 @@ stg_status stg_get_sizes(const stg_ctx* ctx, int level, long long* n_dofs, long 
  * values are those stored for the smoother (rounded to factor_prec). */
 stg_status stg_get_local_inverse(const stg_ctx* ctx, int level, long long cell, double* out);
 
+/* Instrumentation.  stg_profile(ctx, 1) records CUDA events on the context's
+ * stream around every launch of the smoother's colour kernel on the finest
+ * level (y_K = J_K^{-1} R_K r for the cells of one colour, Eq. (3.4)) and
+ * accumulates their device time; stg_profile(ctx, 0) stops and resets.  The
+ * V-cycle graph is recaptured when the setting changes.  stg_profile_read
+ * returns the accumulated milliseconds, the number of launches and the number
+ * of patches they processed (host pointers, each may be NULL). */
+stg_status stg_profile(stg_ctx* ctx, int enable);
+stg_status stg_profile_read(const stg_ctx* ctx, double* total_ms, long long* launches, long long* patches);
+
+/* Number of kernels this library has enqueued in this process (a CUDA-graph
+ * replay counts each of its kernel nodes). */
+long long stg_kernel_launches(void);
+
 /* Text of the last error of this context (or of the last failed stg_setup
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char* stg_last_error(const stg_ctx* ctx);

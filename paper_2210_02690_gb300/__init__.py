@@ -27,8 +27,8 @@ PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16}
 
 EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg_apply_jacobian",
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
-            "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_last_error",
-            "stg_destroy")
+            "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
+            "stg_profile_read", "stg_kernel_launches", "stg_last_error", "stg_destroy")
 
 
 class StgError(RuntimeError):
@@ -79,6 +79,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_gmres_solve": (I, [P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "stg_get_sizes": (I, [P, I, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(I)]),
         "stg_get_local_inverse": (I, [P, I, LL, P]),
+        "stg_profile": (I, [P, I]),
+        "stg_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(LL), ctypes.POINTER(LL)]),
+        "stg_kernel_launches": (LL, []),
         "stg_last_error": (ctypes.c_char_p, [P]),
         "stg_destroy": (None, [P]),
     }
@@ -249,6 +252,19 @@ class Solver:
         _check(self.lib, self.ctx, self.lib.stg_get_local_inverse(self.ctx, level, cell,
                                                                   out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def profile(self, enable: bool):
+        """Start (and reset) or stop CUDA-event timing of the finest-level colour kernels."""
+        self._call(self.lib.stg_profile, 1 if enable else 0)
+
+    def profile_read(self):
+        """(device milliseconds, launches, patches) accumulated since profiling started."""
+        ms, n, p = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        self.lib.stg_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(p))
+        return ms.value, n.value, p.value
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.stg_kernel_launches())
 
     def close(self):
         if getattr(self, "ctx", None):

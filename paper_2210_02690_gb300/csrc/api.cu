@@ -12,6 +12,11 @@
 
 namespace stg {
 
+long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+
 // ------------------------------------------------------------------ geometry
 Geom make_geom(const stg_mesh& m, int level, int k) {
   Geom g{};
@@ -174,6 +179,15 @@ struct stg_ctx {
   double *vin = nullptr, *vout = nullptr, *tmp_a = nullptr, *tmp_b = nullptr;
   double* hh = nullptr;  // pinned host
   cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  int graph_prof_events = 0;
+  long long graph_prof_patches = 0;
+  // instrumentation: CUDA events around the finest-level colour kernels
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used = 0;
+  double prof_ms = 0.0;
+  long long prof_launches = 0, prof_patches = 0, prof_pending_patches = 0;
   std::vector<void*> owned;
   std::string err;
   bool pure_dirichlet = false;
@@ -281,6 +295,16 @@ struct Ops<float> {
   static const float* pv(const LevelBufs& L) { return L.pv32; }
 };
 
+// Event record that also lands in a CUDA graph when the stream is being captured.
+void record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  STG_CUDA_OK(cudaStreamIsCapturing(st, &cap));
+  if (cap == cudaStreamCaptureStatusActive)
+    STG_CUDA_OK(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  else
+    STG_CUDA_OK(cudaEventRecord(ev, st));
+}
+
 template <typename VT>
 void residual(stg_ctx* c, const LevelBufs& L, const VT* x, const VT* b, VT* r) {
   apply_operator<VT, VT>(L.g, L.rowptr, L.colidx, Ops<VT>::vv(L), Ops<VT>::vp(L), Ops<VT>::pv(L), x, b, r, c->st);
@@ -303,7 +327,16 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
         residual<VT>(c, L, x, b, r);
         res = r;
       }
-      for (int col = 0; col < ncol; ++col) vanka_colour<VT, FT>(g, col, jinv, res, z, (VT)1, c->st);
+      for (int col = 0; col < ncol; ++col) {
+        const bool prof = c->prof_on && l == (int)c->lv.size() - 1 && c->prof_used + 2 <= (int)c->prof_ev.size();
+        if (prof) record_event(c->prof_ev[c->prof_used], c->st);
+        vanka_colour<VT, FT>(g, col, jinv, res, z, (VT)1, c->st);
+        if (prof) {
+          record_event(c->prof_ev[c->prof_used + 1], c->st);
+          c->prof_used += 2;
+          c->prof_pending_patches += g.coff[col + 1] - g.coff[col];
+        }
+      }
       vanka_update<VT>(g, x, z, c->opt.omega, c->st);
     } else {
       for (int col = 0; col < ncol; ++col) {
@@ -312,7 +345,14 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
           residual<VT>(c, L, x, b, r);
           res = r;
         }
+        const bool prof = c->prof_on && l == (int)c->lv.size() - 1 && c->prof_used + 2 <= (int)c->prof_ev.size();
+        if (prof) record_event(c->prof_ev[c->prof_used], c->st);
         vanka_colour<VT, FT>(g, col, jinv, res, x, (VT)c->opt.omega, c->st);
+        if (prof) {
+          record_event(c->prof_ev[c->prof_used + 1], c->st);
+          c->prof_used += 2;
+          c->prof_pending_patches += g.coff[col + 1] - g.coff[col];
+        }
       }
     }
   }
@@ -365,10 +405,15 @@ void vcycle_body(stg_ctx* c) {
   }
 }
 
+// One V-cycle; with profiling on, the events of the colour kernels are read
+// back after the cycle (the caller synchronises before the next one).
 void run_vcycle(stg_ctx* c) {
   if (c->opt.use_graph) {
     if (!c->graph) {
       cudaGraph_t graph = nullptr;
+      const long long before = launch_counter();
+      const int used0 = c->prof_used;
+      const long long pend0 = c->prof_pending_patches;
       STG_CUDA_OK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
       try {
         vcycle_body(c);
@@ -378,14 +423,37 @@ void run_vcycle(stg_ctx* c) {
         throw;
       }
       STG_CUDA_OK(cudaStreamEndCapture(c->st, &graph));
+      c->graph_kernels = launch_counter() - before;
+      launch_counter() = before;  // capturing enqueues nothing; replays are counted below
+      c->graph_prof_events = c->prof_used - used0;
+      c->graph_prof_patches = c->prof_pending_patches - pend0;
+      c->prof_used = used0;
+      c->prof_pending_patches = pend0;
       const cudaError_t e = cudaGraphInstantiate(&c->graph, graph, 0);
       cudaGraphDestroy(graph);
       STG_CUDA_OK(e);
     }
     STG_CUDA_OK(cudaGraphLaunch(c->graph, c->st));
+    launch_counter() += c->graph_kernels;
+    c->prof_used += c->graph_prof_events;
+    c->prof_pending_patches += c->graph_prof_patches;
   } else {
     vcycle_body(c);
   }
+}
+
+// Accumulate the recorded colour-kernel times (call after the stream has drained).
+void prof_collect(stg_ctx* c) {
+  if (!c->prof_on || c->prof_used == 0) return;
+  for (int i = 0; i + 1 < c->prof_used; i += 2) {
+    float ms = 0.f;
+    STG_CUDA_OK(cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]));
+    c->prof_ms += ms;
+    ++c->prof_launches;
+  }
+  c->prof_patches += c->prof_pending_patches;
+  c->prof_pending_patches = 0;
+  c->prof_used = 0;
 }
 
 template <typename VT>
@@ -440,6 +508,7 @@ stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double
       multi_dot(n, 1, c->wv, n, c->wv, c->partial, c->hd + 64, c->st);
       STG_CUDA_OK(cudaMemcpyAsync(c->hh, c->hd, sizeof(double) * 65, cudaMemcpyDeviceToHost, c->st));
       STG_CUDA_OK(cudaStreamSynchronize(c->st));
+      prof_collect(c);
       for (int i = 0; i <= j; ++i) Hc(i, j) = c->hh[i] + c->hh[32 + i];
       const double hn = std::sqrt(std::max(c->hh[64], 0.0));
       Hc(j + 1, j) = hn;
@@ -648,6 +717,10 @@ stg_status stg_vcycle(stg_ctx* c, const double* b, double* x) {
     cabi_to_internal<double>(g, b, c->vin, c->st);
     run_vcycle(c);
     internal_to_cabi<double>(g, c->vout, x, c->st);
+    if (c->prof_on) {
+      STG_CUDA_OK(cudaStreamSynchronize(c->st));
+      prof_collect(c);
+    }
     return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -787,6 +860,43 @@ stg_status stg_get_local_inverse(const stg_ctx* cc, int level, long long cell, d
   }
 }
 
+stg_status stg_profile(stg_ctx* c, int enable) {
+  if (!c) return STG_EINVAL;
+  try {
+    if (enable && c->prof_ev.empty()) {
+      const int per_cycle = 2 * (c->opt.nu1 + c->opt.nu2) * (1 << c->mesh.dim);
+      c->prof_ev.resize(per_cycle);
+      for (auto& e : c->prof_ev) STG_CUDA_OK(cudaEventCreate(&e));
+    }
+    if ((bool)enable != c->prof_on) {
+      STG_CUDA_OK(cudaStreamSynchronize(c->st));
+      if (c->graph) {  // the captured V-cycle changes with the instrumentation
+        STG_CUDA_OK(cudaGraphExecDestroy(c->graph));
+        c->graph = nullptr;
+      }
+    }
+    c->prof_on = enable != 0;
+    c->prof_used = 0;
+    c->prof_pending_patches = 0;
+    c->prof_ms = 0.0;
+    c->prof_launches = 0;
+    c->prof_patches = 0;
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_profile_read(const stg_ctx* c, double* total_ms, long long* launches, long long* patches) {
+  if (!c) return STG_EINVAL;
+  if (total_ms) *total_ms = c->prof_ms;
+  if (launches) *launches = c->prof_launches;
+  if (patches) *patches = c->prof_patches;
+  return STG_OK;
+}
+
+long long stg_kernel_launches(void) { return launch_counter(); }
+
 const char* stg_last_error(const stg_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
 
 void stg_destroy(stg_ctx* c) {
@@ -794,6 +904,7 @@ void stg_destroy(stg_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto& e : c->prof_ev) cudaEventDestroy(e);
   c->coarse.release();
   for (void* p : c->owned) cudaFree(p);
   if (c->hh) cudaFreeHost(c->hh);

@@ -570,8 +570,10 @@ void CoarseSolver::factor(const int* rowptr, const int* colidx, const double* vv
   STG_CUDA_OK(cudaMemsetAsync(v.L, 0, sizeof(double) * nsv * mV * mV, st));
   STG_CUDA_OK(cudaMemsetAsync(v.U, 0, sizeof(double) * nsv * mV * mV, st));
   extract_vv<<<grid_for(g.nvel, 128), 128, 0, st>>>(v, rowptr, colidx, vv);
+  STG_LAUNCH_OK();
   const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * (g.dim + 1);
   extract_vp<<<grid_for(nvp, 256), 256, 0, st>>>(v, vp, pv);
+  STG_LAUNCH_OK();
   pin_diag<<<1, 32, 0, st>>>(v);
   STG_LAUNCH_OK();
   // interiors: A_II^{-1}, W = A_II^{-1} A_IV, C = A_VI W, S = A_VV - C (scattered)

@@ -132,7 +132,14 @@ struct Error {
                                         std::to_string(__LINE__) + ": " + cudaGetErrorString(e__)}; \
   } while (0)
 
-#define STG_LAUNCH_OK() STG_CUDA_OK(cudaGetLastError())
+// Every kernel launch is followed by exactly one STG_LAUNCH_OK, which also
+// counts it (graph replays are counted per kernel node by the V-cycle driver).
+long long& launch_counter();
+#define STG_LAUNCH_OK()                    \
+  do {                                     \
+    STG_CUDA_OK(cudaGetLastError());       \
+    ++::stg::launch_counter();             \
+  } while (0)
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 

@@ -79,6 +79,7 @@ void multi_dot(long long n, int m, const double* V, long long ldv, const double*
                cudaStream_t st) {
   if (m > kMaxVec) throw Error{STG_EINVAL, "too many vectors in one orthogonalisation step"};
   multi_dot_partial<<<kDotBlocks, 256, 0, st>>>(n, m, V, ldv, w, partial);
+  STG_LAUNCH_OK();
   multi_dot_final<<<m, 256, 0, st>>>(m, kDotBlocks, partial, h);
   STG_LAUNCH_OK();
 }

@@ -205,6 +205,7 @@ __global__ void convert_kernel(long long n, const S* __restrict__ in, D* __restr
 template <typename VT>
 void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaStream_t st) {
   prolong_vel<VT><<<grid_for(gf.nvel, 256), 256, 0, st>>>(gc, gf, xc, xf);
+  STG_LAUNCH_OK();
   prolong_pres<VT><<<grid_for(gf.npres, 256), 256, 0, st>>>(gc, gf, xc, xf);
   STG_LAUNCH_OK();
 }
@@ -212,6 +213,7 @@ void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaSt
 template <typename VT>
 void restrict_res(const Geom& gc, const Geom& gf, const VT* rf, VT* bc, cudaStream_t st) {
   restrict_vel<VT><<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, rf, bc);
+  STG_LAUNCH_OK();
   restrict_pres<VT><<<grid_for(gc.npres, 256), 256, 0, st>>>(gc, gf, rf, bc);
   STG_LAUNCH_OK();
 }

@@ -309,9 +309,11 @@ void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const M
                     const VT* x, const VT* b, VT* out, cudaStream_t st) {
   if (g.dim == 2) {
     op_vel_rows<2, MT, VT><<<grid_for(g.nvel, 256), 256, 0, st>>>(g, rowptr, colidx, vv, vp, x, b, out);
+    STG_LAUNCH_OK();
     op_pres_rows<2, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
   } else {
     op_vel_rows<3, MT, VT><<<grid_for(g.nvel, 256), 256, 0, st>>>(g, rowptr, colidx, vv, vp, x, b, out);
+    STG_LAUNCH_OK();
     op_pres_rows<3, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
   }
   STG_LAUNCH_OK();
