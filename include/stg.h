@@ -166,6 +166,26 @@ stg_status stg_profile_read(const stg_ctx* ctx, double* total_ms, long long* lau
  * replay counts each of its kernel nodes). */
 long long stg_kernel_launches(void);
 
+/* Allocation-free batched inverse of caller-supplied dense matrices.  (The
+ * paper has no counterpart: it is a service for callers that cannot allocate
+ * device memory when they need local inverses -- code running while a CUDA
+ * stream is captured into a graph, hosts that hand out device memory only
+ * from their own arenas, loops that forbid allocation after start-up.)
+ *   n       matrix order, 1 <= n <= 256 (else STG_EINVAL with a message)
+ *   count   number of matrices (0 is a no-op)
+ *   a       DEVICE doubles [count][n][n], row-major, caller-owned, read only
+ *   a_inv   DEVICE doubles [count][n][n], row-major, caller-owned: the inverses
+ *           (Gauss-Jordan with partial pivoting), zeros for a singular matrix
+ *   stream  cudaStream_t for the work; the call synchronises it
+ * Needs no context and allocates nothing: the working copies live in one
+ * 8 MiB array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  The first call on a device looks up
+ * that array's device address; make it before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU (other streams or host
+ * threads) race.  Returns STG_ESINGULAR (index of the first singular matrix in
+ * stg_last_error(NULL)) or STG_ECUDA on failure. */
+stg_status stg_invert_local_noalloc(int n, long long count, const double* a, double* a_inv, void* stream);
+
 /* Text of the last error of this context (or of the last failed stg_setup
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char* stg_last_error(const stg_ctx* ctx);

@@ -28,7 +28,8 @@ PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16}
 EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg_apply_jacobian",
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
-            "stg_profile_read", "stg_kernel_launches", "stg_last_error", "stg_destroy")
+            "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_last_error",
+            "stg_destroy")
 
 
 class StgError(RuntimeError):
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_profile": (I, [P, I]),
         "stg_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(LL), ctypes.POINTER(LL)]),
         "stg_kernel_launches": (LL, []),
+        "stg_invert_local_noalloc": (I, [I, LL, P, P, P]),
         "stg_last_error": (ctypes.c_char_p, [P]),
         "stg_destroy": (None, [P]),
     }

@@ -575,6 +575,11 @@ stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
 
 }  // namespace
 
+namespace stg {
+// Error text for entry points without a context (read through stg_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_setup_error = msg; }
+}  // namespace stg
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
