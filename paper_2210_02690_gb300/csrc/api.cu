@@ -159,6 +159,7 @@ struct LevelBufs {
   float *vv32 = nullptr, *vp32 = nullptr, *pv32 = nullptr;
   void* jinv = nullptr;
   double* w = nullptr;
+  double* asm_tab = nullptr;
   void *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
 };
 
@@ -250,7 +251,7 @@ void linearise(stg_ctx* c, const double* w_cabi) {
   STG_CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
   for (int l = 0; l < nl; ++l) {
     LevelBufs& L = c->lv[l];
-    assemble_level(L.g, c->td, cf, L.w, L.rowptr, L.vv, L.nnzb, L.vp, L.pv, c->st);
+    assemble_level(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vv, L.nnzb, L.vp, L.pv, c->st);
     if (!vc64(c)) {
       convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, c->st);
       const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
@@ -259,7 +260,8 @@ void linearise(stg_ctx* c, const double* w_cabi) {
     }
     if (l == 0) continue;
     const int fp = c->opt.factor_prec;
-    const int cf32 = fp != STG_F64 && invert_scratch_bytes(L.g, 0) > 0 ? 1 : 0;
+    // FP32/BF16 factors are computed in FP32 on the equilibrated J_K; FP64 factors in FP64
+    const int cf32 = fp != STG_F64 ? 1 : 0;
     if (fp == STG_F64)
       invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, (double*)L.jinv, 0, c->status, c->inv_scratch, c->st);
     else if (fp == STG_F32)
@@ -642,6 +644,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
         L.pv32 = dalloc<float>(c, nvp);
       }
       L.w = dalloc<double>(c, g.nvel);
+      L.asm_tab = dalloc<double>(c, assemble_table_doubles(g.dim));
       L.b = dalloc<char>(c, (long long)vts * g.N);
       L.x = dalloc<char>(c, (long long)vts * g.N);
       L.r = dalloc<char>(c, (long long)vts * g.N);
@@ -650,7 +653,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       STG_CUDA_OK(cudaMemset(L.x, 0, vts * g.N));
       if (l > 0) {
         L.jinv = dalloc<char>(c, (long long)fsize(opt->factor_prec) * patch_stride(g.npatch) * g.n_cells);
-        const int cf32 = opt->factor_prec != STG_F64 && invert_scratch_bytes(g, 0) > 0 ? 1 : 0;
+        const int cf32 = opt->factor_prec != STG_F64 ? 1 : 0;
         scratch = std::max(scratch, invert_scratch_bytes(g, cf32));
       }
     }

@@ -60,25 +60,22 @@ __device__ __forceinline__ void basis_at(const Geom& g, const int* p, int i, dou
   }
 }
 
+// Face class of a cell: bit 2e set when the cell lies on a Dirichlet face
+// x_e = low, bit 2e+1 for x_e = high.  On a uniform box every w-independent
+// element matrix depends only on this class.
 template <int DIM>
-__global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
-                                                      const double* __restrict__ w,
-                                                      const int* __restrict__ rowptr, double* __restrict__ vv,
-                                                      double* __restrict__ vp, double* __restrict__ pv) {
-  constexpr int NQ = Pow3<DIM>::v;
-  constexpr int NL = NQ;
-  __shared__ double phi[NQ][NL];
-  __shared__ double dphi[NQ][NL][DIM];
-  __shared__ double qwd[NQ];
-  __shared__ double wq[5][NQ][DIM];
-  __shared__ double gw[5][NQ][DIM][DIM];
+__device__ __forceinline__ unsigned face_class(const Geom& g, const int* cc) {
+  unsigned faces = 0;
+  for (int e = 0; e < DIM; ++e) {
+    if (cc[e] == 0 && (g.dirichlet >> (2 * e) & 1u)) faces |= 1u << (2 * e);
+    if (cc[e] == g.n[e] - 1 && (g.dirichlet >> (2 * e + 1) & 1u)) faces |= 1u << (2 * e + 1);
+  }
+  return faces;
+}
 
-  const int nt = g.nt, NV = g.NV, NP = g.NP;
-  int cx, cy, cz;
-  patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
-  const int cc[3] = {cx, cy, cz};
-  const long long cell = cell_id(g, cx, cy, cz);
-
+// Reference values phi, physical gradients dphi and weights W|det| of the cell rule.
+template <int DIM, int NQ, int NL>
+__device__ void cell_tables(const Geom& g, double (*phi)[NL], double (*dphi)[NL][DIM], double* qwd) {
   for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x) {
     const int q = t / NL, i = t % NL;
     int p[3] = {q % 3, (q / 3) % 3, q / 9};
@@ -92,8 +89,149 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
       qwd[q] = wt;
     }
   }
+}
+
+// Face rule point fq of face (e0, s0): multi-index p and weight (reference weights times face Jacobian).
+template <int DIM>
+__device__ __forceinline__ double face_point(const Geom& g, int e0, int s0, int fq, int* p) {
+  double wt = 1.0;
+  int o = 0;
+  for (int d = 0; d < DIM; ++d) {
+    if (d == e0) {
+      p[d] = 3 + s0;
+    } else {
+      p[d] = (o == 0) ? fq % 3 : fq / 3;
+      wt *= c_GW[p[d]] * g.h[d] / 2.0;
+      ++o;
+    }
+  }
+  return wt;
+}
+
+// Layout of the per-level table written by element_constants.
+__host__ __device__ __forceinline__ long long tab_class_size(int dim, int nloc) {
+  const long long nd = (long long)nloc * dim;
+  return nd * nd + 2 * nd * (dim + 1);
+}
+
+// w-independent element matrices, one CTA per face class:
+//   mass M_ij (class 0 only), viscosity nu (grad phi_j, grad phi_i) delta_ce plus the Nitsche
+//   terms of A_h and B_GammaD (Eq. (2.1)), and the velocity-pressure / pressure-velocity blocks.
+template <int DIM>
+__global__ void __launch_bounds__(256) element_constants(Geom g, AsmCoef cf, double* __restrict__ tab) {
+  constexpr int NQ = Pow3<DIM>::v;
+  constexpr int NL = NQ;
+  constexpr int ND = NL * DIM;
+  __shared__ double phi[NQ][NL];
+  __shared__ double dphi[NQ][NL][DIM];
+  __shared__ double qwd[NQ];
+  const unsigned faces = blockIdx.x;
+  cell_tables<DIM, NQ, NL>(g, phi, dphi, qwd);
   __syncthreads();
-  // w_a and grad w_a at the quadrature points
+  if (faces == 0)
+    for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) {
+      const int i = t / NL, j = t % NL;
+      double m = 0.0;
+      for (int q = 0; q < NQ; ++q) m += qwd[q] * phi[q][i] * phi[q][j];
+      tab[t] = m;
+    }
+  double* base = tab + NL * NL + (long long)faces * tab_class_size(DIM, NL);
+  for (int t = threadIdx.x; t < ND * ND; t += blockDim.x) {
+    const int I = t / ND, J = t % ND;
+    const int i = I / DIM, c = I % DIM, j = J / DIM, e = J % DIM;
+    double val = 0.0;
+    if (c == e) {
+      double visc = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        double d = 0.0;
+        for (int f = 0; f < DIM; ++f) d += dphi[q][j][f] * dphi[q][i][f];
+        visc += qwd[q] * d;
+      }
+      val += cf.nu * visc;
+    }
+    for (int f = 0; f < 2 * DIM; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      const double ns = s0 ? 1.0 : -1.0, hf = g.h[e0];
+      for (int fq = 0; fq < NQ / 3; ++fq) {
+        int p[3];
+        const double wt = face_point<DIM>(g, e0, s0, fq, p);
+        double vi, vj, gi[3], gj[3];
+        basis_at<DIM>(g, p, i, vi, gi);
+        basis_at<DIM>(g, p, j, vj, gj);
+        const double dni = ns * gi[e0], dnj = ns * gj[e0];
+        double term = 0.0;
+        if (c == e) term += -cf.nu * dnj * vi - cf.nu * vj * dni + cf.gamma1 * cf.nu / hf * vj * vi;
+        if (c == e0 && e == e0) term += cf.gamma2 / hf * vj * vi;
+        val += wt * term;
+      }
+    }
+    base[t] = val;
+  }
+  double* vpt = base + (long long)ND * ND;
+  double* pvt = vpt + (long long)ND * (DIM + 1);
+  for (int t = threadIdx.x; t < ND * (DIM + 1); t += blockDim.x) {
+    const int I = t / (DIM + 1), m = t % (DIM + 1);
+    const int i = I / DIM, c = I % DIM;
+    double vol = 0.0;
+    for (int q = 0; q < NQ; ++q) {
+      const double xi = m == 0 ? 1.0 : c_X[(m == 1) ? q % 3 : (m == 2 ? (q / 3) % 3 : q / 9)];
+      vol += qwd[q] * xi * dphi[q][i][c];
+    }
+    double bnd = 0.0;
+    for (int f = 0; f < 2 * DIM; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      if (c != e0) continue;
+      const double ns = s0 ? 1.0 : -1.0;
+      for (int fq = 0; fq < NQ / 3; ++fq) {
+        int p[3];
+        const double wt = face_point<DIM>(g, e0, s0, fq, p);
+        double vi, gi[3];
+        basis_at<DIM>(g, p, i, vi, gi);
+        const double xi = m == 0 ? 1.0 : c_X[p[m - 1]];
+        bnd += wt * xi * vi * ns;
+      }
+    }
+    vpt[t] = -vol + bnd;                    // -(xi_m, d_c phi_i) + <xi_m, phi_i n_c>
+    pvt[m * ND + I] = vol - bnd;            // (d_c phi_i, xi_m) - <phi_i n_c, xi_m>
+  }
+}
+
+// Per-cell assembly: the convection (and Newton) matrices from w_a at the cell's
+// nodes, combined with the class constants, the time matrix T_ab and the factor
+// tau w_a, added into the BCSR blocks of the cell's node pairs.
+template <int DIM>
+__global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
+                                                      const double* __restrict__ w, const int* __restrict__ rowptr,
+                                                      const double* __restrict__ tab, double* __restrict__ vv,
+                                                      double* __restrict__ vp, double* __restrict__ pv) {
+  constexpr int NQ = Pow3<DIM>::v;
+  constexpr int NL = NQ;
+  constexpr int ND = NL * DIM;
+  constexpr int NTMAX = DIM == 2 ? 5 : 3;
+  constexpr int NTC = DIM == 2 ? NTMAX : 1;  // precomputed convection/Newton matrices in 2D only
+  __shared__ double phi[NQ][NL];
+  __shared__ double dphi[NQ][NL][DIM];
+  __shared__ double qwd[NQ];
+  __shared__ double wq[NTMAX][NQ][DIM];
+  __shared__ double gw[NTMAX][NQ][DIM][DIM];
+  __shared__ double cm[NTC][NL][NL];
+  __shared__ double nm[NTC][NL][NL][DIM][DIM];
+
+  const int nt = g.nt, NV = g.NV;
+  int cx, cy, cz;
+  patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
+  const int cc[3] = {cx, cy, cz};
+  const long long cell = cell_id(g, cx, cy, cz);
+  const unsigned cls = face_class<DIM>(g, cc);
+  const double* mass = tab;
+  const double* cvv = tab + NL * NL + (long long)cls * tab_class_size(DIM, NL);
+  const double* cvp = cvv + (long long)ND * ND;
+  const double* cpv = cvp + (long long)ND * (DIM + 1);
+
+  cell_tables<DIM, NQ, NL>(g, phi, dphi, qwd);
+  __syncthreads();
   for (int t = threadIdx.x; t < nt * NQ * DIM; t += blockDim.x) {
     const int a = t / (NQ * DIM), q = (t / DIM) % NQ, c = t % DIM;
     double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
@@ -107,138 +245,98 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
     for (int e = 0; e < DIM; ++e) gw[a][q][c][e] = gr[e];
   }
   __syncthreads();
-
-  // Dirichlet faces of this cell (bit f = 2*dir + side)
-  unsigned faces = 0;
-  for (int e = 0; e < DIM; ++e) {
-    if (cc[e] == 0 && (g.dirichlet >> (2 * e) & 1u)) faces |= 1u << (2 * e);
-    if (cc[e] == g.n[e] - 1 && (g.dirichlet >> (2 * e + 1) & 1u)) faces |= 1u << (2 * e + 1);
+  if (DIM == 2) {
+    // (w_a . grad phi_j, phi_i) and phi_i phi_j d_e w_a,c for every node pair
+    for (int t = threadIdx.x; t < nt * NL * NL; t += blockDim.x) {
+      const int a = t / (NL * NL), i = (t / NL) % NL, j = t % NL;
+      double conv = 0.0;
+      double nw[DIM][DIM];
+      for (int c = 0; c < DIM; ++c)
+        for (int e = 0; e < DIM; ++e) nw[c][e] = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        double u = 0.0;
+        for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
+        conv += qwd[q] * u * phi[q][i];
+        if (cf.newton) {
+          const double pp = qwd[q] * phi[q][i] * phi[q][j];
+          for (int c = 0; c < DIM; ++c)
+            for (int e = 0; e < DIM; ++e) nw[c][e] += pp * gw[a][q][c][e];
+        }
+      }
+      cm[a % NTC][i][j] = conv;
+      for (int c = 0; c < DIM; ++c)
+        for (int e = 0; e < DIM; ++e) nm[a % NTC][i][j][c][e] = nw[c][e];
+    }
+    __syncthreads();
   }
 
-  // ---- velocity-velocity blocks
   const long long nvv = (long long)NL * NL * NV * NV;
   for (long long t = threadIdx.x; t < nvv; t += blockDim.x) {
     const int s = (int)(t % NV), r = (int)((t / NV) % NV);
     const int j = (int)((t / (NV * NV)) % NL), i = (int)(t / ((long long)NV * NV * NL));
     const int a = r / DIM, c = r % DIM, b = s / DIM, e = s % DIM;
-    double val = 0.0;
-    if (c == e) {
-      double m = 0.0;
-      for (int q = 0; q < NQ; ++q) m += qwd[q] * phi[q][i] * phi[q][j];
-      val += td.T[a][b] * m;
-    }
+    double val = c == e ? td.T[a][b] * mass[i * NL + j] : 0.0;
     if (a == b) {
-      double sp = 0.0;
-      for (int q = 0; q < NQ; ++q) {
-        double term = 0.0;
-        if (c == e) {
-          double conv = 0.0, visc = 0.0;
-          for (int f = 0; f < DIM; ++f) {
-            conv += wq[a][q][f] * dphi[q][j][f];
-            visc += dphi[q][j][f] * dphi[q][i][f];
+      double sp = cvv[(i * DIM + c) * ND + j * DIM + e];
+      if (DIM == 2) {
+        if (c == e) sp += cm[a % NTC][i][j];
+        if (cf.newton) sp += nm[a % NTC][i][j][c][e];
+      } else {
+        double extra = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+          double term = 0.0;
+          if (c == e) {
+            double u = 0.0;
+            for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
+            term += u * phi[q][i];
           }
-          term += conv * phi[q][i] + cf.nu * visc;
+          if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
+          extra += qwd[q] * term;
         }
-        if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
-        sp += qwd[q] * term;
-      }
-      if (faces) {
-        for (int f = 0; f < 2 * DIM; ++f) {
-          if (!(faces >> f & 1u)) continue;
-          const int e0 = f >> 1, s0 = f & 1;
-          const double ns = s0 ? 1.0 : -1.0, hf = g.h[e0];
-          double fdet = 1.0;
-          for (int d = 0; d < DIM; ++d)
-            if (d != e0) fdet *= g.h[d] / 2.0;
-          double acc = 0.0;
-          for (int fq = 0; fq < NQ / 3; ++fq) {
-            int p[3], o = 0, rem = fq;
-            double wt = fdet;
-            for (int d = 0; d < DIM; ++d) {
-              if (d == e0) {
-                p[d] = 3 + s0;
-              } else {
-                p[d] = (o == 0) ? rem % 3 : rem / 3;
-                wt *= c_GW[p[d]];
-                ++o;
-              }
-            }
-            double vi, vj, gi[3], gj[3];
-            basis_at<DIM>(g, p, i, vi, gi);
-            basis_at<DIM>(g, p, j, vj, gj);
-            const double dni = ns * gi[e0], dnj = ns * gj[e0];
-            double term = 0.0;
-            if (c == e) term += -cf.nu * dnj * vi - cf.nu * vj * dni + cf.gamma1 * cf.nu / hf * vj * vi;
-            if (c == e0 && e == e0) term += cf.gamma2 / hf * vj * vi;
-            acc += wt * term;
-          }
-          sp += acc;
-        }
+        sp += extra;
       }
       val += cf.tau * td.w[a] * sp;
     }
-    const int li[3] = {i % 3, (i / 3) % 3, i / 9}, lj[3] = {j % 3, (j / 3) % 3, j / 9};
-    const long long slot = bcsr_slot(g, rowptr, 2 * cx + li[0], 2 * cy + li[1], 2 * cz + li[2], 2 * cx + lj[0],
-                                      2 * cy + lj[1], 2 * cz + lj[2]);
+    const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9, 2 * cx + j % 3,
+                                      2 * cy + (j / 3) % 3, 2 * cz + j / 9);
     vv[slot * NV * NV + (long long)r * NV + s] += val;
   }
 
-  // ---- velocity-pressure [cell][i][a][c][m] and pressure-velocity [cell][a][m][i][c]
+  // velocity-pressure [cell][i][a][c][m] and pressure-velocity [cell][a][m][i][c]
   const int nvp = NL * nt * DIM * (DIM + 1);
   for (int t = threadIdx.x; t < nvp; t += blockDim.x) {
     const int m = t % (DIM + 1), c = (t / (DIM + 1)) % DIM, a = (t / ((DIM + 1) * DIM)) % nt;
     const int i = t / ((DIM + 1) * DIM * nt);
-    double vol = 0.0;
-    for (int q = 0; q < NQ; ++q) {
-      const double xi = m == 0 ? 1.0 : c_X[(m == 1) ? q % 3 : (m == 2 ? (q / 3) % 3 : q / 9)];
-      vol += qwd[q] * xi * dphi[q][i][c];
-    }
-    double bnd = 0.0;
-    for (int f = 0; f < 2 * DIM; ++f) {
-      if (!(faces >> f & 1u)) continue;
-      const int e0 = f >> 1, s0 = f & 1;
-      if (c != e0) continue;
-      const double ns = s0 ? 1.0 : -1.0;
-      double fdet = 1.0;
-      for (int d = 0; d < DIM; ++d)
-        if (d != e0) fdet *= g.h[d] / 2.0;
-      for (int fq = 0; fq < NQ / 3; ++fq) {
-        int p[3], o = 0, rem = fq;
-        double wt = fdet;
-        for (int d = 0; d < DIM; ++d) {
-          if (d == e0) {
-            p[d] = 3 + s0;
-          } else {
-            p[d] = (o == 0) ? rem % 3 : rem / 3;
-            wt *= c_GW[p[d]];
-            ++o;
-          }
-        }
-        double vi, gi[3];
-        basis_at<DIM>(g, p, i, vi, gi);
-        const double xi = m == 0 ? 1.0 : c_X[p[m - 1]];
-        bnd += wt * xi * vi * ns;
-      }
-    }
-    const double s = cf.tau * td.w[a];
-    vp[(((cell * NL + i) * nt + a) * DIM + c) * (DIM + 1) + m] = s * (-vol + bnd);
-    pv[((cell * nt + a) * (DIM + 1) + m) * (long long)NL * DIM + i * DIM + c] = s * (vol - bnd);
+    const double sc = cf.tau * td.w[a];
+    const int I = i * DIM + c;
+    vp[(((cell * NL + i) * nt + a) * DIM + c) * (DIM + 1) + m] = sc * cvp[I * (DIM + 1) + m];
+    pv[((cell * nt + a) * (DIM + 1) + m) * (long long)NL * DIM + I] = sc * cpv[m * ND + I];
   }
-  (void)NP;
 }
 
 }  // namespace
 
+long long assemble_table_doubles(int dim) {
+  const int nloc = dim == 2 ? 9 : 27;
+  return (long long)nloc * nloc + (1LL << (2 * dim)) * tab_class_size(dim, nloc);
+}
+
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
-                    double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st) {
+                    double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st) {
   STG_CUDA_OK(cudaMemsetAsync(vv, 0, sizeof(double) * nnzb * g.NV * g.NV, st));
+  const unsigned ncls = 1u << (2 * g.dim);
+  if (g.dim == 2)
+    element_constants<2><<<ncls, 256, 0, st>>>(g, cf, tab);
+  else
+    element_constants<3><<<ncls, 256, 0, st>>>(g, cf, tab);
+  STG_LAUNCH_OK();
   for (int col = 0; col < (1 << g.dim); ++col) {
     const long long cnt = g.coff[col + 1] - g.coff[col];
     if (cnt == 0) continue;
     if (g.dim == 2)
-      assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, vv, vp, pv);
+      assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, vv, vp, pv);
     else
-      assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, vv, vp, pv);
+      assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, vv, vp, pv);
     STG_LAUNCH_OK();
   }
 }

@@ -22,8 +22,10 @@ struct AsmCoef {
 
 // ---- assembly (assemble.cu)
 void upload_fe_tables();
+// doubles of the per-level table of w-independent element matrices (mass + one set per face class)
+long long assemble_table_doubles(int dim);
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
-                    double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
+                    double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
 
 // ---- operators, smoother and transfers (vanka.cu, transfer.cu)
 // out = b - J x (has_b) or out = J x; MT = operator precision, VT = vector precision
