@@ -81,6 +81,10 @@ typedef struct {
   double gmres_atol;       /* (defaults 1e-8 and 0; the paper's absolute 1e-9: set    */
                            /*  rtol = 0, atol = 1e-9)                                  */
   int use_graph;           /* capture the V-cycle in a CUDA graph (default 1)         */
+  int coarse_refine;       /* FP32 V-cycle only: the coarse factors are FP32 and each  */
+                           /* coarse solve adds this many steps of iterative          */
+                           /* refinement with FP64 residuals (default 2); the FP64    */
+                           /* V-cycle uses FP64 coarse factors                        */
 } stg_options;
 
 /* Fills the defaults listed above.  Returns STG_EINVAL for a null pointer. */

@@ -50,7 +50,7 @@ class stg_options(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("gamma1", ctypes.c_double),
                 ("gamma2", ctypes.c_double), ("factor_prec", ctypes.c_int), ("vcycle_prec", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
-                ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int)]
+                ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int), ("coarse_refine", ctypes.c_int)]
 
 
 _lib = None

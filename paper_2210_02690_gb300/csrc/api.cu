@@ -171,8 +171,9 @@ struct stg_ctx {
   cudaStream_t st = nullptr;
   TimeData td{};
   std::vector<LevelBufs> lv;
-  CoarseSolver coarse;
-  double *cb64 = nullptr, *cx64 = nullptr;
+  CoarseSolver<double> coarse64;  // FP64 form
+  CoarseSolver<float> coarse32;   // FP32 form: FP32 factors, FP64 iterative refinement
+  double *cb64 = nullptr, *cx64 = nullptr, *cr64 = nullptr, *cd64 = nullptr;
   int* status = nullptr;
   void* inv_scratch = nullptr;
   // FGMRES (finest level, internal layout, FP64)
@@ -272,12 +273,15 @@ void linearise(stg_ctx* c, const double* w_cabi) {
                                     c->inv_scratch, c->st);
   }
   LevelBufs& C0 = c->lv[0];
-  c->coarse.factor(C0.rowptr, C0.colidx, C0.vv, C0.vp, C0.pv, c->st);
+  if (vc64(c))
+    c->coarse64.factor(C0.rowptr, C0.colidx, C0.vv, C0.vp, C0.pv, c->st);
+  else
+    c->coarse32.factor(C0.rowptr, C0.colidx, C0.vv, C0.vp, C0.pv, c->st);
   int hs[4];
   STG_CUDA_OK(cudaMemcpyAsync(hs, c->status, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
   STG_CUDA_OK(cudaStreamSynchronize(c->st));
   if (hs[0]) throw Error{STG_ESINGULAR, "singular local matrix J_K of cell " + std::to_string(hs[0] - 1)};
-  const int cs = c->coarse.read_status(c->st);
+  const int cs = vc64(c) ? c->coarse64.read_status(c->st) : c->coarse32.read_status(c->st);
   if (cs > 0) throw Error{STG_ESINGULAR, "singular block in the coarse solver (block " + std::to_string(cs - 1) + ")"};
   if (cs < 0) throw Error{STG_ECUDA, "coarse matrix coupling outside the slab block structure"};
 }
@@ -360,14 +364,31 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
   }
 }
 
+// x = J_0^{-1} b on FP64 vectors.  FP64 form: the FP64 factors.  FP32 form: the
+// FP32 factors followed by coarse_refine steps of iterative refinement with the
+// residual b - J_0 x computed in FP64.
+void coarse_solve64(stg_ctx* c, const double* b, double* x) {
+  if (vc64(c)) {
+    c->coarse64.solve(b, x, c->st);
+    return;
+  }
+  const LevelBufs& L = c->lv[0];
+  c->coarse32.solve(b, x, c->st);
+  for (int it = 0; it < c->opt.coarse_refine; ++it) {
+    apply_operator<double, double>(L.g, L.rowptr, L.colidx, L.vv, L.vp, L.pv, x, b, c->cr64, c->st);
+    c->coarse32.solve(c->cr64, c->cd64, c->st);
+    axpby(L.g.N, 1.0, c->cd64, 1.0, x, c->st);
+  }
+}
+
 template <typename VT>
 void coarse_level(stg_ctx* c) {
   LevelBufs& L = c->lv[0];
   if (std::is_same<VT, double>::value) {
-    c->coarse.solve((const double*)L.b, (double*)L.x, c->st);
+    coarse_solve64(c, (const double*)L.b, (double*)L.x);
   } else {
     convert(L.g.N, (const float*)L.b, c->cb64, c->st);
-    c->coarse.solve(c->cb64, c->cx64, c->st);
+    coarse_solve64(c, c->cb64, c->cx64);
     convert(L.g.N, c->cx64, (float*)L.x, c->st);
   }
 }
@@ -572,6 +593,7 @@ stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
   if (o->nu1 < 0 || o->nu2 < 0) throw Error{STG_EINVAL, "negative smoothing steps"};
   if (o->gmres_restart < 1 || o->gmres_restart > 30) throw Error{STG_EINVAL, "gmres_restart must be in 1..30"};
   if (o->smoother != STG_VANKA_AVERAGED && o->smoother != STG_VANKA_COLOURED) throw Error{STG_EINVAL, "bad smoother"};
+  if (o->coarse_refine < 0 || o->coarse_refine > 20) throw Error{STG_EINVAL, "coarse_refine must be in 0..20"};
   return STG_OK;
 }
 
@@ -602,6 +624,7 @@ stg_status stg_options_default(stg_options* o) {
   o->gmres_rtol = 1e-8;
   o->gmres_atol = 0.0;
   o->use_graph = 1;
+  o->coarse_refine = 2;
   return STG_OK;
 }
 
@@ -658,9 +681,14 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       }
     }
     if (scratch) c->inv_scratch = dalloc<char>(c, (long long)scratch);
-    c->coarse.init(c->lv[0].g, c->pure_dirichlet);
+    if (f64)
+      c->coarse64.init(c->lv[0].g, c->pure_dirichlet);
+    else
+      c->coarse32.init(c->lv[0].g, c->pure_dirichlet);
     c->cb64 = dalloc<double>(c, c->lv[0].g.N);
     c->cx64 = dalloc<double>(c, c->lv[0].g.N);
+    c->cr64 = dalloc<double>(c, c->lv[0].g.N);
+    c->cd64 = dalloc<double>(c, c->lv[0].g.N);
     c->status = dalloc<int>(c, 4);
     const long long n = c->lv.back().g.N;
     const int m = opt->gmres_restart;
@@ -792,9 +820,9 @@ stg_status stg_coarse_solve(stg_ctx* c, const double* b, double* x) {
   if (!c || !b || !x) return STG_EINVAL;
   try {
     const Geom& g = c->lv[0].g;
-    cabi_to_internal<double>(g, b, c->cb64, c->st);
-    c->coarse.solve(c->cb64, c->cx64, c->st);
-    internal_to_cabi<double>(g, c->cx64, x, c->st);
+    cabi_to_internal<double>(g, b, c->tmp_a, c->st);
+    coarse_solve64(c, c->tmp_a, c->tmp_b);
+    internal_to_cabi<double>(g, c->tmp_b, x, c->st);
     return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -913,7 +941,8 @@ void stg_destroy(stg_ctx* c) {
   else cudaDeviceSynchronize();
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto& e : c->prof_ev) cudaEventDestroy(e);
-  c->coarse.release();
+  c->coarse64.release();
+  c->coarse32.release();
   for (void* p : c->owned) cudaFree(p);
   if (c->hh) cudaFreeHost(c->hh);
   delete c;

@@ -15,6 +15,7 @@
 // constant-pressure null vector per Radau node; the pressure coefficient 0 of
 // cell 0 is then fixed to zero at every Radau node (its row and column become
 // identity rows), which yields the solution with that value for consistent b.
+#include <algorithm>
 #include <vector>
 
 #include "coarse.cuh"
@@ -22,34 +23,41 @@
 
 namespace stg {
 
-void copy_ptrs(double* const* src, double* const* dst, int batch, long long n, cudaStream_t st);
+template <typename T>
+void copy_ptrs(T* const* src, T* const* dst, int batch, long long n, cudaStream_t st);
 
 namespace {
 
 // ---------------------------------------------------------------- batched dense kernels
-__global__ void __launch_bounds__(1024) bgj_kernel(int m, double* const* As, int* status) {
-  double* A = As[blockIdx.x];
-  extern __shared__ double sh[];
-  double* colj = sh;
+// In-place Gauss-Jordan inverse with partial pivoting; one CTA per matrix.  With
+// SMEM the matrix is copied into shared memory first (when it fits).
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) bgj_kernel(int m, T* const* As, int* status) {
+  T* G = As[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* A = SMEM ? reinterpret_cast<T*>(sh_raw) : G;
+  T* colj = SMEM ? A + (long long)m * m : reinterpret_cast<T*>(sh_raw);
   int* perm = reinterpret_cast<int*>(colj + m);
   __shared__ int s_piv, s_fail;
-  __shared__ double s_pval;
+  __shared__ T s_pval;
   const int tid = threadIdx.x, nth = blockDim.x;
   if (tid == 0) s_fail = 0;
+  if (SMEM)
+    for (long long t = tid; t < (long long)m * m; t += nth) A[t] = G[t];
   __syncthreads();
   for (int j = 0; j < m; ++j) {
     if (tid < 32) {
-      double best = -1.0;
+      T best = -1;
       int bi = m;
       for (int i = j + tid; i < m; i += 32) {
-        const double v = fabs(A[(long long)i * m + j]);
+        const T v = fabs(A[(long long)i * m + j]);
         if (v > best || (v == best && i < bi)) {
           best = v;
           bi = i;
         }
       }
       for (int off = 16; off > 0; off >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
         const int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ob > best || (ob == best && oi < bi)) {
           best = ob;
@@ -58,9 +66,9 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, double* const* As, int
       }
       if (tid == 0) {
         s_piv = bi;
-        const double pv = bi < m ? A[(long long)bi * m + j] : 0.0;
+        const T pv = bi < m ? A[(long long)bi * m + j] : (T)0;
         s_pval = pv;
-        if (!(fabs(pv) > 0.0) || isinf(pv)) s_fail = 1;
+        if (!(fabs(pv) > (T)0) || isinf(pv)) s_fail = 1;
         perm[j] = bi;
       }
     }
@@ -69,20 +77,20 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, double* const* As, int
     const int pr = s_piv;
     if (pr != j)
       for (int l = tid; l < m; l += nth) {
-        const double t = A[(long long)j * m + l];
+        const T t = A[(long long)j * m + l];
         A[(long long)j * m + l] = A[(long long)pr * m + l];
         A[(long long)pr * m + l] = t;
       }
     __syncthreads();
     for (int i = tid; i < m; i += nth) colj[i] = A[(long long)i * m + j];
     __syncthreads();
-    const double inv = 1.0 / s_pval;
-    for (int l = tid; l < m; l += nth) A[(long long)j * m + l] = (l == j ? 1.0 : A[(long long)j * m + l]) * inv;
+    const T inv = (T)1 / s_pval;
+    for (int l = tid; l < m; l += nth) A[(long long)j * m + l] = (l == j ? (T)1 : A[(long long)j * m + l]) * inv;
     __syncthreads();
     for (long long t = tid; t < (long long)m * m; t += nth) {
       const int i = (int)(t / m), l = (int)(t - (long long)i * m);
       if (i == j) continue;
-      A[t] = (l == j ? 0.0 : A[t]) - colj[i] * A[(long long)j * m + l];
+      A[t] = (l == j ? (T)0 : A[t]) - colj[i] * A[(long long)j * m + l];
     }
     __syncthreads();
   }
@@ -94,36 +102,38 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, double* const* As, int
     const int pj = perm[j];
     if (pj != j)
       for (int i = tid; i < m; i += nth) {
-        const double t = A[(long long)i * m + j];
+        const T t = A[(long long)i * m + j];
         A[(long long)i * m + j] = A[(long long)i * m + pj];
         A[(long long)i * m + pj] = t;
       }
     __syncthreads();
   }
+  if (SMEM)
+    for (long long t = tid; t < (long long)m * m; t += nth) G[t] = A[t];
 }
 
 // C = alpha A B + beta C, row-major, batched through pointer arrays; 32x32 tiles.
-__global__ void __launch_bounds__(256) bgemm_kernel(int M, int N, int K, double alpha, const double* const* As,
-                                                    int lda, const double* const* Bs, int ldb, double beta,
-                                                    double* const* Cs, int ldc) {
-  const double* A = As[blockIdx.z];
-  const double* B = Bs[blockIdx.z];
-  double* C = Cs[blockIdx.z];
-  __shared__ double sa[32][33], sb[32][33];
+template <typename T>
+__global__ void __launch_bounds__(256) bgemm_kernel(int M, int N, int K, T alpha, const T* const* As, int lda,
+                                                    const T* const* Bs, int ldb, T beta, T* const* Cs, int ldc) {
+  const T* A = As[blockIdx.z];
+  const T* B = Bs[blockIdx.z];
+  T* C = Cs[blockIdx.z];
+  __shared__ T sa[32][33], sb[32][33];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  T acc[2][2] = {{0, 0}, {0, 0}};
   for (int k0 = 0; k0 < K; k0 += 32) {
     for (int t = threadIdx.x; t < 32 * 32; t += 256) {
       const int i = t / 32, kk = t % 32;
-      sa[i][kk] = (r0 + i < M && k0 + kk < K) ? A[(long long)(r0 + i) * lda + k0 + kk] : 0.0;
-      sb[i][kk] = (k0 + i < K && c0 + kk < N) ? B[(long long)(k0 + i) * ldb + c0 + kk] : 0.0;
+      sa[i][kk] = (r0 + i < M && k0 + kk < K) ? A[(long long)(r0 + i) * lda + k0 + kk] : (T)0;
+      sb[i][kk] = (k0 + i < K && c0 + kk < N) ? B[(long long)(k0 + i) * ldb + c0 + kk] : (T)0;
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < 32; ++kk) {
-      const double a0 = sa[ty * 2][kk], a1 = sa[ty * 2 + 1][kk];
-      const double b0 = sb[kk][tx * 2], b1 = sb[kk][tx * 2 + 1];
+      const T a0 = sa[ty * 2][kk], a1 = sa[ty * 2 + 1][kk];
+      const T b0 = sb[kk][tx * 2], b1 = sb[kk][tx * 2 + 1];
       acc[0][0] += a0 * b0;
       acc[0][1] += a0 * b1;
       acc[1][0] += a1 * b0;
@@ -135,27 +145,29 @@ __global__ void __launch_bounds__(256) bgemm_kernel(int M, int N, int K, double 
     for (int v = 0; v < 2; ++v) {
       const int r = r0 + ty * 2 + u, c = c0 + tx * 2 + v;
       if (r < M && c < N) {
-        double* p = C + (long long)r * ldc + c;
-        *p = alpha * acc[u][v] + (beta == 0.0 ? 0.0 : beta * *p);
+        T* p = C + (long long)r * ldc + c;
+        *p = alpha * acc[u][v] + (beta == (T)0 ? (T)0 : beta * *p);
       }
     }
 }
 
 // y = alpha A x + beta y, batched; one warp per row.
-__global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, double alpha, const double* const* As, int lda,
-                                                    const double* const* xs, double beta, double* const* ys) {
-  const double* A = As[blockIdx.y];
-  const double* x = xs[blockIdx.y];
-  double* y = ys[blockIdx.y];
+template <typename T>
+__global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, T alpha, const T* const* As, int lda,
+                                                    const T* const* xs, T beta, T* const* ys) {
+  const T* A = As[blockIdx.y];
+  const T* x = xs[blockIdx.y];
+  T* y = ys[blockIdx.y];
   const int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
   if (row >= M) return;
-  double acc = 0.0;
+  T acc = 0;
   for (int c = lane; c < N; c += 32) acc += A[(long long)row * lda + c] * x[c];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if (lane == 0) y[row] = alpha * acc + (beta == 0.0 ? 0.0 : beta * y[row]);
+  if (lane == 0) y[row] = alpha * acc + (beta == (T)0 ? (T)0 : beta * y[row]);
 }
 
-__global__ void copy_kernel(long long n, const double* __restrict__ a, double* __restrict__ b) {
+template <typename T>
+__global__ void copy_kernel(long long n, const T* __restrict__ a, T* __restrict__ b) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = a[t];
 }
@@ -210,13 +222,14 @@ __device__ __forceinline__ bool is_pinned(const Geom& g, int pin, long long t) {
   return u < g.NP && (u % (g.dim + 1)) == 0;  // cell 0, coefficient 0, every Radau node
 }
 
-__device__ void put(const CoarseView& v, long long row, long long col, double val) {
+template <typename T>
+__device__ void put(const CoarseView<T>& v, long long row, long long col, double val) {
   const Geom& g = v.g;
   if (is_pinned(g, v.pin, row) || is_pinned(g, v.pin, col)) return;
   const Cls r = classify(g, v.mV, row), c = classify(g, v.mV, col);
   const int mV = v.mV, mI = v.mI;
   long long idx = -1;
-  double* base = nullptr;
+  T* base = nullptr;
   if (r.type == 1 && c.type == 1) {
     if (r.slab == c.slab) {
       base = v.AII;
@@ -249,12 +262,13 @@ __device__ void put(const CoarseView& v, long long row, long long col, double va
     }
   }
   if (base)
-    base[idx] = val;
+    base[idx] = (T)val;
   else if (val != 0.0)
     atomicOr(v.status + 1, 1);  // coupling outside the expected block structure
 }
 
-__global__ void extract_vv(CoarseView v, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+template <typename T>
+__global__ void extract_vv(CoarseView<T> v, const int* __restrict__ rowptr, const int* __restrict__ colidx,
                            const double* __restrict__ vv) {
   const Geom& g = v.g;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,7 +280,8 @@ __global__ void extract_vv(CoarseView v, const int* __restrict__ rowptr, const i
       put(v, t, (long long)colidx[blk] * g.NV + s, vv[((long long)blk * g.NV + r) * g.NV + s]);
 }
 
-__global__ void extract_vp(CoarseView v, const double* __restrict__ vp, const double* __restrict__ pv) {
+template <typename T>
+__global__ void extract_vp(CoarseView<T> v, const double* __restrict__ vp, const double* __restrict__ pv) {
   const Geom& g = v.g;
   const int d = g.dim;
   const long long per = (long long)g.nloc * g.nt * d * (d + 1);
@@ -289,18 +304,20 @@ __global__ void extract_vp(CoarseView v, const double* __restrict__ vp, const do
 
 // Identity rows for the unused pressure slots of the last vertex plane (it has
 // no cell column to its right) and, when pinned, for the fixed pressure value.
-__global__ void pin_diag(CoarseView v) {
+template <typename T>
+__global__ void pin_diag(CoarseView<T> v) {
   const int a = threadIdx.x;
   if (a >= v.g.nt) return;
   const long long pn = (long long)v.g.nn[1] * v.g.nn[2];
   const long long loc = pn * v.g.NV + a;
   const long long mV = v.mV;
-  v.D[((long long)(v.nsv - 1) * mV + loc) * mV + loc] = 1.0;
-  if (v.pin) v.D[loc * mV + loc] = 1.0;
+  v.D[((long long)(v.nsv - 1) * mV + loc) * mV + loc] = (T)1;
+  if (v.pin) v.D[loc * mV + loc] = (T)1;
 }
 
 // D[t] -= C[t-1](lower right) + C[t](upper left); U[t] -= C[t](upper right); L[t+1] -= C[t](lower left)
-__global__ void schur_combine(CoarseView v, const double* __restrict__ C) {
+template <typename T>
+__global__ void schur_combine(CoarseView<T> v, const T* __restrict__ C) {
   const int mV = v.mV, nsi = v.nsi;
   const long long per = (long long)mV * mV;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,10 +325,10 @@ __global__ void schur_combine(CoarseView v, const double* __restrict__ C) {
   const int s = (int)(t / per);
   const int i = (int)((t % per) / mV), j = (int)(t % mV);
   const long long ld = 2 * mV;
-  double d = v.D[t];
+  T d = v.D[t];
   if (s > 0) d -= C[(long long)(s - 1) * 4 * per + (long long)(mV + i) * ld + mV + j];
   if (s < nsi) {
-    const double* Cs = C + (long long)s * 4 * per;
+    const T* Cs = C + (long long)s * 4 * per;
     d -= Cs[(long long)i * ld + j];
     v.U[t] -= Cs[(long long)i * ld + mV + j];
     v.L[t + per] -= Cs[(long long)(mV + i) * ld + j];
@@ -319,50 +336,54 @@ __global__ void schur_combine(CoarseView v, const double* __restrict__ C) {
   v.D[t] = d;
 }
 
-__global__ void gather_rhs(CoarseView v, const double* __restrict__ b, double* __restrict__ bV,
-                           double* __restrict__ bI) {
+template <typename T>
+__global__ void gather_rhs(CoarseView<T> v, const double* __restrict__ b, T* __restrict__ bV, T* __restrict__ bI) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= v.g.N) return;
   const Cls c = classify(v.g, v.mV, t);
-  const double val = is_pinned(v.g, v.pin, t) ? 0.0 : b[t];
+  const T val = is_pinned(v.g, v.pin, t) ? (T)0 : (T)b[t];
   if (c.type == 0)
     bV[(long long)c.slab * v.mV + c.loc] = val;
   else
     bI[(long long)c.slab * v.mI + c.loc] = val;
 }
 
-__global__ void scatter_sol(CoarseView v, const double* __restrict__ xV, const double* __restrict__ xI,
+template <typename T>
+__global__ void scatter_sol(CoarseView<T> v, const T* __restrict__ xV, const T* __restrict__ xI,
                             double* __restrict__ x) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= v.g.N) return;
   const Cls c = classify(v.g, v.mV, t);
-  x[t] = c.type == 0 ? xV[(long long)c.slab * v.mV + c.loc] : xI[(long long)c.slab * v.mI + c.loc];
+  x[t] = (double)(c.type == 0 ? xV[(long long)c.slab * v.mV + c.loc] : xI[(long long)c.slab * v.mI + c.loc]);
 }
 
 // bV[t] -= cI[t-1](lower half) + cI[t](upper half)
-__global__ void rhs_combine(CoarseView v, const double* __restrict__ cI, double* __restrict__ bV) {
+template <typename T>
+__global__ void rhs_combine(CoarseView<T> v, const T* __restrict__ cI, T* __restrict__ bV) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int mV = v.mV;
   if (t >= (long long)(v.nsi + 1) * mV) return;
   const int s = (int)(t / mV), i = (int)(t % mV);
-  double val = bV[t];
+  T val = bV[t];
   if (s > 0) val -= cI[(long long)(s - 1) * 2 * mV + mV + i];
   if (s < v.nsi) val -= cI[(long long)s * 2 * mV + i];
   bV[t] = val;
 }
 
-double** upload_ptrs(const std::vector<double*>& h, std::vector<void*>& owned) {
+template <typename T>
+T** upload_ptrs(const std::vector<T*>& h, std::vector<void*>& owned) {
   if (h.empty()) return nullptr;
-  double** d = nullptr;
-  STG_CUDA_OK(cudaMalloc(&d, sizeof(double*) * h.size()));
-  STG_CUDA_OK(cudaMemcpy(d, h.data(), sizeof(double*) * h.size(), cudaMemcpyHostToDevice));
+  T** d = nullptr;
+  STG_CUDA_OK(cudaMalloc(&d, sizeof(T*) * h.size()));
+  STG_CUDA_OK(cudaMemcpy(d, h.data(), sizeof(T*) * h.size(), cudaMemcpyHostToDevice));
   owned.push_back(d);
   return d;
 }
 
 }  // namespace
 
-void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
+template <typename T>
+void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   v.g = geom;
   v.pin = pure_dirichlet ? 1 : 0;
   v.nsi = geom.n[0];
@@ -371,8 +392,8 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
   v.mV = (int)(pn * geom.NV + geom.nt);
   v.mI = (int)(pn * geom.NV + (long long)geom.n[1] * geom.n[2] * geom.NP - geom.nt);
   const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
-  auto alloc = [&](double** p, long long n) {
-    STG_CUDA_OK(cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1)));
+  auto alloc = [&](T** p, long long n) {
+    STG_CUDA_OK(cudaMalloc(p, sizeof(T) * (n > 0 ? n : 1)));
     owned.push_back(*p);
   };
   alloc(&v.AII, nsi * mI * mI);
@@ -399,7 +420,7 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
   v.status = st;
 
   // per-slab pointer arrays for the interior elimination
-  std::vector<double*> pAII, pAIV, pAVI, pW, pC, pbI, pgI, pcI, pxVs, pxI;
+  std::vector<T*> pAII, pAIV, pAVI, pW, pC, pbI, pgI, pcI, pxVs, pxI;
   for (long long s = 0; s < nsi; ++s) {
     pAII.push_back(v.AII + s * mI * mI);
     pAIV.push_back(v.AIV + s * mI * 2 * mV);
@@ -425,11 +446,11 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
 
   // cyclic-reduction schedule over the nsv vertex planes
   levels.clear();
-  auto blk = [&](double* base, long long i) { return base + i * mV * mV; };
+  auto blk = [&](T* base, long long i) { return base + i * mV * mV; };
   for (long long st_ = 1; st_ < nsv; st_ *= 2) {
-    CrLevel lv;
+    CrLevel<T> lv;
     lv.stride = st_;
-    std::vector<double*> oD, oL, oU, oGL, oGU, ob, ot;
+    std::vector<T*> oD, oL, oU, oGL, oGU, ob, ot;
     for (long long i = st_; i < nsv; i += 2 * st_) {
       oD.push_back(blk(v.D, i));
       oL.push_back(blk(v.L, i));
@@ -448,8 +469,8 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
     lv.ob = upload_ptrs(ob, owned);
     lv.ot = upload_ptrs(ot, owned);
     // even j with a left neighbour j - st (always odd) and/or a right neighbour j + st
-    std::vector<double*> lD, lL, lGU, lGL, lT, lb, lt;
-    std::vector<double*> rD, rU, rGL, rGU, rT, rb, rt;
+    std::vector<T*> lD, lL, lGU, lGL, lT, lb, lt;
+    std::vector<T*> rD, rU, rGL, rGU, rT, rb, rt;
     for (long long j = 0; j < nsv; j += 2 * st_) {
       if (j - st_ >= 0) {
         lD.push_back(blk(v.D, j));
@@ -472,14 +493,14 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
     }
     lv.n_left = (int)lD.size();
     lv.n_right = (int)rD.size();
-    std::vector<double*> sL, sU;
+    std::vector<T*> sL, sU;
     for (int q = 0; q < lv.n_left; ++q) {
-      double* p = nullptr;
+      T* p = nullptr;
       alloc(&p, mV * mV);
       sL.push_back(p);
     }
     for (int q = 0; q < lv.n_right; ++q) {
-      double* p = nullptr;
+      T* p = nullptr;
       alloc(&p, mV * mV);
       sU.push_back(p);
     }
@@ -500,7 +521,7 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
     lv.rb = upload_ptrs(rb, owned);
     lv.rt = upload_ptrs(rt, owned);
     // back substitution of the odd blocks: x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}
-    std::vector<double*> bx, bGL, bxl, bGU, bxr, bx2, bt;
+    std::vector<T*> bx, bGL, bxl, bGU, bxr, bx2, bt;
     for (long long i = st_; i < nsv; i += 2 * st_) {
       bx.push_back(xV + i * mV);
       bt.push_back(tV + i * mV);
@@ -522,121 +543,137 @@ void CoarseSolver::init(const Geom& geom, bool pure_dirichlet) {
     lv.bx2 = upload_ptrs(bx2, owned);
     levels.push_back(lv);
   }
-  std::vector<double*> top{v.D}, topb{bV}, topx{xV};
+  std::vector<T*> top{v.D}, topb{bV}, topx{xV};
   d_top = upload_ptrs(top, owned);
   d_topb = upload_ptrs(topb, owned);
   d_topx = upload_ptrs(topx, owned);
 }
 
-void CoarseSolver::release() {
+template <typename T>
+void CoarseSolver<T>::release() {
   for (void* p : owned) cudaFree(p);
   owned.clear();
 }
 
-static void gj(int m, double* const* A, int batch, int* status, cudaStream_t st) {
+template <typename T>
+static void gj(int m, T* const* A, int batch, int* status, cudaStream_t st) {
   if (batch <= 0 || m <= 0) return;
-  const size_t sm = sizeof(double) * m + sizeof(int) * m;
-  if (sm > 48 * 1024)  // a per-function maximum: only ever raised above the 48 KB default
-    STG_CUDA_OK(cudaFuncSetAttribute(bgj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  bgj_kernel<<<batch, 1024, sm, st>>>(m, A, status);
+  const size_t tail = sizeof(T) * m + sizeof(int) * m;
+  const size_t full = sizeof(T) * (size_t)m * m + tail;
+  if (full <= 220 * 1024) {  // the whole matrix in shared memory
+    STG_CUDA_OK(cudaFuncSetAttribute(bgj_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(full, 48 * 1024)));
+    bgj_kernel<T, true><<<batch, 1024, full, st>>>(m, A, status);
+  } else {
+    STG_CUDA_OK(cudaFuncSetAttribute(bgj_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(tail, 48 * 1024)));
+    bgj_kernel<T, false><<<batch, 1024, tail, st>>>(m, A, status);
+  }
   STG_LAUNCH_OK();
 }
 
-static void gemm(int M, int N, int K, double alpha, const double* const* A, int lda, const double* const* B, int ldb,
-                 double beta, double* const* C, int ldc, int batch, cudaStream_t st) {
+template <typename T>
+static void gemm(int M, int N, int K, T alpha, const T* const* A, int lda, const T* const* B, int ldb, T beta,
+                 T* const* C, int ldc, int batch, cudaStream_t st) {
   if (batch <= 0) return;
   dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
-  bgemm_kernel<<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  bgemm_kernel<T><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   STG_LAUNCH_OK();
 }
 
-static void gemv(int M, int N, double alpha, const double* const* A, int lda, const double* const* x, double beta,
-                 double* const* y, int batch, cudaStream_t st) {
+template <typename T>
+static void gemv(int M, int N, T alpha, const T* const* A, int lda, const T* const* x, T beta, T* const* y,
+                 int batch, cudaStream_t st) {
   if (batch <= 0) return;
   dim3 grid((M + 7) / 8, batch);
-  bgemv_kernel<<<grid, 256, 0, st>>>(M, N, alpha, A, lda, x, beta, y);
+  bgemv_kernel<T><<<grid, 256, 0, st>>>(M, N, alpha, A, lda, x, beta, y);
   STG_LAUNCH_OK();
 }
 
-void CoarseSolver::factor(const int* rowptr, const int* colidx, const double* vv, const double* vp, const double* pv,
-                          cudaStream_t st) {
+template <typename T>
+void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double* vv, const double* vp,
+                             const double* pv, cudaStream_t st) {
   const Geom& g = v.g;
   const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
   STG_CUDA_OK(cudaMemsetAsync(v.status, 0, sizeof(int) * 2, st));
-  STG_CUDA_OK(cudaMemsetAsync(v.AII, 0, sizeof(double) * nsi * mI * mI, st));
-  STG_CUDA_OK(cudaMemsetAsync(v.AIV, 0, sizeof(double) * nsi * mI * 2 * mV, st));
-  STG_CUDA_OK(cudaMemsetAsync(v.AVI, 0, sizeof(double) * nsi * 2 * mV * mI, st));
-  STG_CUDA_OK(cudaMemsetAsync(v.D, 0, sizeof(double) * nsv * mV * mV, st));
-  STG_CUDA_OK(cudaMemsetAsync(v.L, 0, sizeof(double) * nsv * mV * mV, st));
-  STG_CUDA_OK(cudaMemsetAsync(v.U, 0, sizeof(double) * nsv * mV * mV, st));
-  extract_vv<<<grid_for(g.nvel, 128), 128, 0, st>>>(v, rowptr, colidx, vv);
+  STG_CUDA_OK(cudaMemsetAsync(v.AII, 0, sizeof(T) * nsi * mI * mI, st));
+  STG_CUDA_OK(cudaMemsetAsync(v.AIV, 0, sizeof(T) * nsi * mI * 2 * mV, st));
+  STG_CUDA_OK(cudaMemsetAsync(v.AVI, 0, sizeof(T) * nsi * 2 * mV * mI, st));
+  STG_CUDA_OK(cudaMemsetAsync(v.D, 0, sizeof(T) * nsv * mV * mV, st));
+  STG_CUDA_OK(cudaMemsetAsync(v.L, 0, sizeof(T) * nsv * mV * mV, st));
+  STG_CUDA_OK(cudaMemsetAsync(v.U, 0, sizeof(T) * nsv * mV * mV, st));
+  extract_vv<T><<<grid_for(g.nvel, 128), 128, 0, st>>>(v, rowptr, colidx, vv);
   STG_LAUNCH_OK();
   const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * (g.dim + 1);
-  extract_vp<<<grid_for(nvp, 256), 256, 0, st>>>(v, vp, pv);
+  extract_vp<T><<<grid_for(nvp, 256), 256, 0, st>>>(v, vp, pv);
   STG_LAUNCH_OK();
-  pin_diag<<<1, 32, 0, st>>>(v);
+  pin_diag<T><<<1, 32, 0, st>>>(v);
   STG_LAUNCH_OK();
   // interiors: A_II^{-1}, W = A_II^{-1} A_IV, C = A_VI W, S = A_VV - C (scattered)
-  gj((int)mI, d_AII, (int)nsi, v.status, st);
-  gemm((int)mI, (int)(2 * mV), (int)mI, 1.0, d_AII, (int)mI, d_AIV, (int)(2 * mV), 0.0, d_W, (int)(2 * mV), (int)nsi,
-       st);
-  gemm((int)(2 * mV), (int)(2 * mV), (int)mI, 1.0, d_AVI, (int)mI, d_W, (int)(2 * mV), 0.0, d_C, (int)(2 * mV),
-       (int)nsi, st);
-  schur_combine<<<grid_for(nsv * mV * mV, 256), 256, 0, st>>>(v, C);
+  gj<T>((int)mI, d_AII, (int)nsi, v.status, st);
+  const T one = 1, zero = 0, mone = -1;
+  gemm<T>((int)mI, (int)(2 * mV), (int)mI, one, d_AII, (int)mI, d_AIV, (int)(2 * mV), zero, d_W, (int)(2 * mV),
+          (int)nsi, st);
+  gemm<T>((int)(2 * mV), (int)(2 * mV), (int)mI, one, d_AVI, (int)mI, d_W, (int)(2 * mV), zero, d_C, (int)(2 * mV),
+          (int)nsi, st);
+  schur_combine<T><<<grid_for(nsv * mV * mV, 256), 256, 0, st>>>(v, C);
   STG_LAUNCH_OK();
   // block cyclic reduction of the vertex-plane system
   const int m = (int)mV;
-  for (const CrLevel& lv : levels) {
-    gj(m, lv.oD, lv.n_odd, v.status, st);
-    gemm(m, m, m, 1.0, lv.oD, m, lv.oL, m, 0.0, lv.oGL, m, lv.n_odd, st);
-    gemm(m, m, m, 1.0, lv.oD, m, lv.oU, m, 0.0, lv.oGU, m, lv.n_odd, st);
+  for (const auto& lv : levels) {
+    gj<T>(m, lv.oD, lv.n_odd, v.status, st);
+    gemm<T>(m, m, m, one, lv.oD, m, lv.oL, m, zero, lv.oGL, m, lv.n_odd, st);
+    gemm<T>(m, m, m, one, lv.oD, m, lv.oU, m, zero, lv.oGU, m, lv.n_odd, st);
     // D_j -= L_j GU_{j-st} + U_j GL_{j+st}
-    gemm(m, m, m, -1.0, lv.lL, m, lv.lGU, m, 1.0, lv.lD, m, lv.n_left, st);
-    gemm(m, m, m, -1.0, lv.rU, m, lv.rGL, m, 1.0, lv.rD, m, lv.n_right, st);
+    gemm<T>(m, m, m, mone, lv.lL, m, lv.lGU, m, one, lv.lD, m, lv.n_left, st);
+    gemm<T>(m, m, m, mone, lv.rU, m, lv.rGL, m, one, lv.rD, m, lv.n_right, st);
     // L_j <- -L_j GL_{j-st}; U_j <- -U_j GU_{j+st} (through TL)
     // the solve needs this level's L_j, U_j: keep copies before they are replaced
-    copy_ptrs(lv.lL, lv.sL, lv.n_left, (long long)m * m, st);
-    copy_ptrs(lv.rU, lv.sU, lv.n_right, (long long)m * m, st);
-    gemm(m, m, m, -1.0, lv.lL, m, lv.lGL, m, 0.0, lv.lT, m, lv.n_left, st);
-    copy_ptrs(lv.lT, lv.lL, lv.n_left, (long long)m * m, st);
-    gemm(m, m, m, -1.0, lv.rU, m, lv.rGU, m, 0.0, lv.rT, m, lv.n_right, st);
-    copy_ptrs(lv.rT, lv.rU, lv.n_right, (long long)m * m, st);
+    copy_ptrs<T>(lv.lL, lv.sL, lv.n_left, (long long)m * m, st);
+    copy_ptrs<T>(lv.rU, lv.sU, lv.n_right, (long long)m * m, st);
+    gemm<T>(m, m, m, mone, lv.lL, m, lv.lGL, m, zero, lv.lT, m, lv.n_left, st);
+    copy_ptrs<T>(lv.lT, lv.lL, lv.n_left, (long long)m * m, st);
+    gemm<T>(m, m, m, mone, lv.rU, m, lv.rGU, m, zero, lv.rT, m, lv.n_right, st);
+    copy_ptrs<T>(lv.rT, lv.rU, lv.n_right, (long long)m * m, st);
   }
-  gj(m, d_top, 1, v.status, st);
+  gj<T>(m, d_top, 1, v.status, st);
 }
 
-void CoarseSolver::solve(const double* b, double* x, cudaStream_t st) {
+template <typename T>
+void CoarseSolver<T>::solve(const double* b, double* x, cudaStream_t st) {
   const Geom& g = v.g;
   const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
-  STG_CUDA_OK(cudaMemsetAsync(bV, 0, sizeof(double) * nsv * mV, st));  // unused slots stay zero
-  gather_rhs<<<grid_for(g.N, 256), 256, 0, st>>>(v, b, bV, bI);
+  STG_CUDA_OK(cudaMemsetAsync(bV, 0, sizeof(T) * nsv * mV, st));  // unused slots stay zero
+  gather_rhs<T><<<grid_for(g.N, 256), 256, 0, st>>>(v, b, bV, bI);
   STG_LAUNCH_OK();
-  gemv((int)mI, (int)mI, 1.0, d_AII, (int)mI, d_bI, 0.0, d_gI, (int)nsi, st);
-  gemv((int)(2 * mV), (int)mI, 1.0, d_AVI, (int)mI, d_gI, 0.0, d_cI, (int)nsi, st);
-  rhs_combine<<<grid_for(nsv * mV, 256), 256, 0, st>>>(v, cI, bV);
+  const T one = 1, zero = 0, mone = -1;
+  gemv<T>((int)mI, (int)mI, one, d_AII, (int)mI, d_bI, zero, d_gI, (int)nsi, st);
+  gemv<T>((int)(2 * mV), (int)mI, one, d_AVI, (int)mI, d_gI, zero, d_cI, (int)nsi, st);
+  rhs_combine<T><<<grid_for(nsv * mV, 256), 256, 0, st>>>(v, cI, bV);
   STG_LAUNCH_OK();
   const int m = (int)mV;
-  for (const CrLevel& lv : levels) {
-    gemv(m, m, 1.0, lv.oD, m, lv.ob, 0.0, lv.ot, lv.n_odd, st);
-    gemv(m, m, -1.0, lv.sL, m, lv.lt, 1.0, lv.lb, lv.n_left, st);
-    gemv(m, m, -1.0, lv.sU, m, lv.rt, 1.0, lv.rb, lv.n_right, st);
+  for (const auto& lv : levels) {
+    gemv<T>(m, m, one, lv.oD, m, lv.ob, zero, lv.ot, lv.n_odd, st);
+    gemv<T>(m, m, mone, lv.sL, m, lv.lt, one, lv.lb, lv.n_left, st);
+    gemv<T>(m, m, mone, lv.sU, m, lv.rt, one, lv.rb, lv.n_right, st);
   }
-  gemv(m, m, 1.0, d_top, m, d_topb, 0.0, d_topx, 1, st);
+  gemv<T>(m, m, one, d_top, m, d_topb, zero, d_topx, 1, st);
   for (auto it = levels.rbegin(); it != levels.rend(); ++it) {
-    const CrLevel& lv = *it;
-    copy_ptrs(lv.bt, lv.bx, lv.n_odd, mV, st);
-    gemv(m, m, -1.0, lv.bGL, m, lv.bxl, 1.0, lv.bx, lv.n_odd, st);
-    gemv(m, m, -1.0, lv.bGU, m, lv.bxr, 1.0, lv.bx2, lv.n_bright, st);
+    const auto& lv = *it;
+    copy_ptrs<T>(lv.bt, lv.bx, lv.n_odd, mV, st);
+    gemv<T>(m, m, mone, lv.bGL, m, lv.bxl, one, lv.bx, lv.n_odd, st);
+    gemv<T>(m, m, mone, lv.bGU, m, lv.bxr, one, lv.bx2, lv.n_bright, st);
   }
   // x_I = g_I - W [x_V,s ; x_V,s+1]
-  copy_kernel<<<grid_for(nsi * mI, 256), 256, 0, st>>>(nsi * mI, gI, xI);
+  copy_kernel<T><<<grid_for(nsi * mI, 256), 256, 0, st>>>(nsi * mI, gI, xI);
   STG_LAUNCH_OK();
-  gemv((int)mI, (int)(2 * mV), -1.0, d_W, (int)(2 * mV), d_xVs, 1.0, d_xI, (int)nsi, st);
-  scatter_sol<<<grid_for(g.N, 256), 256, 0, st>>>(v, xV, xI, x);
+  gemv<T>((int)mI, (int)(2 * mV), mone, d_W, (int)(2 * mV), d_xVs, one, d_xI, (int)nsi, st);
+  scatter_sol<T><<<grid_for(g.N, 256), 256, 0, st>>>(v, xV, xI, x);
   STG_LAUNCH_OK();
 }
 
-int CoarseSolver::read_status(cudaStream_t st) {
+template <typename T>
+int CoarseSolver<T>::read_status(cudaStream_t st) {
   int h[2] = {0, 0};
   STG_CUDA_OK(cudaMemcpyAsync(h, v.status, sizeof(h), cudaMemcpyDeviceToHost, st));
   STG_CUDA_OK(cudaStreamSynchronize(st));
@@ -645,19 +682,24 @@ int CoarseSolver::read_status(cudaStream_t st) {
 }
 
 namespace {
-__global__ void copy_ptrs_kernel(const double* const* src, double* const* dst, long long n) {
-  const double* s = src[blockIdx.y];
-  double* d = dst[blockIdx.y];
+template <typename T>
+__global__ void copy_ptrs_kernel(const T* const* src, T* const* dst, long long n) {
+  const T* s = src[blockIdx.y];
+  T* d = dst[blockIdx.y];
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     d[t] = s[t];
 }
 }  // namespace
 
-void copy_ptrs(double* const* src, double* const* dst, int batch, long long n, cudaStream_t st) {
+template <typename T>
+void copy_ptrs(T* const* src, T* const* dst, int batch, long long n, cudaStream_t st) {
   if (batch <= 0) return;
   dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), batch);
-  copy_ptrs_kernel<<<grid, 256, 0, st>>>(src, dst, n);
+  copy_ptrs_kernel<T><<<grid, 256, 0, st>>>(src, dst, n);
   STG_LAUNCH_OK();
 }
+
+template struct CoarseSolver<double>;
+template struct CoarseSolver<float>;
 
 }  // namespace stg

@@ -1,5 +1,5 @@
 // Coarse-level direct solver: interior elimination per cell column plus block
-// cyclic reduction over the vertex planes (FP64).  See coarse.cu.
+// cyclic reduction over the vertex planes, in precision T.  See coarse.cu.
 #pragma once
 
 #include <vector>
@@ -8,43 +8,44 @@
 
 namespace stg {
 
+template <typename T>
 struct CoarseView {
   Geom g;
   int pin, nsi, nsv, mV, mI;
-  double *AII, *AIV, *AVI, *D, *L, *U;
+  T *AII, *AIV, *AVI, *D, *L, *U;
   int* status;  // [0]: 1 + first singular block, [1]: unexpected coupling
 };
 
+template <typename T>
 struct CrLevel {
   long long stride;
   int n_odd, n_left, n_right, n_bright;
-  double **oD, **oL, **oU, **oGL, **oGU, **ob, **ot;
-  double **lD, **lL, **lGU, **lGL, **lT, **lb, **lt, **sL;
-  double **rD, **rU, **rGL, **rGU, **rT, **rb, **rt, **sU;
-  double **bx, **bt, **bGL, **bxl, **bGU, **bxr, **bx2;
+  T **oD, **oL, **oU, **oGL, **oGU, **ob, **ot;
+  T **lD, **lL, **lGU, **lGL, **lT, **lb, **lt, **sL;
+  T **rD, **rU, **rGL, **rGU, **rT, **rb, **rt, **sU;
+  T **bx, **bt, **bGL, **bxl, **bGU, **bxr, **bx2;
 };
 
+template <typename T>
 struct CoarseSolver {
-  CoarseView v{};
-  double *W = nullptr, *C = nullptr, *GL = nullptr, *GU = nullptr, *TL = nullptr;
-  double *bV = nullptr, *tV = nullptr, *xV = nullptr, *bI = nullptr, *gI = nullptr, *cI = nullptr, *xI = nullptr;
-  double **d_AII = nullptr, **d_AIV = nullptr, **d_AVI = nullptr, **d_W = nullptr, **d_C = nullptr;
-  double **d_bI = nullptr, **d_gI = nullptr, **d_cI = nullptr, **d_xVs = nullptr, **d_xI = nullptr;
-  double **d_top = nullptr, **d_topb = nullptr, **d_topx = nullptr;
-  std::vector<CrLevel> levels;
+  CoarseView<T> v{};
+  T *W = nullptr, *C = nullptr, *GL = nullptr, *GU = nullptr, *TL = nullptr;
+  T *bV = nullptr, *tV = nullptr, *xV = nullptr, *bI = nullptr, *gI = nullptr, *cI = nullptr, *xI = nullptr;
+  T **d_AII = nullptr, **d_AIV = nullptr, **d_AVI = nullptr, **d_W = nullptr, **d_C = nullptr;
+  T **d_bI = nullptr, **d_gI = nullptr, **d_cI = nullptr, **d_xVs = nullptr, **d_xI = nullptr;
+  T **d_top = nullptr, **d_topb = nullptr, **d_topx = nullptr;
+  std::vector<CrLevel<T>> levels;
   std::vector<void*> owned;
 
   void init(const Geom& g, bool pure_dirichlet);
   void release();
-  // factor J_0 given in the internal level layout (FP64)
+  // factor J_0 given in the internal level layout (FP64 operator), factors stored in T
   void factor(const int* rowptr, const int* colidx, const double* vv, const double* vp, const double* pv,
               cudaStream_t st);
-  // x = J_0^{-1} b, both in the internal level layout (FP64)
+  // x = J_0^{-1} b, both FP64 in the internal level layout, arithmetic in T
   void solve(const double* b, double* x, cudaStream_t st);
   // 0 = ok, > 0: 1 + singular block, -1: coupling outside the block structure (synchronises)
   int read_status(cudaStream_t st);
 };
-
-void copy_ptrs(double* const* src, double* const* dst, int batch, long long n, cudaStream_t st);
 
 }  // namespace stg
