@@ -83,7 +83,7 @@ typedef struct {
   int use_graph;           /* capture the V-cycle in a CUDA graph (default 1)         */
   int coarse_refine;       /* FP32 V-cycle only: the coarse factors are FP32 and each  */
                            /* coarse solve adds this many steps of iterative          */
-                           /* refinement with FP64 residuals (default 2); the FP64    */
+                           /* refinement with FP64 residuals (default 1); the FP64    */
                            /* V-cycle uses FP64 coarse factors                        */
 } stg_options;
 

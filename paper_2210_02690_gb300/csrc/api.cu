@@ -176,6 +176,7 @@ struct stg_ctx {
   double *cb64 = nullptr, *cx64 = nullptr, *cr64 = nullptr, *cd64 = nullptr;
   int* status = nullptr;
   void* inv_scratch = nullptr;
+  int* inv_flags = nullptr;  // per patch: redo with pivoting
   // FGMRES (finest level, internal layout, FP64)
   double *V = nullptr, *Z = nullptr, *wv = nullptr, *rv = nullptr, *partial = nullptr, *hd = nullptr;
   double *vin = nullptr, *vout = nullptr, *tmp_a = nullptr, *tmp_b = nullptr;
@@ -264,13 +265,15 @@ void linearise(stg_ctx* c, const double* w_cabi) {
     // FP32/BF16 factors are computed in FP32 on the equilibrated J_K; FP64 factors in FP64
     const int cf32 = fp != STG_F64 ? 1 : 0;
     if (fp == STG_F64)
-      invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, (double*)L.jinv, 0, c->status, c->inv_scratch, c->st);
+      invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, nullptr, nullptr, nullptr, (double*)L.jinv, 0, c->status, c->inv_scratch,
+                             c->inv_flags, c->st);
     else if (fp == STG_F32)
-      invert_patches<float>(L.g, L.rowptr, L.vv, L.vp, L.pv, (float*)L.jinv, cf32, c->status, c->inv_scratch,
-                            c->st);
+      invert_patches<float>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32, (float*)L.jinv, cf32, c->status, c->inv_scratch,
+                            c->inv_flags, c->st);
     else
-      invert_patches<__nv_bfloat16>(L.g, L.rowptr, L.vv, L.vp, L.pv, (__nv_bfloat16*)L.jinv, cf32, c->status,
-                                    c->inv_scratch, c->st);
+      invert_patches<__nv_bfloat16>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32,
+                                    (__nv_bfloat16*)L.jinv, cf32, c->status,
+                                    c->inv_scratch, c->inv_flags, c->st);
   }
   LevelBufs& C0 = c->lv[0];
   if (vc64(c))
@@ -624,7 +627,7 @@ stg_status stg_options_default(stg_options* o) {
   o->gmres_rtol = 1e-8;
   o->gmres_atol = 0.0;
   o->use_graph = 1;
-  o->coarse_refine = 2;
+  o->coarse_refine = 1;
   return STG_OK;
 }
 
@@ -667,7 +670,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
         L.pv32 = dalloc<float>(c, nvp);
       }
       L.w = dalloc<double>(c, g.nvel);
-      L.asm_tab = dalloc<double>(c, assemble_table_doubles(g.dim));
+      L.asm_tab = dalloc<double>(c, assemble_table_doubles(g.dim, k));
       L.b = dalloc<char>(c, (long long)vts * g.N);
       L.x = dalloc<char>(c, (long long)vts * g.N);
       L.r = dalloc<char>(c, (long long)vts * g.N);
@@ -681,6 +684,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       }
     }
     if (scratch) c->inv_scratch = dalloc<char>(c, (long long)scratch);
+    c->inv_flags = dalloc<int>(c, c->lv.back().g.n_cells);
     if (f64)
       c->coarse64.init(c->lv[0].g, c->pure_dirichlet);
     else

@@ -108,10 +108,15 @@ __device__ __forceinline__ double face_point(const Geom& g, int e0, int s0, int 
   return wt;
 }
 
-// Layout of the per-level table written by element_constants.
+// Layout of the per-level table written by element_constants:
+//   [mass NL^2 | 4^d face classes x (vv ND^2, vp ND(d+1), pv (d+1)ND) | phi NQ NL | dphi NQ NL d |
+//    qwd NQ | pp NQ NL NL], pp[q][i][j] = W_q |det| phi_i(q) phi_j(q).
 __host__ __device__ __forceinline__ long long tab_class_size(int dim, int nloc) {
   const long long nd = (long long)nloc * dim;
   return nd * nd + 2 * nd * (dim + 1);
+}
+__host__ __device__ __forceinline__ long long tab_extra_offset(int dim, int nloc) {
+  return (long long)nloc * nloc + (1LL << (2 * dim)) * tab_class_size(dim, nloc);
 }
 
 // w-independent element matrices, one CTA per face class:
@@ -128,13 +133,29 @@ __global__ void __launch_bounds__(256) element_constants(Geom g, AsmCoef cf, dou
   const unsigned faces = blockIdx.x;
   cell_tables<DIM, NQ, NL>(g, phi, dphi, qwd);
   __syncthreads();
-  if (faces == 0)
+  if (faces == 0) {
     for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) {
       const int i = t / NL, j = t % NL;
       double m = 0.0;
       for (int q = 0; q < NQ; ++q) m += qwd[q] * phi[q][i] * phi[q][j];
       tab[t] = m;
     }
+    double* x = tab + tab_extra_offset(DIM, NL);
+    double* xphi = x;
+    double* xdphi = xphi + NQ * NL;
+    double* xqwd = xdphi + NQ * NL * DIM;
+    double* xpp = xqwd + NQ;
+    for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x) {
+      const int q = t / NL, i = t % NL;
+      xphi[t] = phi[q][i];
+      for (int e = 0; e < DIM; ++e) xdphi[t * DIM + e] = dphi[q][i][e];
+    }
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) xqwd[q] = qwd[q];
+    for (int t = threadIdx.x; t < NQ * NL * NL; t += blockDim.x) {
+      const int q = t / (NL * NL), i = (t / NL) % NL, j = t % NL;
+      xpp[t] = qwd[q] * phi[q][i] * phi[q][j];
+    }
+  }
   double* base = tab + NL * NL + (long long)faces * tab_class_size(DIM, NL);
   for (int t = threadIdx.x; t < ND * ND; t += blockDim.x) {
     const int I = t / ND, J = t % ND;
@@ -198,14 +219,34 @@ __global__ void __launch_bounds__(256) element_constants(Geom g, AsmCoef cf, dou
   }
 }
 
+// K[a][cls][(i,c),(j,e)] = T_aa M_ij delta_ce + tau w_a C[cls][(i,c),(j,e)]: the w-independent
+// part of the diagonal time block a for face class cls.
+template <int DIM>
+__global__ void diag_blocks(Geom g, TimeData td, AsmCoef cf, const double* __restrict__ tab, double* __restrict__ K) {
+  constexpr int NL = Pow3<DIM>::v;
+  constexpr int ND = NL * DIM;
+  const int ncls = 1 << (2 * DIM);
+  const long long per = (long long)ND * ND;
+  const long long total = (long long)g.nt * ncls * per;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t / (ncls * per));
+    const int cls = (int)((t / per) % ncls);
+    const int I = (int)((t % per) / ND), J = (int)(t % ND);
+    const int i = I / DIM, c = I % DIM, j = J / DIM, e = J % DIM;
+    const double* cvv = tab + NL * NL + (long long)cls * tab_class_size(DIM, NL);
+    K[t] = (c == e ? td.T[a][a] * tab[i * NL + j] : 0.0) + cf.tau * td.w[a] * cvv[t % per];
+  }
+}
+
 // Per-cell assembly: the convection (and Newton) matrices from w_a at the cell's
 // nodes, combined with the class constants, the time matrix T_ab and the factor
 // tau w_a, added into the BCSR blocks of the cell's node pairs.
 template <int DIM>
 __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
                                                       const double* __restrict__ w, const int* __restrict__ rowptr,
-                                                      const double* __restrict__ tab, double* __restrict__ vv,
-                                                      double* __restrict__ vp, double* __restrict__ pv) {
+                                                      const double* __restrict__ tab, const double* __restrict__ K,
+                                                      double* __restrict__ vv, double* __restrict__ vp,
+                                                      double* __restrict__ pv) {
   constexpr int NQ = Pow3<DIM>::v;
   constexpr int NL = NQ;
   constexpr int ND = NL * DIM;
@@ -218,6 +259,10 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
   __shared__ double gw[NTMAX][NQ][DIM][DIM];
   __shared__ double cm[NTC][NL][NL];
   __shared__ double nm[NTC][NL][NL][DIM][DIM];
+  __shared__ double uq[NTC][NQ][NL];             // w_a . grad phi_j at q
+  __shared__ double pq[DIM == 2 ? NQ : 1][DIM == 2 ? NL : 1];  // W_q |det| phi_i(q)
+  __shared__ double ppq[DIM == 2 ? NQ : 1][DIM == 2 ? NL * NL : 1];
+  __shared__ int slots[NL * NL];
 
   const int nt = g.nt, NV = g.NV;
   int cx, cy, cz;
@@ -230,7 +275,26 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
   const double* cvp = cvv + (long long)ND * ND;
   const double* cpv = cvp + (long long)ND * (DIM + 1);
 
-  cell_tables<DIM, NQ, NL>(g, phi, dphi, qwd);
+  {
+    const double* x = tab + tab_extra_offset(DIM, NL);
+    for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x) {
+      const int q = t / NL, i = t % NL;
+      phi[q][i] = x[t];
+      for (int e = 0; e < DIM; ++e) dphi[q][i][e] = x[NQ * NL + t * DIM + e];
+    }
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) qwd[q] = x[NQ * NL * (1 + DIM) + q];
+    if (DIM == 2) {
+      for (int t = threadIdx.x; t < NQ * NL * NL; t += blockDim.x)
+        ppq[t / (NL * NL)][t % (NL * NL)] = x[NQ * NL * (1 + DIM) + NQ + t];
+      for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x)
+        pq[t / NL][t % NL] = x[NQ * NL * (1 + DIM) + t / NL] * x[t];
+    }
+  }
+  for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) {
+    const int i = t / NL, j = t % NL;
+    slots[t] = (int)bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9, 2 * cx + j % 3,
+                              2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+  }
   __syncthreads();
   for (int t = threadIdx.x; t < nt * NQ * DIM; t += blockDim.x) {
     const int a = t / (NQ * DIM), q = (t / DIM) % NQ, c = t % DIM;
@@ -246,41 +310,54 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
   }
   __syncthreads();
   if (DIM == 2) {
-    // (w_a . grad phi_j, phi_i) and phi_i phi_j d_e w_a,c for every node pair
+    // u_j(q) = w_a(q) . grad phi_j(q)
+    for (int t = threadIdx.x; t < nt * NQ * NL; t += blockDim.x) {
+      const int a = t / (NQ * NL), q = (t / NL) % NQ, j = t % NL;
+      double u = 0.0;
+      for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
+      uq[a % NTC][q][j] = u;
+    }
+    __syncthreads();
+    // convection (w_a . grad phi_j, phi_i) = sum_q W phi_i u_j; Newton phi_i phi_j d_e w_a,c (symmetric in i, j)
     for (int t = threadIdx.x; t < nt * NL * NL; t += blockDim.x) {
       const int a = t / (NL * NL), i = (t / NL) % NL, j = t % NL;
+      const double sa = cf.tau * td.w[a];
       double conv = 0.0;
-      double nw[DIM][DIM];
-      for (int c = 0; c < DIM; ++c)
-        for (int e = 0; e < DIM; ++e) nw[c][e] = 0.0;
-      for (int q = 0; q < NQ; ++q) {
-        double u = 0.0;
-        for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
-        conv += qwd[q] * u * phi[q][i];
-        if (cf.newton) {
-          const double pp = qwd[q] * phi[q][i] * phi[q][j];
+      for (int q = 0; q < NQ; ++q) conv += pq[q][i] * uq[a % NTC][q][j];
+      cm[a % NTC][i][j] = sa * conv;
+      if (cf.newton && i <= j) {
+        double nw[DIM][DIM];
+        for (int c = 0; c < DIM; ++c)
+          for (int e = 0; e < DIM; ++e) nw[c][e] = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+          const double pp = ppq[q][i * NL + j];
           for (int c = 0; c < DIM; ++c)
             for (int e = 0; e < DIM; ++e) nw[c][e] += pp * gw[a][q][c][e];
         }
+        for (int c = 0; c < DIM; ++c)
+          for (int e = 0; e < DIM; ++e) {
+            nm[a % NTC][i][j][c][e] = sa * nw[c][e];
+            nm[a % NTC][j][i][c][e] = sa * nw[c][e];
+          }
       }
-      cm[a % NTC][i][j] = conv;
-      for (int c = 0; c < DIM; ++c)
-        for (int e = 0; e < DIM; ++e) nm[a % NTC][i][j][c][e] = nw[c][e];
     }
     __syncthreads();
   }
 
   const long long nvv = (long long)NL * NL * NV * NV;
+  const long long kper = (long long)ND * ND;
+  const int ncls = 1 << (2 * DIM);
+#pragma unroll 2
   for (long long t = threadIdx.x; t < nvv; t += blockDim.x) {
     const int s = (int)(t % NV), r = (int)((t / NV) % NV);
     const int j = (int)((t / (NV * NV)) % NL), i = (int)(t / ((long long)NV * NV * NL));
     const int a = r / DIM, c = r % DIM, b = s / DIM, e = s % DIM;
-    double val = c == e ? td.T[a][b] * mass[i * NL + j] : 0.0;
+    double val;
     if (a == b) {
-      double sp = cvv[(i * DIM + c) * ND + j * DIM + e];
+      val = K[((long long)a * ncls + cls) * kper + (i * DIM + c) * ND + j * DIM + e];
       if (DIM == 2) {
-        if (c == e) sp += cm[a % NTC][i][j];
-        if (cf.newton) sp += nm[a % NTC][i][j][c][e];
+        if (c == e) val += cm[a % NTC][i][j];
+        if (cf.newton) val += nm[a % NTC][i][j][c][e];
       } else {
         double extra = 0.0;
         for (int q = 0; q < NQ; ++q) {
@@ -293,13 +370,12 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
           if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
           extra += qwd[q] * term;
         }
-        sp += extra;
+        val += cf.tau * td.w[a] * extra;
       }
-      val += cf.tau * td.w[a] * sp;
+    } else {
+      val = c == e ? td.T[a][b] * mass[i * NL + j] : 0.0;
     }
-    const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9, 2 * cx + j % 3,
-                                      2 * cy + (j / 3) % 3, 2 * cz + j / 9);
-    vv[slot * NV * NV + (long long)r * NV + s] += val;
+    vv[(long long)slots[i * NL + j] * NV * NV + (long long)r * NV + s] += val;
   }
 
   // velocity-pressure [cell][i][a][c][m] and pressure-velocity [cell][a][m][i][c]
@@ -316,27 +392,37 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
 
 }  // namespace
 
-long long assemble_table_doubles(int dim) {
-  const int nloc = dim == 2 ? 9 : 27;
-  return (long long)nloc * nloc + (1LL << (2 * dim)) * tab_class_size(dim, nloc);
+long long assemble_table_doubles(int dim, int k) {
+  const int nloc = dim == 2 ? 9 : 27, nq = nloc;
+  const long long nd = (long long)nloc * dim;
+  const long long base = tab_extra_offset(dim, nloc) + (long long)nq * nloc * (1 + dim) + nq + (long long)nq * nloc * nloc;
+  return base + (long long)(k + 1) * (1LL << (2 * dim)) * nd * nd;  // followed by K
 }
 
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                     double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st) {
   STG_CUDA_OK(cudaMemsetAsync(vv, 0, sizeof(double) * nnzb * g.NV * g.NV, st));
   const unsigned ncls = 1u << (2 * g.dim);
+  const int nloc = g.dim == 2 ? 9 : 27;
+  double* K = tab + assemble_table_doubles(g.dim, -1);
   if (g.dim == 2)
     element_constants<2><<<ncls, 256, 0, st>>>(g, cf, tab);
   else
     element_constants<3><<<ncls, 256, 0, st>>>(g, cf, tab);
   STG_LAUNCH_OK();
+  const long long nK = (long long)g.nt * ncls * nloc * g.dim * nloc * g.dim;
+  if (g.dim == 2)
+    diag_blocks<2><<<grid_for(nK, 256), 256, 0, st>>>(g, td, cf, tab, K);
+  else
+    diag_blocks<3><<<grid_for(nK, 256), 256, 0, st>>>(g, td, cf, tab, K);
+  STG_LAUNCH_OK();
   for (int col = 0; col < (1 << g.dim); ++col) {
     const long long cnt = g.coff[col + 1] - g.coff[col];
     if (cnt == 0) continue;
     if (g.dim == 2)
-      assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, vv, vp, pv);
+      assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
     else
-      assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, vv, vp, pv);
+      assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
     STG_LAUNCH_OK();
   }
 }

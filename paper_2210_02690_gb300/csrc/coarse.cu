@@ -30,7 +30,10 @@ namespace {
 
 // ---------------------------------------------------------------- batched dense kernels
 // In-place Gauss-Jordan inverse with partial pivoting; one CTA per matrix.  With
-// SMEM the matrix is copied into shared memory first (when it fits).
+// SMEM the matrix is copied into shared memory first (when it fits).  Each
+// pivot step has three phases separated by barriers: pivot search (one warp);
+// row interchange, saved pivot column and scaled pivot row (all threads, from
+// the values before the interchange); rank-one update of the other rows.
 template <typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) bgj_kernel(int m, T* const* As, int* status) {
   T* G = As[blockIdx.x];
@@ -39,8 +42,9 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, T* const* As, int* sta
   T* colj = SMEM ? A + (long long)m * m : reinterpret_cast<T*>(sh_raw);
   int* perm = reinterpret_cast<int*>(colj + m);
   __shared__ int s_piv, s_fail;
-  __shared__ T s_pval;
+  __shared__ T s_pval, s_ajj;
   const int tid = threadIdx.x, nth = blockDim.x;
+  const int w = tid >> 5, ln = tid & 31, nw = nth >> 5;
   if (tid == 0) s_fail = 0;
   if (SMEM)
     for (long long t = tid; t < (long long)m * m; t += nth) A[t] = G[t];
@@ -68,6 +72,7 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, T* const* As, int* sta
         s_piv = bi;
         const T pv = bi < m ? A[(long long)bi * m + j] : (T)0;
         s_pval = pv;
+        s_ajj = A[(long long)j * m + j];
         if (!(fabs(pv) > (T)0) || isinf(pv)) s_fail = 1;
         perm[j] = bi;
       }
@@ -75,22 +80,25 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, T* const* As, int* sta
     __syncthreads();
     if (s_fail) break;
     const int pr = s_piv;
-    if (pr != j)
-      for (int l = tid; l < m; l += nth) {
-        const T t = A[(long long)j * m + l];
-        A[(long long)j * m + l] = A[(long long)pr * m + l];
-        A[(long long)pr * m + l] = t;
-      }
-    __syncthreads();
-    for (int i = tid; i < m; i += nth) colj[i] = A[(long long)i * m + j];
-    __syncthreads();
     const T inv = (T)1 / s_pval;
-    for (int l = tid; l < m; l += nth) A[(long long)j * m + l] = (l == j ? (T)1 : A[(long long)j * m + l]) * inv;
+    // column j of every row before the interchange (rows j and pr swap their entries)
+    for (int i = tid; i < m; i += nth)
+      colj[i] = i == j ? s_pval : (i == pr ? s_ajj : A[(long long)i * m + j]);
+    // interchange rows j and pr, scale the new pivot row
+    for (int l = tid; l < m; l += nth) {
+      const T vj = A[(long long)j * m + l], vp = A[(long long)pr * m + l];
+      A[(long long)j * m + l] = l == j ? inv : vp * inv;
+      if (pr != j) A[(long long)pr * m + l] = vj;
+    }
     __syncthreads();
-    for (long long t = tid; t < (long long)m * m; t += nth) {
-      const int i = (int)(t / m), l = (int)(t - (long long)i * m);
-      if (i == j) continue;
-      A[t] = (l == j ? (T)0 : A[t]) - colj[i] * A[(long long)j * m + l];
+    {
+      const T* rj = A + (long long)j * m;
+      for (int i = w; i < m; i += nw) {
+        if (i == j) continue;
+        const T f = colj[i];
+        T* ri = A + (long long)i * m;
+        for (int l = ln; l < m; l += 32) ri[l] = (l == j ? (T)0 : ri[l]) - f * rj[l];
+      }
     }
     __syncthreads();
   }

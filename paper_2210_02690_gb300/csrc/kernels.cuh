@@ -23,7 +23,7 @@ struct AsmCoef {
 // ---- assembly (assemble.cu)
 void upload_fe_tables();
 // doubles of the per-level table of w-independent element matrices (mass + one set per face class)
-long long assemble_table_doubles(int dim);
+long long assemble_table_doubles(int dim, int k);
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                     double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
 
@@ -39,7 +39,8 @@ void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const M
 size_t invert_scratch_bytes(const Geom& g, int compute_f32);
 template <typename FT>
 void invert_patches(const Geom& g, const int* rowptr, const double* vv, const double* vp, const double* pv,
-                    FT* jinv, int compute_f32, int* status, void* scratch, cudaStream_t st);
+                    const float* vv32, const float* vp32, const float* pv32, FT* jinv, int compute_f32, int* status,
+                    void* scratch, int* flags, cudaStream_t st);
 
 // One colour phase of the smoother: y_K = J_K^{-1} R_K r for all cells of colour
 // `colour`; accumulate (averaged mode: z += y) or apply (coloured mode: z += omega y).

@@ -9,7 +9,7 @@
 namespace stg {
 namespace {
 
-constexpr int kDotBlocks = 304;  // 2 x 152 SMs
+constexpr int kDotBlocks = 1216;  // 8 x 152 SMs
 constexpr int kMaxVec = 32;
 
 __global__ void __launch_bounds__(256) multi_dot_partial(long long n, int m, const double* __restrict__ V,
@@ -18,7 +18,15 @@ __global__ void __launch_bounds__(256) multi_dot_partial(long long n, int m, con
   double acc[kMaxVec];
 #pragma unroll
   for (int i = 0; i < kMaxVec; ++i) acc[i] = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; t + stride < n; t += 2 * stride) {  // two independent elements per pass
+    const double w0 = w[t], w1 = w[t + stride];
+#pragma unroll
+    for (int i = 0; i < kMaxVec; ++i)
+      if (i < m) acc[i] += V[i * ldv + t] * w0 + V[i * ldv + t + stride] * w1;
+  }
+  for (; t < n; t += stride) {
     const double wt = w[t];
 #pragma unroll
     for (int i = 0; i < kMaxVec; ++i)

@@ -15,10 +15,12 @@ namespace stg {
 namespace {
 
 // Coarse node indices and weights feeding fine node index f along one direction.
-__device__ __forceinline__ int prolong_1d(int f, int* idx, double* w) {
+// The weights are exact in binary, so the transfers run in the vector precision.
+template <typename W>
+__device__ __forceinline__ int prolong_1d(int f, int* idx, W* w) {
   if (!(f & 1)) {
     idx[0] = f >> 1;
-    w[0] = 1.0;
+    w[0] = (W)1;
     return 1;
   }
   const int cc = f >> 2;
@@ -26,36 +28,37 @@ __device__ __forceinline__ int prolong_1d(int f, int* idx, double* w) {
   idx[1] = 2 * cc + 1;
   idx[2] = 2 * cc + 2;
   if ((f & 3) == 1) {
-    w[0] = 0.375;
-    w[1] = 0.75;
-    w[2] = -0.125;
+    w[0] = (W)0.375;
+    w[1] = (W)0.75;
+    w[2] = (W)-0.125;
   } else {
-    w[0] = -0.125;
-    w[1] = 0.75;
-    w[2] = 0.375;
+    w[0] = (W)-0.125;
+    w[1] = (W)0.75;
+    w[2] = (W)0.375;
   }
   return 3;
 }
 
 // Fine node indices and weights of row c of P^T along one direction (nnf fine nodes).
-__device__ __forceinline__ int restrict_1d(int c, int nnf, int* idx, double* w) {
+template <typename W>
+__device__ __forceinline__ int restrict_1d(int c, int nnf, int* idx, W* w) {
   int n = 0;
-  auto add = [&](int f, double wt) {
+  auto add = [&](int f, W wt) {
     if (f >= 0 && f < nnf) {
       idx[n] = f;
       w[n] = wt;
       ++n;
     }
   };
-  add(2 * c, 1.0);
+  add(2 * c, (W)1);
   if (c & 1) {
-    add(2 * c - 1, 0.75);
-    add(2 * c + 1, 0.75);
+    add(2 * c - 1, (W)0.75);
+    add(2 * c + 1, (W)0.75);
   } else {
-    add(2 * c - 1, 0.375);
-    add(2 * c + 1, 0.375);
-    add(2 * c - 3, -0.125);
-    add(2 * c + 3, -0.125);
+    add(2 * c - 1, (W)0.375);
+    add(2 * c + 1, (W)0.375);
+    add(2 * c - 3, (W)-0.125);
+    add(2 * c + 3, (W)-0.125);
   }
   return n;
 }
@@ -70,14 +73,14 @@ __global__ void prolong_vel(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __r
   const int f[3] = {(int)(node % gf.nn[0]), (int)((node / gf.nn[0]) % gf.nn[1]),
                     (int)(node / ((long long)gf.nn[0] * gf.nn[1]))};
   int ix[3][3], n[3];
-  double w[3][3];
-  for (int e = 0; e < 3; ++e) n[e] = prolong_1d(f[e], ix[e], w[e]);
-  double acc = 0.0;
+  VT w[3][3];
+  for (int e = 0; e < 3; ++e) n[e] = prolong_1d<VT>(f[e], ix[e], w[e]);
+  VT acc = 0;
   for (int c = 0; c < n[2]; ++c)
     for (int b = 0; b < n[1]; ++b)
       for (int a = 0; a < n[0]; ++a)
-        acc += w[0][a] * w[1][b] * w[2][c] * (double)xc[node_id(gc, ix[0][a], ix[1][b], ix[2][c]) * NV + v];
-  xf[t] += (VT)acc;
+        acc += w[0][a] * w[1][b] * w[2][c] * xc[node_id(gc, ix[0][a], ix[1][b], ix[2][c]) * NV + v];
+  xf[t] += acc;
 }
 
 template <typename VT>
@@ -91,14 +94,14 @@ __global__ void prolong_pres(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __
   const int f[3] = {(int)(K % gf.n[0]), (int)((K / gf.n[0]) % gf.n[1]), (int)(K / ((long long)gf.n[0] * gf.n[1]))};
   const long long Kc = cell_id(gc, f[0] >> 1, f[1] >> 1, f[2] >> 1);
   const VT* c = xc + gc.nvel + Kc * gc.NP + a * (d + 1);
-  double val;
+  VT val;
   if (m == 0) {
-    val = (double)c[0];
-    for (int e = 0; e < d; ++e) val += ((f[e] & 1) ? 0.5 : -0.5) * (double)c[e + 1];
+    val = c[0];
+    for (int e = 0; e < d; ++e) val += ((f[e] & 1) ? (VT)0.5 : (VT)-0.5) * c[e + 1];
   } else {
-    val = 0.5 * (double)c[m];
+    val = (VT)0.5 * c[m];
   }
-  xf[gf.nvel + t] += (VT)val;
+  xf[gf.nvel + t] += val;
 }
 
 template <typename VT>
@@ -111,14 +114,14 @@ __global__ void restrict_vel(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __
   const int c[3] = {(int)(node % gc.nn[0]), (int)((node / gc.nn[0]) % gc.nn[1]),
                     (int)(node / ((long long)gc.nn[0] * gc.nn[1]))};
   int ix[3][5], n[3];
-  double w[3][5];
-  for (int e = 0; e < 3; ++e) n[e] = restrict_1d(c[e], gf.nn[e], ix[e], w[e]);
-  double acc = 0.0;
+  VT w[3][5];
+  for (int e = 0; e < 3; ++e) n[e] = restrict_1d<VT>(c[e], gf.nn[e], ix[e], w[e]);
+  VT acc = 0;
   for (int z = 0; z < n[2]; ++z)
     for (int y = 0; y < n[1]; ++y)
       for (int x = 0; x < n[0]; ++x)
-        acc += w[0][x] * w[1][y] * w[2][z] * (double)rf[node_id(gf, ix[0][x], ix[1][y], ix[2][z]) * NV + v];
-  bc[t] = (VT)acc;
+        acc += w[0][x] * w[1][y] * w[2][z] * rf[node_id(gf, ix[0][x], ix[1][y], ix[2][z]) * NV + v];
+  bc[t] = acc;
 }
 
 template <typename VT>
@@ -130,20 +133,20 @@ __global__ void restrict_pres(Geom gc, Geom gf, const VT* __restrict__ rf, VT* _
   const int q = (int)(t - K * gc.NP);
   const int a = q / (d + 1), m = q % (d + 1);
   const int c[3] = {(int)(K % gc.n[0]), (int)((K / gc.n[0]) % gc.n[1]), (int)(K / ((long long)gc.n[0] * gc.n[1]))};
-  double acc = 0.0;
+  VT acc = 0;
   const int nch = 1 << d;
   for (int o = 0; o < nch; ++o) {
     const int fx = 2 * c[0] + (o & 1), fy = d > 1 ? 2 * c[1] + ((o >> 1) & 1) : 0;
     const int fz = d > 2 ? 2 * c[2] + ((o >> 2) & 1) : 0;
     const VT* f = rf + gf.nvel + cell_id(gf, fx, fy, fz) * gf.NP + a * (d + 1);
     if (m == 0) {
-      acc += (double)f[0];
+      acc += f[0];
     } else {
-      const double s = ((o >> (m - 1)) & 1) ? 0.5 : -0.5;
-      acc += s * (double)f[0] + 0.5 * (double)f[m];
+      const VT s = ((o >> (m - 1)) & 1) ? (VT)0.5 : (VT)-0.5;
+      acc += s * f[0] + (VT)0.5 * f[m];
     }
   }
-  bc[gc.nvel + t] = (VT)acc;
+  bc[gc.nvel + t] = acc;
 }
 
 __device__ __forceinline__ long long cabi_index(const Geom& g, long long t) {

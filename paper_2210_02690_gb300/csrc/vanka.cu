@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) op_vel_rows(Geom g, const int* __restrict
   const int r = (int)(t - node * NV);
   VT acc = 0;
   const int b0 = rowptr[node], b1 = rowptr[node + 1];
+#pragma unroll 4
   for (int blk = b0; blk < b1; ++blk) {
     const MT* vals = vv + (long long)blk * NV * NV + (long long)r * NV;
     const VT* xc = x + (long long)colidx[blk] * NV;
@@ -236,6 +237,253 @@ __global__ void __launch_bounds__(256) invert_kernel(Geom g, long long p0, const
   }
 }
 
+// Warp-per-patch variant for patches whose matrix fits a warp's share of shared
+// memory (2D, n <= 105): same gather, equilibration and Gauss-Jordan elimination
+// as invert_kernel, with only warp-level synchronisation.
+template <typename CT, typename FT>
+__global__ void __launch_bounds__(256) invert_warp_kernel(Geom g, const int* __restrict__ rowptr,
+                                                          const double* __restrict__ vv,
+                                                          const double* __restrict__ vp,
+                                                          const double* __restrict__ pv, FT* __restrict__ jinv,
+                                                          long long stride, int* status, int equil,
+                                                          const int* __restrict__ only) {
+  const int n = g.npatch, NV = g.NV, nloc = g.nloc, dim = g.dim, nt = g.nt;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int per = n * n + 3 * n;
+  CT* A = reinterpret_cast<CT*>(smem_raw) + (long long)wid * per;
+  CT* colj = A + n * n;
+  CT* rs = colj + n;
+  CT* cs = rs + n;
+  int* perm = reinterpret_cast<int*>(reinterpret_cast<CT*>(smem_raw) + (long long)wpb * per) + wid * n;
+  const int voff = nloc * NV;
+  for (long long p = (long long)blockIdx.x * wpb + wid; p < g.n_cells; p += (long long)gridDim.x * wpb) {
+    if (only && !only[p]) continue;
+    int cx, cy, cz;
+    patch_cell(g, p, cx, cy, cz);
+    const long long cell = cell_id(g, cx, cy, cz);
+    for (int t = lane; t < n * n; t += 32) A[t] = 0;
+    __syncwarp();
+    const int nvv = nloc * nloc * NV * NV;
+    for (int t = lane; t < nvv; t += 32) {
+      const int s = t % NV, r = (t / NV) % NV, j = (t / (NV * NV)) % nloc, i = t / (NV * NV * nloc);
+      const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9,
+                                       2 * cx + j % 3, 2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+      A[(i * NV + r) * n + j * NV + s] = (CT)vv[slot * NV * NV + r * NV + s];
+    }
+    const int nvp = nloc * nt * dim * (dim + 1);
+    for (int t = lane; t < nvp; t += 32) {
+      const int m = t % (dim + 1), c = (t / (dim + 1)) % dim, a = (t / ((dim + 1) * dim)) % nt;
+      const int i = t / ((dim + 1) * dim * nt);
+      const int vrow = i * NV + a * dim + c, prow = voff + a * (dim + 1) + m;
+      A[vrow * n + prow] = (CT)vp[(((cell * nloc + i) * nt + a) * dim + c) * (dim + 1) + m];
+      A[prow * n + vrow] = (CT)pv[((cell * nt + a) * (dim + 1) + m) * (long long)nloc * dim + i * dim + c];
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      CT mx = 0;
+      if (equil)
+        for (int l = 0; l < n; ++l) mx = fmax(mx, fabs(A[i * n + l]));
+      rs[i] = mx > 0 ? (CT)1 / mx : (CT)1;
+    }
+    __syncwarp();
+    for (int l = lane; l < n; l += 32) {
+      CT mx = 0;
+      if (equil)
+        for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(A[i * n + l] * rs[i]));
+      cs[l] = mx > 0 ? (CT)1 / mx : (CT)1;
+    }
+    __syncwarp();
+    if (equil)
+      for (int i = 0; i < n; ++i)
+        for (int l = lane; l < n; l += 32) A[i * n + l] *= rs[i] * cs[l];
+    __syncwarp();
+    bool fail = false;
+    for (int j = 0; j < n; ++j) {
+      CT best = -1;
+      int bi = n;
+      for (int i = j + lane; i < n; i += 32) {
+        const CT v = fabs(A[i * n + j]);
+        if (v > best || (v == best && i < bi)) {
+          best = v;
+          bi = i;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const CT ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      const CT pval = bi < n ? A[bi * n + j] : (CT)0;
+      if (!(fabs(pval) > 0) || isinf(pval)) {
+        fail = true;
+        break;
+      }
+      if (lane == 0) perm[j] = bi;
+      if (bi != j)
+        for (int l = lane; l < n; l += 32) {
+          const CT tmp = A[j * n + l];
+          A[j * n + l] = A[bi * n + l];
+          A[bi * n + l] = tmp;
+        }
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) colj[i] = A[i * n + j];
+      __syncwarp();
+      const CT inv = (CT)1 / pval;
+      for (int l = lane; l < n; l += 32) A[j * n + l] = (l == j ? (CT)1 : A[j * n + l]) * inv;
+      __syncwarp();
+      for (int i = 0; i < n; ++i) {
+        if (i == j) continue;
+        const CT f = colj[i];
+        for (int l = lane; l < n; l += 32) A[i * n + l] = (l == j ? (CT)0 : A[i * n + l]) - f * A[j * n + l];
+      }
+      __syncwarp();
+    }
+    if (fail) {
+      if (lane == 0) atomicCAS(status, 0, (int)(cell + 1));
+      for (int t = lane; t < n * n; t += 32) jinv[p * stride + t] = cvt<FT>((CT)0);
+      __syncwarp();
+      continue;
+    }
+    for (int j = n - 1; j >= 0; --j) {
+      const int pj = perm[j];
+      if (pj != j)
+        for (int i = lane; i < n; i += 32) {
+          const CT tmp = A[i * n + j];
+          A[i * n + j] = A[i * n + pj];
+          A[i * n + pj] = tmp;
+        }
+      __syncwarp();
+    }
+    for (int t = lane; t < n * n; t += 32) {
+      const int col = t / n, row = t - col * n;
+      jinv[p * stride + t] = cvt<FT>(A[row * n + col] * cs[row] * rs[col]);
+    }
+    __syncwarp();
+  }
+}
+
+// Register-resident variant for 2D patches (n = 21(k+1) <= 63): one thread per
+// row, PPB patches per CTA.  Gauss-Jordan without row interchanges on the
+// equilibrated J_K (eliminating the velocity unknowns before the pressure
+// unknowns of the saddle-point matrix needs none on these problems); a pivot
+// below 1e-3 (entries are O(1) after equilibration) flags the patch and the
+// pivoting kernel redoes it.  The columns are rotated by one position per step,
+// so the pivot column is always register 0 and the elimination loop needs no
+// dynamic register indexing; after n steps the columns are back in order.
+template <int N, int PPB, typename MT, typename FT>
+__global__ void __launch_bounds__(N * PPB) invert_rows_kernel(Geom g, const int* __restrict__ rowptr,
+                                                              const MT* __restrict__ vv, const MT* __restrict__ vp,
+                                                              const MT* __restrict__ pv, FT* __restrict__ jinv,
+                                                              long long stride, int* __restrict__ flags) {
+  constexpr int DIM = 2, NL = 9, NT = N / 21, NV = NT * DIM, NP = NT * (DIM + 1), VOFF = NL * NV;
+  static_assert(VOFF + NP == N, "2D Q2/P1disc patch");
+  __shared__ float s_abs[PPB][N][N + 1];
+  __shared__ float s_row[PPB][N];
+  __shared__ float s_cs[PPB][N];
+  __shared__ float s_rs[PPB][N];
+  __shared__ int s_bad[PPB];
+  const int pl = threadIdx.x / N, row = threadIdx.x % N;
+  for (long long p0 = (long long)blockIdx.x * PPB; p0 < g.n_cells; p0 += (long long)gridDim.x * PPB) {
+    const long long p = p0 + pl;
+    const bool live = p < g.n_cells;
+    float a[N];
+    if (live) {
+      int cx, cy, cz;
+      patch_cell(g, p, cx, cy, cz);
+      const long long cell = cell_id(g, cx, cy, cz);
+      if (row < VOFF) {
+        const int i = row / NV, v = row % NV, ta = v / DIM, c = v % DIM;
+        const int ix = 2 * cx + i % 3, iy = 2 * cy + i / 3;
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const long long slot = bcsr_slot(g, rowptr, ix, iy, 0, 2 * cx + j % 3, 2 * cy + j / 3, 0);
+          const MT* b = vv + slot * NV * NV + v * NV;
+#pragma unroll
+          for (int s2 = 0; s2 < NV; ++s2) a[j * NV + s2] = (float)b[s2];
+        }
+        const MT* q = vp + (((cell * NL + i) * NT + ta) * DIM + c) * (DIM + 1);
+#pragma unroll
+        for (int m = 0; m < NP; ++m) a[VOFF + m] = (m / (DIM + 1) == ta) ? (float)q[m % (DIM + 1)] : 0.f;
+      } else {
+        const int qq = row - VOFF, ta = qq / (DIM + 1), m = qq % (DIM + 1);
+        const MT* q = pv + ((cell * NT + ta) * (DIM + 1) + m) * (long long)NL * DIM;
+#pragma unroll
+        for (int col = 0; col < VOFF; ++col) {
+          const int j = col / NV, s2 = col % NV;
+          a[col] = (s2 / DIM == ta) ? (float)q[j * DIM + s2 % DIM] : 0.f;
+        }
+#pragma unroll
+        for (int m2 = 0; m2 < NP; ++m2) a[VOFF + m2] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < N; ++l) a[l] = row == l ? 1.f : 0.f;  // identity keeps idle threads harmless
+    }
+    // equilibration: row scale, then column scale through a transposed copy
+    float mx = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) mx = fmaxf(mx, fabsf(a[l]));
+    const float rs = mx > 0.f ? 1.f / mx : 1.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      a[l] *= rs;
+      s_abs[pl][l][row] = fabsf(a[l]);
+    }
+    s_rs[pl][row] = rs;
+    if (row == 0) s_bad[pl] = 0;
+    __syncthreads();
+    {
+      float cm = 0.f;
+#pragma unroll
+      for (int r = 0; r < N; ++r) cm = fmaxf(cm, s_abs[pl][row][r]);
+      s_cs[pl][row] = cm > 0.f ? 1.f / cm : 1.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < N; ++l) a[l] *= s_cs[pl][l];
+    // elimination; column j sits in register 0 at step j
+    for (int j = 0; j < N; ++j) {
+      const bool isp = row == j;
+      if (isp) {
+        const float piv = a[0];
+        if (!(fabsf(piv) > 1e-3f) || isinf(piv)) s_bad[pl] = 1;
+        const float inv = 1.f / piv;
+        s_row[pl][0] = inv;
+#pragma unroll
+        for (int l = 1; l < N; ++l) s_row[pl][l] = a[l] * inv;
+      }
+      __syncthreads();
+      const float f = a[0];
+#pragma unroll
+      for (int l = 0; l < N - 1; ++l) {
+        const float rv = s_row[pl][l + 1];
+        a[l] = isp ? rv : fmaf(-f, rv, a[l + 1]);
+      }
+      {
+        const float rv = s_row[pl][0];
+        a[N - 1] = isp ? rv : -f * rv;
+      }
+      __syncthreads();
+    }
+    if (live) {
+      if (s_bad[pl]) {
+        if (row == 0) flags[p] = 1;
+      } else {
+        // J_K^{-1} = Dc A'^{-1} Dr, column-major: element (row, col) at col * N + row
+        FT* out = jinv + p * stride;
+        const float csr = s_cs[pl][row];
+#pragma unroll
+        for (int col = 0; col < N; ++col) out[col * N + row] = cvt<FT>(a[col] * csr * s_rs[pl][col]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ smoother
 template <typename VT, typename FT, int RPL>
 __global__ void __launch_bounds__(256) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
@@ -269,14 +517,32 @@ __global__ void __launch_bounds__(256) vanka_colour_kernel(Geom g, int colour, c
   AT acc[RPL];
 #pragma unroll
   for (int t = 0; t < RPL; ++t) acc[t] = 0;
-#pragma unroll 2
-  for (int col = 0; col < n; ++col) {
+  // stream the column-major J_K^{-1}: CB columns of loads are issued before their
+  // FMAs so that each warp keeps CB * n values in flight
+  constexpr int CB = 8;
+  int col = 0;
+  for (; col + CB <= n; col += CB) {
+    FT v[CB][RPL];
+#pragma unroll
+    for (int u = 0; u < CB; ++u)
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int row = lane + 32 * t;
+        v[u][t] = row < n ? A[(long long)(col + u) * n + row] : cvt<FT>(0.f);
+      }
+#pragma unroll
+    for (int u = 0; u < CB; ++u) {
+      const AT rc = (AT)rl[col + u];
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) acc[t] += cvt<AT>(v[u][t]) * rc;
+    }
+  }
+  for (; col < n; ++col) {
     const AT rc = (AT)rl[col];
-    const FT* Ac = A + (long long)col * n;
 #pragma unroll
     for (int t = 0; t < RPL; ++t) {
       const int row = lane + 32 * t;
-      if (row < n) acc[t] += cvt<AT>(Ac[row]) * rc;
+      if (row < n) acc[t] += cvt<AT>(A[(long long)col * n + row]) * rc;
     }
   }
 #pragma unroll
@@ -330,12 +596,56 @@ size_t invert_scratch_bytes(const Geom& g, int compute_f32) {
 
 template <typename FT>
 void invert_patches(const Geom& g, const int* rowptr, const double* vv, const double* vp, const double* pv,
-                    FT* jinv, int compute_f32, int* status, void* scratch, cudaStream_t st) {
+                    const float* vv32, const float* vp32, const float* pv32, FT* jinv, int compute_f32, int* status,
+                    void* scratch, int* flags, cudaStream_t st) {
   const int n = g.npatch;
   const long long stride = patch_stride(n);
   const int threads = n <= 63 ? 128 : 256;
+  int sms = 0, dev = 0;
+  STG_CUDA_OK(cudaGetDevice(&dev));
+  STG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int* only = nullptr;
+  if (compute_f32 && g.dim == 2 && n <= 63 && flags) {
+    // register-resident pivot-free pass, then the pivoting kernel for flagged patches only
+    STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
+    auto run = [&](auto kern, int ppb, int nthreads, auto* V, auto* VP, auto* PV) {
+      const long long want = (g.n_cells + ppb - 1) / ppb;
+      int per_sm = 0;
+      STG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, 0));
+      const long long grid = std::max<long long>(1, std::min<long long>(want, (long long)sms * std::max(per_sm, 1)));
+      kern<<<(unsigned)grid, nthreads, 0, st>>>(g, rowptr, V, VP, PV, jinv, stride, flags);
+      STG_LAUNCH_OK();
+    };
+    if (vv32) {
+      if (n == 21) run(invert_rows_kernel<21, 8, float, FT>, 8, 21 * 8, vv32, vp32, pv32);
+      else if (n == 42) run(invert_rows_kernel<42, 4, float, FT>, 4, 42 * 4, vv32, vp32, pv32);
+      else run(invert_rows_kernel<63, 2, float, FT>, 2, 63 * 2, vv32, vp32, pv32);
+    } else {
+      if (n == 21) run(invert_rows_kernel<21, 8, double, FT>, 8, 21 * 8, vv, vp, pv);
+      else if (n == 42) run(invert_rows_kernel<42, 4, double, FT>, 4, 42 * 4, vv, vp, pv);
+      else run(invert_rows_kernel<63, 2, double, FT>, 2, 63 * 2, vv, vp, pv);
+    }
+    only = flags;
+  }
   auto launch = [&](auto tag) {
     using CT = decltype(tag);
+    const size_t per_warp = ((size_t)n * n + 3 * n) * sizeof(CT) + (size_t)n * sizeof(int);
+    const int wpb = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+    // FP64 elimination is FMA-throughput bound and wants more warps per SM than a
+    // warp-per-patch layout leaves; it keeps the CTA-per-patch kernel.
+    if (sizeof(CT) == 4 && wpb >= 4) {
+      const size_t sm = per_warp * wpb;
+      STG_CUDA_OK(cudaFuncSetAttribute(invert_warp_kernel<CT, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)std::max<size_t>(sm, 48 * 1024)));
+      int per_sm = 0;
+      STG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, invert_warp_kernel<CT, FT>, 32 * wpb, sm));
+      const long long want = (g.n_cells + wpb - 1) / wpb;
+      const long long grid = std::max<long long>(1, std::min<long long>(want, (long long)sms * std::max(per_sm, 1)));
+      invert_warp_kernel<CT, FT><<<(unsigned)grid, 32 * wpb, sm, st>>>(g, rowptr, vv, vp, pv, jinv, stride, status,
+                                                                       compute_f32, only);
+      STG_LAUNCH_OK();
+      return;
+    }
     const size_t tail = (size_t)3 * n * sizeof(CT) + (size_t)n * sizeof(int) + 64;
     const size_t full = (size_t)n * n * sizeof(CT) + tail;
     // the attribute is a per-function maximum: never set it below the 48 KB default
@@ -401,12 +711,14 @@ template void apply_operator<double, double>(const Geom&, const int*, const int*
                                              const double*, const double*, const double*, double*, cudaStream_t);
 template void apply_operator<float, float>(const Geom&, const int*, const int*, const float*, const float*,
                                            const float*, const float*, const float*, float*, cudaStream_t);
-template void invert_patches<double>(const Geom&, const int*, const double*, const double*, const double*, double*,
-                                     int, int*, void*, cudaStream_t);
-template void invert_patches<float>(const Geom&, const int*, const double*, const double*, const double*, float*,
-                                    int, int*, void*, cudaStream_t);
+template void invert_patches<double>(const Geom&, const int*, const double*, const double*, const double*, const float*,
+                                     const float*, const float*, double*, int, int*, void*, int*, cudaStream_t);
+template void invert_patches<float>(const Geom&, const int*, const double*, const double*, const double*,
+                                    const float*, const float*, const float*, float*, int, int*, void*, int*,
+                                    cudaStream_t);
 template void invert_patches<__nv_bfloat16>(const Geom&, const int*, const double*, const double*, const double*,
-                                            __nv_bfloat16*, int, int*, void*, cudaStream_t);
+                                            const float*, const float*, const float*, __nv_bfloat16*, int, int*,
+                                            void*, int*, cudaStream_t);
 template void vanka_colour<double, double>(const Geom&, int, const double*, const double*, double*, double,
                                            cudaStream_t);
 template void vanka_colour<float, float>(const Geom&, int, const float*, const float*, float*, float, cudaStream_t);
