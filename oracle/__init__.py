@@ -20,9 +20,10 @@ the Navier-Stokes equations"):
 * ``transfer``   -- nested-space prolongation and its transpose.
 * ``multigrid``  -- the V-cycle with a direct coarse solve on T_0.
 * ``fgmres``     -- right-preconditioned flexible GMRES.
+* ``newton``     -- nonlinear slab residual F_n, damped Newton (Sec. 3).
 
 Every part is pinned by the ``-m "not gpu"`` tests against closed forms,
 invariants and brute-force dense linear algebra.
 """
-from . import timebasis, element, mesh, assemble, vanka, transfer, multigrid, fgmres  # noqa: F401
+from . import timebasis, element, mesh, assemble, vanka, transfer, multigrid, fgmres, newton  # noqa: F401
 from .multigrid import Hierarchy  # noqa: F401
