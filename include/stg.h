@@ -143,6 +143,30 @@ stg_status stg_coarse_solve(stg_ctx* ctx, const double* b, double* x);
  * pointers, may be NULL, and are written even on STG_ENOCONV. */
 stg_status stg_gmres_solve(stg_ctx* ctx, const double* b, double* x, int* iters, double* rel_res);
 
+/* Damped Newton for the nonlinear slab problem F_n(X_n) = 0 of Eq. (3.2)
+ * (Sec. 3): F_n(X) = J_Oseen(w = v(X)) X - b with
+ *   b_a = tau w_a [ (f_a, psi) + B_GammaD(g_a, (psi, xi)) ] + chi_a(0) (v_prev, psi),
+ * each correction from J_Newton(v(X)) C = -F_n(X) by FGMRES with the V-cycle
+ * (options of the context), damping lambda = 1, 1/2, .., 1/16 until
+ * ||F(X + lambda C)|| < (1 - 1e-4 lambda) ||F(X)|| (1/16 is taken otherwise).
+ *   v_prev  DEVICE [R] velocity at t_{n-1} (velocity part of the C-ABI order) or NULL (0)
+ *   f, g    DEVICE [(k+1) R] body force and Dirichlet data at the finest Q2 nodes per
+ *           Radau node (the integrals use their Q2 interpolants) or NULL (0)
+ *   X       DEVICE [N]: initial guess in, solution out (C-ABI order)
+ *   stops when ||F|| <= max(rtol ||F(X_0)||, atol) or after maxit steps (STG_ENOCONV)
+ * newton_steps, gmres_iters (total), residual (final ||F||) are host pointers, may be
+ * NULL.  Afterwards the finest operator holds the Oseen Jacobian of the final iterate and
+ * the other levels the Newton Jacobian of the previous one: call
+ * stg_update_linearisation before using the linear-solve entry points again. */
+stg_status stg_newton_slab(stg_ctx* ctx, const double* v_prev, const double* f, const double* g, double* X,
+                           double rtol, double atol, int maxit, int* newton_steps, int* gmres_iters,
+                           double* residual);
+
+/* X0 = the previous slab's end value (the last Radau-node block of X_prev, velocity
+ * and pressure) repeated at every Radau node: the initial guess of the next slab.
+ * DEVICE vectors of length N in the C-ABI order. */
+stg_status stg_slab_initial_guess(stg_ctx* ctx, const double* X_prev, double* X0);
+
 /* Sizes of level `level`: space-time DoFs N_l = (k+1)(R+S), cells, and the
  * local patch size (k+1)(R^ + S^) (21(k+1) in 2D, 85(k+1) in 3D).  Host
  * pointers, each may be NULL. */

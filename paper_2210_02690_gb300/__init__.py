@@ -28,8 +28,8 @@ PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16}
 EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg_apply_jacobian",
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
-            "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_last_error",
-            "stg_destroy")
+            "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_newton_slab",
+            "stg_slab_initial_guess", "stg_last_error", "stg_destroy")
 
 
 class StgError(RuntimeError):
@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(LL), ctypes.POINTER(LL)]),
         "stg_kernel_launches": (LL, []),
         "stg_invert_local_noalloc": (I, [I, LL, P, P, P]),
+        "stg_newton_slab": (I, [P, P, P, P, P, D, D, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stg_slab_initial_guess": (I, [P, P, P]),
         "stg_last_error": (ctypes.c_char_p, [P]),
         "stg_destroy": (None, [P]),
     }
@@ -246,6 +248,22 @@ class Solver:
         its, rel = ctypes.c_int(), ctypes.c_double()
         st = self._call(self.lib.stg_gmres_solve, self._p(b), self._p(x), ctypes.byref(its), ctypes.byref(rel))
         return x, its.value, rel.value, st == STG_OK
+
+    def newton_slab(self, X0, v_prev=None, f=None, g=None, rtol=1e-8, atol=0.0, maxit=20):
+        """Damped Newton for the slab; returns (X, Newton steps, GMRES iterations, final ||F||, converged)."""
+        X = self._dev(X0).clone()
+        opt = [self._dev(a) if a is not None else None for a in (v_prev, f, g)]
+        ptr = [self._p(a) if a is not None else None for a in opt]
+        steps, its, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        st = self._call(self.lib.stg_newton_slab, ptr[0], ptr[1], ptr[2], self._p(X), rtol, atol, maxit,
+                        ctypes.byref(steps), ctypes.byref(its), ctypes.byref(res))
+        return X, steps.value, its.value, res.value, st == STG_OK
+
+    def slab_initial_guess(self, X_prev):
+        Xp = self._dev(X_prev)
+        X0 = self.torch.empty_like(Xp)
+        self._call(self.lib.stg_slab_initial_guess, self._p(Xp), self._p(X0))
+        return X0
 
     def local_inverse(self, level: int, cell: int) -> np.ndarray:
         n = self.sizes(level)[2]

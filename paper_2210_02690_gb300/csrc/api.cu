@@ -191,6 +191,9 @@ struct stg_ctx {
   int prof_used = 0;
   double prof_ms = 0.0;
   long long prof_launches = 0, prof_patches = 0, prof_pending_patches = 0;
+  // damped Newton (finest level, internal layout, FP64)
+  double *nb = nullptr, *nX = nullptr, *nr = nullptr, *nC = nullptr, *nXt = nullptr;
+  double *nf = nullptr, *ng = nullptr, *rhs_tab = nullptr;
   std::vector<void*> owned;
   std::string err;
   bool pure_dirichlet = false;
@@ -243,11 +246,10 @@ void build_pattern(stg_ctx* c, LevelBufs& L) {
 
 bool vc64(const stg_ctx* c) { return c->opt.vcycle_prec == STG_F64; }
 
-// Assemble every level, invert the local matrices, factor the coarse system.
-void linearise(stg_ctx* c, const double* w_cabi) {
+// Assemble every level for the finest-level linearisation velocity in F.w (internal
+// layout), invert the local matrices, factor the coarse system.
+void linearise_internal(stg_ctx* c) {
   const int nl = (int)c->lv.size();
-  LevelBufs& F = c->lv[nl - 1];
-  w_to_internal(F.g, w_cabi, F.w, c->st);
   for (int l = nl - 1; l > 0; --l) inject_w(c->lv[l - 1].g, c->lv[l].g, c->lv[l].w, c->lv[l - 1].w, c->st);
   AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, c->opt.linearisation == STG_NEWTON ? 1 : 0};
   STG_CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
@@ -287,6 +289,12 @@ void linearise(stg_ctx* c, const double* w_cabi) {
   const int cs = vc64(c) ? c->coarse64.read_status(c->st) : c->coarse32.read_status(c->st);
   if (cs > 0) throw Error{STG_ESINGULAR, "singular block in the coarse solver (block " + std::to_string(cs - 1) + ")"};
   if (cs < 0) throw Error{STG_ECUDA, "coarse matrix coupling outside the slab block structure"};
+}
+
+void linearise(stg_ctx* c, const double* w_cabi) {
+  LevelBufs& F = c->lv.back();
+  w_to_internal(F.g, w_cabi, F.w, c->st);
+  linearise_internal(c);
 }
 
 template <typename VT>
@@ -568,6 +576,54 @@ stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double
   return beta <= tol || bnorm == 0.0 ? STG_OK : STG_ENOCONV;
 }
 
+// r = b - F... precisely r = -F_n(X) = b - J_Oseen(w = v(X)) X on the finest level (the finest
+// operator storage is overwritten by the Oseen Jacobian at v(X)).
+double neg_residual(stg_ctx* c, const double* X, double* r) {
+  LevelBufs& F = c->lv.back();
+  AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, 0};
+  // the velocity part of an internal vector is laid out exactly like an internal w
+  assemble_level(F.g, c->td, cf, X, F.rowptr, F.asm_tab, F.vv, F.nnzb, F.vp, F.pv, c->st);
+  apply_operator<double, double>(F.g, F.rowptr, F.colidx, F.vv, F.vp, F.pv, X, c->nb, r, c->st);
+  return std::sqrt(dot_host(c, r, r));
+}
+
+// Damped Newton for F_n(X) = 0 (Sec. 3) on internal vectors; X in/out.
+stg_status newton(stg_ctx* c, double* X, double rtol, double atol, int maxit, int* steps_out, int* gmres_out,
+                  double* res_out) {
+  LevelBufs& F = c->lv.back();
+  const long long n = F.g.N;
+  double nr = neg_residual(c, X, c->nr);
+  const double tol = std::max(rtol * nr, atol);
+  int steps = 0, gits = 0;
+  stg_status st = STG_OK;
+  while (nr > tol && steps < maxit) {
+    STG_CUDA_OK(cudaMemcpyAsync(F.w, X, sizeof(double) * F.g.nvel, cudaMemcpyDeviceToDevice, c->st));
+    linearise_internal(c);  // Newton Jacobian at v(X) on every level, local inverses, coarse factors
+    STG_CUDA_OK(cudaMemsetAsync(c->nC, 0, sizeof(double) * n, c->st));
+    int its = 0;
+    double rel = 0.0;
+    const stg_status ls = fgmres(c, c->nr, c->nC, &its, &rel);  // J C = -F
+    gits += its;
+    if (ls == STG_ENOCONV) st = STG_ENOCONV;
+    double lam = 1.0, nt = 0.0;
+    for (;;) {
+      axpby(n, 1.0, X, 0.0, c->nXt, c->st);
+      axpby(n, lam, c->nC, 1.0, c->nXt, c->st);
+      nt = neg_residual(c, c->nXt, c->nr);
+      if (nt < (1.0 - 1e-4 * lam) * nr || lam <= 1.0 / 16.0) break;
+      lam *= 0.5;
+    }
+    STG_CUDA_OK(cudaMemcpyAsync(X, c->nXt, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+    nr = nt;
+    ++steps;
+  }
+  if (steps_out) *steps_out = steps;
+  if (gmres_out) *gmres_out = gits;
+  if (res_out) *res_out = nr;
+  if (nr > tol) return STG_ENOCONV;
+  return st;
+}
+
 stg_status fail(stg_ctx* c, const Error& e) {
   if (c)
     c->err = e.msg;
@@ -705,6 +761,14 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->tmp_a = dalloc<double>(c, n);
     c->tmp_b = dalloc<double>(c, n);
     c->partial = dalloc<double>(c, (long long)dot_partial_doubles());
+    c->nb = dalloc<double>(c, n);
+    c->nX = dalloc<double>(c, n);
+    c->nr = dalloc<double>(c, n);
+    c->nC = dalloc<double>(c, n);
+    c->nXt = dalloc<double>(c, n);
+    c->nf = dalloc<double>(c, c->lv.back().g.nvel);
+    c->ng = dalloc<double>(c, c->lv.back().g.nvel);
+    c->rhs_tab = dalloc<double>(c, rhs_table_doubles(mesh->dim));
     c->hd = dalloc<double>(c, 160);
     STG_CUDA_OK(cudaMallocHost(&c->hh, sizeof(double) * 160));
     linearise(c, w);
@@ -844,6 +908,40 @@ stg_status stg_gmres_solve(stg_ctx* c, const double* b, double* x, int* iters, d
     STG_CUDA_OK(cudaStreamSynchronize(c->st));
     if (s == STG_ENOCONV) c->err = "FGMRES reached gmres_maxit";
     return s;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_newton_slab(stg_ctx* c, const double* v_prev, const double* f, const double* g, double* X,
+                           double rtol, double atol, int maxit, int* newton_steps, int* gmres_iters,
+                           double* residual) {
+  if (!c || !X || maxit < 0 || rtol < 0 || atol < 0) return STG_EINVAL;
+  try {
+    LevelBufs& F = c->lv.back();
+    const Geom& gg = F.g;
+    if (f) w_to_internal(gg, f, c->nf, c->st);
+    if (g) w_to_internal(gg, g, c->ng, c->st);
+    // assemble_level fills the mass matrix of the level's table used by the right-hand side
+    AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, 0};
+    assemble_rhs_level(gg, c->td, cf, F.asm_tab, c->rhs_tab, f ? c->nf : nullptr, g ? c->ng : nullptr, v_prev,
+                       c->nb, c->st);
+    cabi_to_internal<double>(gg, X, c->nX, c->st);
+    const stg_status s = newton(c, c->nX, rtol, atol, maxit, newton_steps, gmres_iters, residual);
+    internal_to_cabi<double>(gg, c->nX, X, c->st);
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    if (s == STG_ENOCONV) c->err = "Newton or FGMRES reached its iteration limit";
+    return s;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_slab_initial_guess(stg_ctx* c, const double* X_prev, double* X0) {
+  if (!c || !X_prev || !X0) return STG_EINVAL;
+  try {
+    replicate_end_value(c->lv.back().g, X_prev, X0, c->st);
+    return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);
   }

@@ -390,6 +390,112 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
   }
 }
 
+
+// Data terms of the right-hand side of Eq. (2.2), one CTA per face class:
+//   NB[(i,c),(j,e)]: B_GammaD(phi_j e_e, (phi_i e_c, 0)) = -nu <phi_j, d_n phi_i> delta_ce
+//                    + gamma1 nu / h <phi_j, phi_i> delta_ce + gamma2 / h <phi_j n_e, phi_i n_c>
+//   PB[m][(j,e)]  : B_GammaD(phi_j e_e, (0, xi_m)) = -<phi_j n_e, xi_m>
+template <int DIM>
+__global__ void __launch_bounds__(256) rhs_constants(Geom g, AsmCoef cf, double* __restrict__ rt) {
+  constexpr int NQ = Pow3<DIM>::v;
+  constexpr int NL = NQ;
+  constexpr int ND = NL * DIM;
+  const unsigned faces = blockIdx.x;
+  double* nb = rt + (long long)faces * (ND * ND + (DIM + 1) * ND);
+  double* pb = nb + ND * ND;
+  for (int t = threadIdx.x; t < ND * ND; t += blockDim.x) {
+    const int I = t / ND, J = t % ND;
+    const int i = I / DIM, c = I % DIM, j = J / DIM, e = J % DIM;
+    double val = 0.0;
+    for (int f = 0; f < 2 * DIM; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      const double ns = s0 ? 1.0 : -1.0, hf = g.h[e0];
+      for (int fq = 0; fq < NQ / 3; ++fq) {
+        int p[3];
+        const double wt = face_point<DIM>(g, e0, s0, fq, p);
+        double vi, vj, gi[3], gj[3];
+        basis_at<DIM>(g, p, i, vi, gi);
+        basis_at<DIM>(g, p, j, vj, gj);
+        double term = 0.0;
+        if (c == e) term += -cf.nu * vj * ns * gi[e0] + cf.gamma1 * cf.nu / hf * vj * vi;
+        if (c == e0 && e == e0) term += cf.gamma2 / hf * vj * vi;
+        val += wt * term;
+      }
+    }
+    nb[t] = val;
+  }
+  for (int t = threadIdx.x; t < (DIM + 1) * ND; t += blockDim.x) {
+    const int m = t / ND, J = t % ND, j = J / DIM, e = J % DIM;
+    double val = 0.0;
+    for (int f = 0; f < 2 * DIM; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      if (e != e0) continue;
+      const double ns = s0 ? 1.0 : -1.0;
+      for (int fq = 0; fq < NQ / 3; ++fq) {
+        int p[3];
+        const double wt = face_point<DIM>(g, e0, s0, fq, p);
+        double vj, gj[3];
+        basis_at<DIM>(g, p, j, vj, gj);
+        const double xi = m == 0 ? 1.0 : c_X[p[m - 1]];
+        val -= wt * vj * ns * xi;
+      }
+    }
+    pb[t] = val;
+  }
+}
+
+// Right-hand side b_a = tau w_a [ M f_a + NB g_a ] + chi_a(0) M v_prev (velocity rows, added
+// colour by colour) and tau w_a PB g_a (pressure rows of the cell).  f, g: nodal data in
+// the internal velocity layout [node][a][c]; v_prev: [node][c]; each may be null.
+template <int DIM>
+__global__ void __launch_bounds__(256) assemble_rhs(Geom g, int colour, TimeData td, AsmCoef cf,
+                                                    const double* __restrict__ tab,
+                                                    const double* __restrict__ rt, const double* __restrict__ f,
+                                                    const double* __restrict__ gd,
+                                                    const double* __restrict__ vprev, double* __restrict__ b) {
+  constexpr int NL = Pow3<DIM>::v;
+  constexpr int ND = NL * DIM;
+  __shared__ double fl[NL * 5 * DIM], gl[NL * 5 * DIM], vl[NL * DIM];
+  __shared__ long long nodes[NL];
+  const int nt = g.nt, NV = g.NV;
+  int cx, cy, cz;
+  patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
+  const int cc[3] = {cx, cy, cz};
+  const long long cell = cell_id(g, cx, cy, cz);
+  const unsigned cls = face_class<DIM>(g, cc);
+  const double* nb = rt + (long long)cls * (ND * ND + (DIM + 1) * ND);
+  const double* pb = nb + ND * ND;
+  for (int i = threadIdx.x; i < NL; i += blockDim.x)
+    nodes[i] = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
+  __syncthreads();
+  for (int t = threadIdx.x; t < NL * NV; t += blockDim.x) {
+    const int i = t / NV, v = t % NV;
+    fl[t] = f ? f[nodes[i] * NV + v] : 0.0;
+    gl[t] = gd ? gd[nodes[i] * NV + v] : 0.0;
+  }
+  for (int t = threadIdx.x; t < NL * DIM; t += blockDim.x) vl[t] = vprev ? vprev[nodes[t / DIM] * DIM + t % DIM] : 0.0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < NL * NV; t += blockDim.x) {
+    const int i = t / NV, v = t % NV, a = v / DIM, c = v % DIM;
+    double mf = 0.0, mv = 0.0, ng = 0.0;
+    for (int j = 0; j < NL; ++j) {
+      const double mij = tab[i * NL + j];
+      mf += mij * fl[j * NV + v];
+      mv += mij * vl[j * DIM + c];
+      for (int e = 0; e < DIM; ++e) ng += nb[(i * DIM + c) * ND + j * DIM + e] * gl[j * NV + a * DIM + e];
+    }
+    b[nodes[i] * NV + v] += cf.tau * td.w[a] * (mf + ng) + td.jump[a] * mv;
+  }
+  for (int t = threadIdx.x; t < nt * (DIM + 1); t += blockDim.x) {
+    const int a = t / (DIM + 1), m = t % (DIM + 1);
+    double s = 0.0;
+    for (int J = 0; J < ND; ++J) s += pb[m * ND + J] * gl[(J / DIM) * NV + a * DIM + J % DIM];
+    b[g.nvel + cell * g.NP + t] = cf.tau * td.w[a] * s;
+  }
+}
+
 }  // namespace
 
 long long assemble_table_doubles(int dim, int k) {
@@ -423,6 +529,35 @@ void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const 
       assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
     else
       assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
+    STG_LAUNCH_OK();
+  }
+}
+
+}  // namespace stg
+
+namespace stg {
+
+long long rhs_table_doubles(int dim) {
+  const long long nd = (long long)(dim == 2 ? 9 : 27) * dim;
+  return (1LL << (2 * dim)) * (nd * nd + (dim + 1) * nd);
+}
+
+void assemble_rhs_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* tab, double* rt,
+                        const double* f, const double* gd, const double* vprev, double* b, cudaStream_t st) {
+  STG_CUDA_OK(cudaMemsetAsync(b, 0, sizeof(double) * g.N, st));
+  const unsigned ncls = 1u << (2 * g.dim);
+  if (g.dim == 2)
+    rhs_constants<2><<<ncls, 256, 0, st>>>(g, cf, rt);
+  else
+    rhs_constants<3><<<ncls, 256, 0, st>>>(g, cf, rt);
+  STG_LAUNCH_OK();
+  for (int col = 0; col < (1 << g.dim); ++col) {
+    const long long cnt = g.coff[col + 1] - g.coff[col];
+    if (cnt == 0) continue;
+    if (g.dim == 2)
+      assemble_rhs<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, tab, rt, f, gd, vprev, b);
+    else
+      assemble_rhs<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, tab, rt, f, gd, vprev, b);
     STG_LAUNCH_OK();
   }
 }

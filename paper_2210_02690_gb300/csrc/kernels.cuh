@@ -27,6 +27,12 @@ long long assemble_table_doubles(int dim, int k);
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                     double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
 
+// right-hand side of Eq. (2.2) from nodal f, g (internal velocity layout) and v_prev ([node][c]);
+// the mass matrix comes from the assembly table of the level (assemble_level first)
+long long rhs_table_doubles(int dim);
+void assemble_rhs_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* tab, double* rt,
+                        const double* f, const double* gd, const double* vprev, double* b, cudaStream_t st);
+
 // ---- operators, smoother and transfers (vanka.cu, transfer.cu)
 // out = b - J x (has_b) or out = J x; MT = operator precision, VT = vector precision
 template <typename MT, typename VT>
@@ -63,6 +69,8 @@ template <typename VT>
 void internal_to_cabi(const Geom& g, const VT* in, double* out, cudaStream_t st);
 // velocity-only (k+1) x R C-ABI block -> internal node-major velocity
 void w_to_internal(const Geom& g, const double* in, double* out, cudaStream_t st);
+// X0 = last Radau-node block of X_prev repeated (C-ABI order), the slab's initial guess
+void replicate_end_value(const Geom& g, const double* xp, double* x0, cudaStream_t st);
 // coarse velocity at node 2g of the fine level (injection)
 void inject_w(const Geom& gc, const Geom& gf, const double* wf, double* wc, cudaStream_t st);
 

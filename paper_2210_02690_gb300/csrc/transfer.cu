@@ -197,6 +197,14 @@ __global__ void inject_w_kernel(Geom gc, Geom gf, const double* __restrict__ wf,
   wc[t] = wf[node_id(gf, 2 * c[0], 2 * c[1], 2 * c[2]) * gf.NV + v];
 }
 
+// X0 (C-ABI order) = the last Radau-node block of X_prev, repeated for every node.
+__global__ void replicate_kernel(Geom g, const double* __restrict__ xp, double* __restrict__ x0) {
+  const long long blk = g.nvel / g.nt + g.npres / g.nt;  // R + S
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N) return;
+  x0[t] = xp[(long long)(g.nt - 1) * blk + t % blk];
+}
+
 template <typename D, typename S>
 __global__ void convert_kernel(long long n, const S* __restrict__ in, D* __restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -240,6 +248,11 @@ void w_to_internal(const Geom& g, const double* in, double* out, cudaStream_t st
 
 void inject_w(const Geom& gc, const Geom& gf, const double* wf, double* wc, cudaStream_t st) {
   inject_w_kernel<<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, wf, wc);
+  STG_LAUNCH_OK();
+}
+
+void replicate_end_value(const Geom& g, const double* xp, double* x0, cudaStream_t st) {
+  replicate_kernel<<<grid_for(g.N, 256), 256, 0, st>>>(g, xp, x0);
   STG_LAUNCH_OK();
 }
 
