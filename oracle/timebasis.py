@@ -16,7 +16,6 @@ from __future__ import annotations
 
 import numpy as np
 from numpy.polynomial import legendre as L
-from numpy.polynomial import polynomial as P
 
 
 def radau_nodes(k: int) -> np.ndarray:
@@ -29,40 +28,65 @@ def radau_nodes(k: int) -> np.ndarray:
     return (x + 1.0) / 2.0
 
 
-def lagrange_polys(nodes: np.ndarray) -> list:
-    """Power-series coefficients of the Lagrange polynomials chi_a at `nodes`."""
-    polys = []
+def lagrange_values(nodes: np.ndarray, s) -> np.ndarray:
+    """chi_a(s) in product form; shape (len(s), len(nodes))."""
+    s = np.atleast_1d(np.asarray(s, float))
+    out = np.ones((len(s), len(nodes)))
     for a, ca in enumerate(nodes):
-        others = np.delete(nodes, a)
-        num = P.polyfromroots(others) if len(others) else np.array([1.0])
-        polys.append(num / np.prod(ca - others))
-    return polys
+        for b, cb in enumerate(nodes):
+            if b != a:
+                out[:, a] *= (s - cb) / (ca - cb)
+    return out
+
+
+def lagrange_derivatives(nodes: np.ndarray, s) -> np.ndarray:
+    """chi_a'(s) = sum_{m != a} 1/(c_a - c_m) prod_{l != a, m} (s - c_l)/(c_a - c_l); shape (len(s), n)."""
+    s = np.atleast_1d(np.asarray(s, float))
+    n = len(nodes)
+    out = np.zeros((len(s), n))
+    for a in range(n):
+        for m in range(n):
+            if m == a:
+                continue
+            term = np.full(len(s), 1.0 / (nodes[a] - nodes[m]))
+            for l in range(n):
+                if l != a and l != m:
+                    term *= (s - nodes[l]) / (nodes[a] - nodes[l])
+            out[:, a] += term
+    return out
+
+
+def _gauss01(k: int):
+    """(k+1)-point Gauss-Legendre rule on [0, 1] (exact to degree 2k+1)."""
+    x, w = L.leggauss(k + 1)
+    return (x + 1.0) / 2.0, w / 2.0
 
 
 def radau_weights(k: int) -> np.ndarray:
-    chis = lagrange_polys(radau_nodes(k))
-    return np.array([P.polyval(1.0, P.polyint(c)) - P.polyval(0.0, P.polyint(c)) for c in chis])
+    """w_a = int_0^1 chi_a(s) ds."""
+    q, qw = _gauss01(k)
+    return qw @ lagrange_values(radau_nodes(k), q)
 
 
 def time_matrix(k: int) -> np.ndarray:
-    """T_ab = int_0^1 chi_b' chi_a ds + chi_a(0) chi_b(0) (row a = test, column b = trial)."""
-    chis = lagrange_polys(radau_nodes(k))
-    n = k + 1
-    t = np.zeros((n, n))
-    for a in range(n):
-        for b in range(n):
-            integrand = P.polymul(P.polyder(chis[b]), chis[a])
-            anti = P.polyint(integrand)
-            t[a, b] = P.polyval(1.0, anti) - P.polyval(0.0, anti) + P.polyval(0.0, chis[a]) * P.polyval(0.0, chis[b])
-    return t
+    """T_ab = int_0^1 chi_b' chi_a ds + chi_a(0) chi_b(0) (row a = test, column b = trial).
+
+    The integrand has degree 2k - 1, so the (k+1)-point Gauss rule is exact; the
+    Lagrange polynomials are evaluated in product form (a monomial expansion loses
+    about 1e-12 relative accuracy at k = 4)."""
+    nodes = radau_nodes(k)
+    q, qw = _gauss01(k)
+    chi = lagrange_values(nodes, q)
+    dchi = lagrange_derivatives(nodes, q)
+    j0 = lagrange_values(nodes, 0.0)[0]
+    return np.einsum("q,qa,qb->ab", qw, chi, dchi) + np.outer(j0, j0)
 
 
 def jump_vector(k: int) -> np.ndarray:
     """chi_a(0): the coefficient of the previous slab's end value in the jump term."""
-    return np.array([P.polyval(0.0, c) for c in lagrange_polys(radau_nodes(k))])
+    return lagrange_values(radau_nodes(k), 0.0)[0]
 
 
 def eval_basis(k: int, s) -> np.ndarray:
     """chi_a(s) for all a, s in [0, 1]; shape (len(s), k+1)."""
-    s = np.atleast_1d(np.asarray(s, float))
-    return np.stack([P.polyval(s, c) for c in lagrange_polys(radau_nodes(k))], axis=1)
+    return lagrange_values(radau_nodes(k), s)

@@ -79,3 +79,23 @@ def test_stability_function_is_pade(z):
     assert abs(_stability(1, z) - (1 + z / 3) / (1 - 2 * z / 3 + z * z / 6)) < 1e-13
     # k = 2: (2,3) Pade: (1 + 2z/5 + z^2/20) / (1 - 3z/5 + 3z^2/20 - z^3/60)
     assert abs(_stability(2, z) - (1 + 2 * z / 5 + z * z / 20) / (1 - 3 * z / 5 + 3 * z * z / 20 - z ** 3 / 60)) < 1e-13
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_time_matrix_against_high_precision(k):
+    sp = pytest.importorskip("sympy")
+    t, x = sp.symbols("t x")
+    roots = sorted(sp.re(r) for r in sp.Poly(sp.legendre(k, x) - sp.legendre(k + 1, x), x).nroots(n=40))
+    c = [(r + 1) / 2 for r in roots]
+    chi = []
+    for a in range(k + 1):
+        pa = sp.Integer(1)
+        for b in range(k + 1):
+            if b != a:
+                pa *= (t - c[b]) / (c[a] - c[b])
+        chi.append(sp.expand(pa))
+    ref = np.array([[float(sp.integrate(sp.diff(chi[b], t) * chi[a], (t, 0, 1)) + chi[a].subs(t, 0) * chi[b].subs(t, 0))
+                     for b in range(k + 1)] for a in range(k + 1)])
+    wref = np.array([float(sp.integrate(ch, (t, 0, 1))) for ch in chi])
+    assert np.abs(tb.time_matrix(k) - ref).max() < 1e-14 * np.abs(ref).max()
+    assert np.abs(tb.radau_weights(k) - wref).max() < 1e-15
