@@ -214,6 +214,27 @@ long long stg_kernel_launches(void);
  * stg_last_error(NULL)) or STG_ECUDA on failure. */
 stg_status stg_invert_local_noalloc(int n, long long count, const double* a, double* a_inv, void* stream);
 
+/* Autotuner: times every variant of the smoother's colour kernel (3 column-batch
+ * depths x 3 CTA sizes) on every level >= 1 and keeps the fastest per level; the
+ * V-cycle graph is recaptured.  variant (host, may be NULL) receives the finest
+ * level's choice, sweep_ms (host, may be NULL) the finest level's time of one
+ * sweep's colour kernels.  (Engineering service; the paper has no counterpart.) */
+stg_status stg_autotune(stg_ctx* ctx, int* variant, double* sweep_ms);
+
+/* Batched solves of several independent problems (contexts of any mesh size and
+ * k, each created with its own non-default stream): the V-cycles of all problems
+ * are captured once into a single CUDA graph with one concurrent branch per
+ * problem, and stg_batch_gmres_solve runs FGMRES (Sec. 3) on all problems in lock
+ * step, one graph launch per iteration.  b, x: HOST arrays of n DEVICE pointers
+ * (C-ABI order of each problem); iters, rel: host arrays of n entries or NULL.
+ * The contexts must not be used elsewhere while they belong to a batch, and the
+ * batch must be destroyed before them.  (The paper has no counterpart.) */
+typedef struct stg_batch stg_batch;
+stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out);
+stg_status stg_batch_gmres_solve(stg_batch* batch, const double* const* b, double* const* x, int* iters,
+                                 double* rel);
+void stg_batch_destroy(stg_batch* batch);
+
 /* Text of the last error of this context (or of the last failed stg_setup
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char* stg_last_error(const stg_ctx* ctx);

@@ -29,7 +29,8 @@ EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
             "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_newton_slab",
-            "stg_slab_initial_guess", "stg_last_error", "stg_destroy")
+            "stg_slab_initial_guess", "stg_autotune", "stg_batch_create", "stg_batch_gmres_solve",
+            "stg_batch_destroy", "stg_last_error", "stg_destroy")
 
 
 class StgError(RuntimeError):
@@ -86,6 +87,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_invert_local_noalloc": (I, [I, LL, P, P, P]),
         "stg_newton_slab": (I, [P, P, P, P, P, D, D, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "stg_slab_initial_guess": (I, [P, P, P]),
+        "stg_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stg_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P)]),
+        "stg_batch_gmres_solve": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I),
+                                      ctypes.POINTER(D)]),
+        "stg_batch_destroy": (None, [P]),
         "stg_last_error": (ctypes.c_char_p, [P]),
         "stg_destroy": (None, [P]),
     }
@@ -283,6 +289,12 @@ class Solver:
         self.lib.stg_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(p))
         return ms.value, n.value, p.value
 
+    def autotune(self):
+        """Picks the fastest colour-kernel variant per level; returns (finest variant, sweep ms)."""
+        v, ms = ctypes.c_int(), ctypes.c_double()
+        self._call(self.lib.stg_autotune, ctypes.byref(v), ctypes.byref(ms))
+        return v.value, ms.value
+
     def kernel_launches(self) -> int:
         return int(self.lib.stg_kernel_launches())
 
@@ -290,6 +302,56 @@ class Solver:
         if getattr(self, "ctx", None):
             self.lib.stg_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several independent Solvers solved together: one CUDA graph holds all V-cycles."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.lib = load_library()
+        n = len(self.solvers)
+        arr = (ctypes.c_void_p * n)(*[s.ctx for s in self.solvers])
+        out = ctypes.c_void_p()
+        for s in self.solvers:
+            s.stream.synchronize()
+        st = self.lib.stg_batch_create(n, arr, ctypes.byref(out))
+        if st != STG_OK:
+            msg = self.lib.stg_last_error(None)
+            raise StgError(st, msg.decode() if msg else "")
+        self.handle = out
+
+    def gmres_solve(self, rhs, x0=None):
+        import torch
+
+        n = len(self.solvers)
+        bs = [s._dev(b) for s, b in zip(self.solvers, rhs)]
+        xs = [torch.zeros_like(b) if x0 is None else s._dev(x).clone() for s, b, x in
+              zip(self.solvers, bs, x0 if x0 is not None else [None] * n)]
+        for s in self.solvers:
+            s._enter()
+        pb = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        px = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        its = (ctypes.c_int * n)()
+        rel = (ctypes.c_double * n)()
+        st = self.lib.stg_batch_gmres_solve(self.handle, pb, px, its, rel)
+        for s in self.solvers:
+            s._leave()
+        if st not in (STG_OK, STG_ENOCONV):
+            msg = self.lib.stg_last_error(None)
+            raise StgError(st, msg.decode() if msg else "")
+        return xs, list(its), list(rel), st == STG_OK
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.stg_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

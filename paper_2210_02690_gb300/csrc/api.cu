@@ -70,23 +70,6 @@ Geom make_geom(const stg_mesh& m, int level, int k) {
 
 // ------------------------------------------------------------------ time basis
 namespace {
-using Poly = std::vector<double>;  // monomial coefficients, low order first
-Poly pmul(const Poly& a, const Poly& b) {
-  Poly r(a.size() + b.size() - 1, 0.0);
-  for (size_t i = 0; i < a.size(); ++i)
-    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
-  return r;
-}
-Poly pder(const Poly& a) {
-  Poly r(a.size() > 1 ? a.size() - 1 : 1, 0.0);
-  for (size_t i = 1; i < a.size(); ++i) r[i - 1] = a[i] * (double)i;
-  return r;
-}
-double pint01(const Poly& a) {
-  double s = 0.0;
-  for (size_t i = 0; i < a.size(); ++i) s += a[i] / (double)(i + 1);
-  return s;
-}
 double legendre(int n, double x) {
   if (n == 0) return 1.0;
   double p0 = 1.0, p1 = x;
@@ -97,17 +80,16 @@ double legendre(int n, double x) {
   }
   return p1;
 }
-}  // namespace
 
-TimeData time_basis(int k) {
-  // right Radau points: roots of P_k - P_{k+1} on (-1, 1], mapped to [0, 1]
-  auto f = [k](double x) { return legendre(k, x) - legendre(k + 1, x); };
+// Sign-change roots of f on (-1, 1) by bisection to machine precision.
+template <typename F>
+std::vector<double> roots_in(F f) {
   std::vector<double> x;
   const int ns = 4000;
-  for (int i = 0; i < ns; ++i) {
+  for (int i = 0; i < ns - 1; ++i) {
     double a = -1.0 + 2.0 * i / ns, b = -1.0 + 2.0 * (i + 1) / ns;
-    if (i == ns - 1) break;  // the root x = 1 is added exactly below
-    double fa = f(a), fb = f(b);
+    double fa = f(a);
+    const double fb = f(b);
     if (fa == 0.0) {
       x.push_back(a);
       continue;
@@ -125,23 +107,61 @@ TimeData time_basis(int k) {
       x.push_back(0.5 * (a + b));
     }
   }
+  return x;
+}
+
+// Lagrange polynomial a at nodes c, and its derivative, in product form.
+double lag(const std::vector<double>& c, int a, double s) {
+  double v = 1.0;
+  for (size_t b = 0; b < c.size(); ++b)
+    if ((int)b != a) v *= (s - c[b]) / (c[a] - c[b]);
+  return v;
+}
+double dlag(const std::vector<double>& c, int a, double s) {
+  double d = 0.0;
+  for (size_t m = 0; m < c.size(); ++m) {
+    if ((int)m == a) continue;
+    double t = 1.0 / (c[a] - c[m]);
+    for (size_t l = 0; l < c.size(); ++l)
+      if ((int)l != a && l != m) t *= (s - c[l]) / (c[a] - c[l]);
+    d += t;
+  }
+  return d;
+}
+}  // namespace
+
+TimeData time_basis(int k) {
+  // right Radau points: roots of P_k - P_{k+1} on (-1, 1], mapped to [0, 1]
+  std::vector<double> x = roots_in([k](double t) { return legendre(k, t) - legendre(k + 1, t); });
   x.push_back(1.0);
   if ((int)x.size() != k + 1) throw Error{STG_EINVAL, "Radau root search failed"};
-  TimeData td{};
-  std::vector<Poly> chi(k + 1);
-  for (int a = 0; a <= k; ++a) {
-    td.c[a] = 0.5 * (x[a] + 1.0);
+  // (k+1)-point Gauss-Legendre rule on [0, 1]: exact for the degree-2k integrands below
+  const int nq = k + 1;
+  std::vector<double> gx = roots_in([nq](double t) { return legendre(nq, t); });
+  if ((int)gx.size() != nq) throw Error{STG_EINVAL, "Gauss root search failed"};
+  std::vector<double> q(nq), qw(nq);
+  for (int i = 0; i < nq; ++i) {
+    const double t = gx[i];
+    const double dp = nq * (t * legendre(nq, t) - legendre(nq - 1, t)) / (t * t - 1.0);
+    q[i] = 0.5 * (t + 1.0);
+    qw[i] = 1.0 / ((1.0 - t * t) * dp * dp);  // 2 / ((1 - t^2) P'(t)^2), halved for [0, 1]
   }
+  TimeData td{};
+  std::vector<double> c(k + 1);
+  for (int a = 0; a <= k; ++a) c[a] = 0.5 * (x[a] + 1.0);
   for (int a = 0; a <= k; ++a) {
-    Poly p{1.0};
-    for (int b = 0; b <= k; ++b)
-      if (b != a) p = pmul(p, Poly{-td.c[b] / (td.c[a] - td.c[b]), 1.0 / (td.c[a] - td.c[b])});
-    chi[a] = p;
-    td.w[a] = pint01(p);
-    td.jump[a] = p[0];
+    td.c[a] = c[a];
+    td.jump[a] = lag(c, a, 0.0);
+    double w = 0.0;
+    for (int i = 0; i < nq; ++i) w += qw[i] * lag(c, a, q[i]);
+    td.w[a] = w;
   }
   for (int a = 0; a <= k; ++a)
-    for (int b = 0; b <= k; ++b) td.T[a][b] = pint01(pmul(pder(chi[b]), chi[a])) + chi[a][0] * chi[b][0];
+    for (int b = 0; b <= k; ++b) {
+      double t = 0.0;
+      for (int i = 0; i < nq; ++i) t += qw[i] * dlag(c, b, q[i]) * lag(c, a, q[i]);
+      td.T[a][b] = t + td.jump[a] * td.jump[b];
+    }
   return td;
 }
 
@@ -160,6 +180,7 @@ struct LevelBufs {
   void* jinv = nullptr;
   double* w = nullptr;
   double* asm_tab = nullptr;
+  int colour_variant = kColourDefault;
   void *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr;
 };
 
@@ -347,7 +368,7 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
       for (int col = 0; col < ncol; ++col) {
         const bool prof = c->prof_on && l == (int)c->lv.size() - 1 && c->prof_used + 2 <= (int)c->prof_ev.size();
         if (prof) record_event(c->prof_ev[c->prof_used], c->st);
-        vanka_colour<VT, FT>(g, col, jinv, res, z, (VT)1, c->st);
+        vanka_colour<VT, FT>(g, col, jinv, res, z, (VT)1, c->st, L.colour_variant);
         if (prof) {
           record_event(c->prof_ev[c->prof_used + 1], c->st);
           c->prof_used += 2;
@@ -364,7 +385,7 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
         }
         const bool prof = c->prof_on && l == (int)c->lv.size() - 1 && c->prof_used + 2 <= (int)c->prof_ev.size();
         if (prof) record_event(c->prof_ev[c->prof_used], c->st);
-        vanka_colour<VT, FT>(g, col, jinv, res, x, (VT)c->opt.omega, c->st);
+        vanka_colour<VT, FT>(g, col, jinv, res, x, (VT)c->opt.omega, c->st, L.colour_variant);
         if (prof) {
           record_event(c->prof_ev[c->prof_used + 1], c->st);
           c->prof_used += 2;
@@ -508,72 +529,139 @@ double dot_host(stg_ctx* c, const double* a, const double* b) {
   return c->hh[0];
 }
 
-// Flexible GMRES(m), right preconditioned by one V-cycle; b, x internal FP64.
-stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double* rel_out) {
-  const long long n = c->lv.back().g.N;
-  const int m = c->opt.gmres_restart;
-  const double bnorm = std::sqrt(dot_host(c, b, b));
-  const double tol = std::max(c->opt.gmres_rtol * bnorm, c->opt.gmres_atol);
-  int its = 0;
-  double beta = 0.0;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-  auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-  for (;;) {
-    apply_fine64(c, x, c->rv);
-    axpby(n, 1.0, b, -1.0, c->rv, c->st);  // r = b - J x
-    beta = std::sqrt(dot_host(c, c->rv, c->rv));
-    if (beta <= tol || its >= c->opt.gmres_maxit || bnorm == 0.0) break;
-    axpby(n, 1.0 / beta, c->rv, 0.0, c->V, c->st);
-    std::fill(gv.begin(), gv.end(), 0.0);
-    gv[0] = beta;
-    int jend = 0;
-    for (int j = 0; j < m; ++j) {
-      double* vj = c->V + (long long)j * n;
-      double* zj = c->Z + (long long)j * n;
-      STG_CUDA_OK(cudaMemcpyAsync(c->vin, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
-      run_vcycle(c);
-      STG_CUDA_OK(cudaMemcpyAsync(zj, c->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
-      apply_fine64(c, zj, c->wv);
-      // classical Gram-Schmidt, twice
-      multi_dot(n, j + 1, c->V, n, c->wv, c->partial, c->hd, c->st);
-      multi_axpy_sub(n, j + 1, c->V, n, c->hd, c->wv, c->st);
-      multi_dot(n, j + 1, c->V, n, c->wv, c->partial, c->hd + 32, c->st);
-      multi_axpy_sub(n, j + 1, c->V, n, c->hd + 32, c->wv, c->st);
-      multi_dot(n, 1, c->wv, n, c->wv, c->partial, c->hd + 64, c->st);
-      STG_CUDA_OK(cudaMemcpyAsync(c->hh, c->hd, sizeof(double) * 65, cudaMemcpyDeviceToHost, c->st));
-      STG_CUDA_OK(cudaStreamSynchronize(c->st));
-      prof_collect(c);
-      for (int i = 0; i <= j; ++i) Hc(i, j) = c->hh[i] + c->hh[32 + i];
-      const double hn = std::sqrt(std::max(c->hh[64], 0.0));
-      Hc(j + 1, j) = hn;
-      if (hn > 0.0) axpby(n, 1.0 / hn, c->wv, 0.0, c->V + (long long)(j + 1) * n, c->st);
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
-        Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
-        Hc(i, j) = t;
-      }
-      const double rho = std::hypot(Hc(j, j), Hc(j + 1, j));
-      cs[j] = rho > 0 ? Hc(j, j) / rho : 1.0;
-      sn[j] = rho > 0 ? Hc(j + 1, j) / rho : 0.0;
-      Hc(j, j) = rho;
-      Hc(j + 1, j) = 0.0;
-      gv[j + 1] = -sn[j] * gv[j];
-      gv[j] = cs[j] * gv[j];
-      ++its;
-      jend = j + 1;
-      if (std::fabs(gv[j + 1]) <= tol || its >= c->opt.gmres_maxit || rho == 0.0 || hn == 0.0) break;
-    }
-    for (int i = jend - 1; i >= 0; --i) {
-      double s = gv[i];
-      for (int l = i + 1; l < jend; ++l) s -= Hc(i, l) * y[l];
-      y[i] = Hc(i, i) != 0.0 ? s / Hc(i, i) : 0.0;
-    }
-    STG_CUDA_OK(cudaMemcpyAsync(c->hd + 96, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, c->st));
-    multi_axpy_add(n, jend, c->Z, n, c->hd + 96, x, c->st);
+// Flexible GMRES(m), right preconditioned by one V-cycle (Sec. 3), as a state machine so
+// that one problem or a batch of problems (stepped in lock step) share the code.
+struct FgState {
+  stg_ctx* c = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  long long n = 0;
+  int m = 0, its = 0, j = 0, jend = 0;
+  double bnorm = 0.0, tol = 0.0, beta = 0.0;
+  bool active = false, done = false;
+  std::vector<double> H, cs, sn, gv, y;
+  double& Hc(int i, int jj) { return H[(size_t)i * m + jj]; }
+};
+
+void fg_begin(FgState& S, stg_ctx* c, const double* b, double* x) {
+  S.c = c;
+  S.b = b;
+  S.x = x;
+  S.n = c->lv.back().g.N;
+  S.m = c->opt.gmres_restart;
+  S.H.assign((size_t)(S.m + 1) * S.m, 0.0);
+  S.cs.assign(S.m, 0.0);
+  S.sn.assign(S.m, 0.0);
+  S.gv.assign(S.m + 1, 0.0);
+  S.y.assign(S.m, 0.0);
+  S.bnorm = std::sqrt(dot_host(c, b, b));
+  S.tol = std::max(c->opt.gmres_rtol * S.bnorm, c->opt.gmres_atol);
+  S.its = 0;
+  S.active = false;
+  S.done = false;
+}
+
+// r = b - J x; stop or open a new restart cycle (synchronises the context's stream)
+void fg_restart(FgState& S) {
+  stg_ctx* c = S.c;
+  apply_fine64(c, S.x, c->rv);
+  axpby(S.n, 1.0, S.b, -1.0, c->rv, c->st);
+  S.beta = std::sqrt(dot_host(c, c->rv, c->rv));
+  if (S.beta <= S.tol || S.its >= c->opt.gmres_maxit || S.bnorm == 0.0) {
+    S.done = true;
+    return;
   }
-  if (iters_out) *iters_out = its;
-  if (rel_out) *rel_out = bnorm > 0 ? beta / bnorm : 0.0;
-  return beta <= tol || bnorm == 0.0 ? STG_OK : STG_ENOCONV;
+  axpby(S.n, 1.0 / S.beta, c->rv, 0.0, c->V, c->st);
+  std::fill(S.gv.begin(), S.gv.end(), 0.0);
+  S.gv[0] = S.beta;
+  S.j = 0;
+  S.active = true;
+}
+
+// V-cycle input v_j
+void fg_pre(FgState& S) {
+  stg_ctx* c = S.c;
+  STG_CUDA_OK(cudaMemcpyAsync(c->vin, c->V + (long long)S.j * S.n, sizeof(double) * S.n, cudaMemcpyDeviceToDevice,
+                              c->st));
+}
+
+// z_j = V(v_j), w = J z_j, classical Gram-Schmidt twice, ||w||; the coefficients go to the host
+void fg_post(FgState& S) {
+  stg_ctx* c = S.c;
+  const long long n = S.n;
+  const int j = S.j;
+  double* zj = c->Z + (long long)j * n;
+  STG_CUDA_OK(cudaMemcpyAsync(zj, c->vout, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st));
+  apply_fine64(c, zj, c->wv);
+  multi_dot(n, j + 1, c->V, n, c->wv, c->partial, c->hd, c->st);
+  multi_axpy_sub(n, j + 1, c->V, n, c->hd, c->wv, c->st);
+  multi_dot(n, j + 1, c->V, n, c->wv, c->partial, c->hd + 32, c->st);
+  multi_axpy_sub(n, j + 1, c->V, n, c->hd + 32, c->wv, c->st);
+  multi_dot(n, 1, c->wv, n, c->wv, c->partial, c->hd + 64, c->st);
+  STG_CUDA_OK(cudaMemcpyAsync(c->hh, c->hd, sizeof(double) * 65, cudaMemcpyDeviceToHost, c->st));
+}
+
+// after the stream has drained: Arnoldi column, Givens rotations, and at the end of a
+// cycle the update x += Z y
+void fg_update(FgState& S) {
+  stg_ctx* c = S.c;
+  const long long n = S.n;
+  const int j = S.j;
+  for (int i = 0; i <= j; ++i) S.Hc(i, j) = c->hh[i] + c->hh[32 + i];
+  const double hn = std::sqrt(std::max(c->hh[64], 0.0));
+  S.Hc(j + 1, j) = hn;
+  if (hn > 0.0) axpby(n, 1.0 / hn, c->wv, 0.0, c->V + (long long)(j + 1) * n, c->st);
+  for (int i = 0; i < j; ++i) {
+    const double t = S.cs[i] * S.Hc(i, j) + S.sn[i] * S.Hc(i + 1, j);
+    S.Hc(i + 1, j) = -S.sn[i] * S.Hc(i, j) + S.cs[i] * S.Hc(i + 1, j);
+    S.Hc(i, j) = t;
+  }
+  const double rho = std::hypot(S.Hc(j, j), S.Hc(j + 1, j));
+  S.cs[j] = rho > 0 ? S.Hc(j, j) / rho : 1.0;
+  S.sn[j] = rho > 0 ? S.Hc(j + 1, j) / rho : 0.0;
+  S.Hc(j, j) = rho;
+  S.Hc(j + 1, j) = 0.0;
+  S.gv[j + 1] = -S.sn[j] * S.gv[j];
+  S.gv[j] = S.cs[j] * S.gv[j];
+  ++S.its;
+  S.jend = j + 1;
+  S.j = j + 1;
+  const bool end = std::fabs(S.gv[j + 1]) <= S.tol || S.its >= c->opt.gmres_maxit || rho == 0.0 || hn == 0.0 ||
+                   S.j == S.m;
+  if (!end) return;
+  const int je = S.jend;
+  for (int i = je - 1; i >= 0; --i) {
+    double sum = S.gv[i];
+    for (int l = i + 1; l < je; ++l) sum -= S.Hc(i, l) * S.y[l];
+    S.y[i] = S.Hc(i, i) != 0.0 ? sum / S.Hc(i, i) : 0.0;
+  }
+  STG_CUDA_OK(cudaMemcpyAsync(c->hd + 96, S.y.data(), sizeof(double) * je, cudaMemcpyHostToDevice, c->st));
+  multi_axpy_add(n, je, c->Z, n, c->hd + 96, S.x, c->st);
+  S.active = false;
+}
+
+stg_status fg_result(const FgState& S, int* iters_out, double* rel_out) {
+  if (iters_out) *iters_out = S.its;
+  if (rel_out) *rel_out = S.bnorm > 0 ? S.beta / S.bnorm : 0.0;
+  return S.beta <= S.tol || S.bnorm == 0.0 ? STG_OK : STG_ENOCONV;
+}
+
+stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double* rel_out) {
+  FgState S;
+  fg_begin(S, c, b, x);
+  for (;;) {
+    if (!S.active) {
+      fg_restart(S);
+      if (S.done) break;
+    }
+    fg_pre(S);
+    run_vcycle(c);
+    fg_post(S);
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    fg_update(S);
+  }
+  return fg_result(S, iters_out, rel_out);
 }
 
 // r = b - F... precisely r = -F_n(X) = b - J_Oseen(w = v(X)) X on the finest level (the finest
@@ -622,6 +710,40 @@ stg_status newton(stg_ctx* c, double* X, double rtol, double atol, int maxit, in
   if (res_out) *res_out = nr;
   if (nr > tol) return STG_ENOCONV;
   return st;
+}
+
+// Times every colour-kernel variant on one level (all colours of one sweep, `reps` times)
+// and keeps the fastest; returns its time per sweep in ms.
+template <typename VT, typename FT>
+double tune_level(stg_ctx* c, int l, int reps) {
+  LevelBufs& L = c->lv[l];
+  cudaEvent_t e0, e1;
+  STG_CUDA_OK(cudaEventCreate(&e0));
+  STG_CUDA_OK(cudaEventCreate(&e1));
+  double best = 1e30;
+  int bestv = L.colour_variant;
+  for (int v = 0; v < kColourVariants; ++v) {
+    for (int w = 0; w < 2; ++w)  // warm-up
+      for (int col = 0; col < (1 << L.g.dim); ++col)
+        vanka_colour<VT, FT>(L.g, col, (const FT*)L.jinv, (const VT*)L.r, (VT*)L.z, (VT)1, c->st, v);
+    STG_CUDA_OK(cudaEventRecord(e0, c->st));
+    for (int rep = 0; rep < reps; ++rep)
+      for (int col = 0; col < (1 << L.g.dim); ++col)
+        vanka_colour<VT, FT>(L.g, col, (const FT*)L.jinv, (const VT*)L.r, (VT*)L.z, (VT)1, c->st, v);
+    STG_CUDA_OK(cudaEventRecord(e1, c->st));
+    STG_CUDA_OK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    STG_CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / reps < best) {
+      best = ms / reps;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.colour_variant = bestv;
+  STG_CUDA_OK(cudaMemsetAsync(L.z, 0, (vc64(c) ? 8 : 4) * L.g.N, c->st));  // the smoother expects z = 0
+  return best;
 }
 
 stg_status fail(stg_ctx* c, const Error& e) {
@@ -1034,6 +1156,158 @@ stg_status stg_profile_read(const stg_ctx* c, double* total_ms, long long* launc
 }
 
 long long stg_kernel_launches(void) { return launch_counter(); }
+
+stg_status stg_autotune(stg_ctx* c, int* variant, double* sweep_ms) {
+  if (!c) return STG_EINVAL;
+  try {
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    double ms = 0.0;
+    for (int l = 1; l < (int)c->lv.size(); ++l) {
+      if (vc64(c))
+        ms = tune_level<double, double>(c, l, 5);
+      else if (c->opt.factor_prec == STG_F32)
+        ms = tune_level<float, float>(c, l, 5);
+      else
+        ms = tune_level<float, __nv_bfloat16>(c, l, 5);
+    }
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    if (c->graph) {  // recapture with the chosen variants
+      STG_CUDA_OK(cudaGraphExecDestroy(c->graph));
+      c->graph = nullptr;
+    }
+    if (variant) *variant = c->lv.back().colour_variant;
+    if (sweep_ms) *sweep_ms = ms;
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+}  // extern "C"
+
+struct stg_batch {
+  std::vector<stg_ctx*> ctx;
+  cudaStream_t main = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+extern "C" {
+
+stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out) {
+  if (!out || n < 1 || !ctxs) return STG_EINVAL;
+  *out = nullptr;
+  stg_batch* B = new (std::nothrow) stg_batch();
+  if (!B) return STG_ENOMEM;
+  try {
+    for (int p = 0; p < n; ++p) {
+      stg_ctx* c = ctxs[p];
+      if (!c || !c->st) throw Error{STG_EINVAL, "every batched context needs its own non-default stream"};
+      for (int q = 0; q < p; ++q)
+        if (ctxs[q]->st == c->st) throw Error{STG_EINVAL, "batched contexts must use distinct streams"};
+      if (c->prof_on) throw Error{STG_EINVAL, "turn profiling off before batching"};
+      B->ctx.push_back(c);
+    }
+    STG_CUDA_OK(cudaStreamCreateWithFlags(&B->main, cudaStreamNonBlocking));
+    B->ev.resize(n + 1);
+    for (auto& e : B->ev) STG_CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (stg_ctx* c : B->ctx) STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    // one graph: every problem's V-cycle as its own branch (fork from and join into the batch stream)
+    cudaGraph_t graph = nullptr;
+    const long long before = launch_counter();
+    STG_CUDA_OK(cudaStreamBeginCapture(B->main, cudaStreamCaptureModeThreadLocal));
+    try {
+      STG_CUDA_OK(cudaEventRecord(B->ev[n], B->main));
+      for (int p = 0; p < n; ++p) {
+        stg_ctx* c = B->ctx[p];
+        STG_CUDA_OK(cudaStreamWaitEvent(c->st, B->ev[n], 0));
+        vcycle_body(c);
+        STG_CUDA_OK(cudaEventRecord(B->ev[p], c->st));
+        STG_CUDA_OK(cudaStreamWaitEvent(B->main, B->ev[p], 0));
+      }
+    } catch (...) {
+      cudaStreamEndCapture(B->main, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    STG_CUDA_OK(cudaStreamEndCapture(B->main, &graph));
+    B->graph_kernels = launch_counter() - before;
+    launch_counter() = before;
+    const cudaError_t e = cudaGraphInstantiate(&B->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    STG_CUDA_OK(e);
+    *out = B;
+    return STG_OK;
+  } catch (const Error& e) {
+    g_setup_error = e.msg;
+    stg_batch_destroy(B);
+    return e.st;
+  }
+}
+
+stg_status stg_batch_gmres_solve(stg_batch* B, const double* const* b, double* const* x, int* iters, double* rel) {
+  if (!B || !b || !x) return STG_EINVAL;
+  const int n = (int)B->ctx.size();
+  try {
+    std::vector<FgState> S(n);
+    for (int p = 0; p < n; ++p) {
+      stg_ctx* c = B->ctx[p];
+      const Geom& g = c->lv.back().g;
+      cabi_to_internal<double>(g, b[p], c->tmp_a, c->st);
+      cabi_to_internal<double>(g, x[p], c->tmp_b, c->st);
+      fg_begin(S[p], c, c->tmp_a, c->tmp_b);
+    }
+    std::vector<int> live;
+    for (;;) {
+      live.clear();
+      for (int p = 0; p < n; ++p) {
+        if (S[p].done) continue;
+        if (!S[p].active) fg_restart(S[p]);
+        if (!S[p].done) live.push_back(p);
+      }
+      if (live.empty()) break;
+      for (int p : live) {
+        fg_pre(S[p]);
+        STG_CUDA_OK(cudaEventRecord(B->ev[p], B->ctx[p]->st));
+        STG_CUDA_OK(cudaStreamWaitEvent(B->main, B->ev[p], 0));
+      }
+      STG_CUDA_OK(cudaGraphLaunch(B->graph, B->main));  // all problems' V-cycles, concurrently
+      launch_counter() += B->graph_kernels;
+      STG_CUDA_OK(cudaEventRecord(B->ev[n], B->main));
+      for (int p : live) {
+        STG_CUDA_OK(cudaStreamWaitEvent(B->ctx[p]->st, B->ev[n], 0));
+        fg_post(S[p]);
+      }
+      for (int p : live) {
+        STG_CUDA_OK(cudaStreamSynchronize(B->ctx[p]->st));
+        fg_update(S[p]);
+      }
+    }
+    stg_status all = STG_OK;
+    for (int p = 0; p < n; ++p) {
+      stg_ctx* c = B->ctx[p];
+      internal_to_cabi<double>(c->lv.back().g, c->tmp_b, x[p], c->st);
+      const stg_status sp = fg_result(S[p], iters ? iters + p : nullptr, rel ? rel + p : nullptr);
+      if (sp != STG_OK) all = sp;
+    }
+    for (stg_ctx* c : B->ctx) STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    return all;
+  } catch (const Error& e) {
+    g_setup_error = e.msg;
+    return e.st;
+  }
+}
+
+void stg_batch_destroy(stg_batch* B) {
+  if (!B) return;
+  if (B->main) cudaStreamSynchronize(B->main);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  for (auto& e : B->ev)
+    if (e) cudaEventDestroy(e);
+  if (B->main) cudaStreamDestroy(B->main);
+  delete B;
+}
 
 const char* stg_last_error(const stg_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }
 

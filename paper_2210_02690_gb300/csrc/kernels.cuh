@@ -50,8 +50,12 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
 
 // One colour phase of the smoother: y_K = J_K^{-1} R_K r for all cells of colour
 // `colour`; accumulate (averaged mode: z += y) or apply (coloured mode: z += omega y).
+// variant = 3 * column-batch index (4, 8, 16 columns in flight) + CTA-size index (128, 256, 512)
+constexpr int kColourVariants = 9;
+constexpr int kColourDefault = 4;  // 8 columns, 256 threads
 template <typename VT, typename FT>
-void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st);
+void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st,
+                  int variant = kColourDefault);
 
 // d += omega z / p (p = static multiplicity of (S2)); z = 0.
 template <typename VT>

@@ -485,8 +485,8 @@ __global__ void __launch_bounds__(N * PPB) invert_rows_kernel(Geom g, const int*
 }
 
 // ------------------------------------------------------------------ smoother
-template <typename VT, typename FT, int RPL>
-__global__ void __launch_bounds__(256) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
+template <typename VT, typename FT, int RPL, int CB>
+__global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
                                                            long long stride, const VT* __restrict__ r,
                                                            VT* __restrict__ z, VT scale) {
   using AT = typename AccT<VT>::type;
@@ -519,7 +519,6 @@ __global__ void __launch_bounds__(256) vanka_colour_kernel(Geom g, int colour, c
   for (int t = 0; t < RPL; ++t) acc[t] = 0;
   // stream the column-major J_K^{-1}: CB columns of loads are issued before their
   // FMAs so that each warp keeps CB * n values in flight
-  constexpr int CB = 8;
   int col = 0;
   for (; col + CB <= n; col += CB) {
     FT v[CB][RPL];
@@ -674,28 +673,39 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
 }
 
 template <typename VT, typename FT>
-void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st) {
+void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st,
+                  int variant) {
   const long long cnt = g.coff[colour + 1] - g.coff[colour];
   if (cnt == 0) return;
   const int n = g.npatch;
   const long long stride = patch_stride(n);
-  const int threads = 256, wpb = threads / 32;
+  const int cb_idx = (variant / 3) % 3, th_idx = variant % 3;
+  const int threads = 128 << th_idx, wpb = threads / 32;
   const size_t sm = (size_t)wpb * n * sizeof(VT);
   const unsigned grid = grid_for(cnt, wpb);
-#define STG_VC(RPL)                                                                                     \
-  vanka_colour_kernel<VT, FT, RPL><<<grid, threads, sm, st>>>(g, colour, jinv, stride, r, z, scale)
-  if (n <= 32)
-    STG_VC(1);
-  else if (n <= 64)
-    STG_VC(2);
-  else if (n <= 96)
-    STG_VC(3);
-  else if (n <= 128)
-    STG_VC(4);
-  else if (n <= 192)
-    STG_VC(6);
-  else
-    STG_VC(8);
+#define STG_VC(RPL, CB) \
+  vanka_colour_kernel<VT, FT, RPL, CB><<<grid, threads, sm, st>>>(g, colour, jinv, stride, r, z, scale)
+#define STG_VCB(RPL)      \
+  if (cb_idx == 0)        \
+    STG_VC(RPL, 4);       \
+  else if (cb_idx == 1)   \
+    STG_VC(RPL, 8);       \
+  else                    \
+    STG_VC(RPL, 16)
+  if (n <= 32) {
+    STG_VCB(1);
+  } else if (n <= 64) {
+    STG_VCB(2);
+  } else if (n <= 96) {
+    STG_VCB(3);
+  } else if (n <= 128) {
+    STG_VCB(4);
+  } else if (n <= 192) {
+    STG_VCB(6);
+  } else {
+    STG_VCB(8);
+  }
+#undef STG_VCB
 #undef STG_VC
   STG_LAUNCH_OK();
 }
@@ -720,10 +730,11 @@ template void invert_patches<__nv_bfloat16>(const Geom&, const int*, const doubl
                                             const float*, const float*, const float*, __nv_bfloat16*, int, int*,
                                             void*, int*, cudaStream_t);
 template void vanka_colour<double, double>(const Geom&, int, const double*, const double*, double*, double,
-                                           cudaStream_t);
-template void vanka_colour<float, float>(const Geom&, int, const float*, const float*, float*, float, cudaStream_t);
+                                           cudaStream_t, int);
+template void vanka_colour<float, float>(const Geom&, int, const float*, const float*, float*, float, cudaStream_t,
+                                         int);
 template void vanka_colour<float, __nv_bfloat16>(const Geom&, int, const __nv_bfloat16*, const float*, float*,
-                                                 float, cudaStream_t);
+                                                 float, cudaStream_t, int);
 template void vanka_update<double>(const Geom&, double*, double*, double, cudaStream_t);
 template void vanka_update<float>(const Geom&, float*, float*, double, cudaStream_t);
 

@@ -1,7 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on small meshes.
 
-Tolerances (FP64 form): operators, transfers and other fixed-order sums agree
-to a few ulps (1e-13 relative); results that pass through the local inverses
+Tolerances (FP64 form): operator applications are held to the forward-error
+bound of a product whose entries carry a few tens of ulps (each entry is a sum
+of ~30 quadrature terms): 64 eps || |J| |x| || / || J x ||; transfers (exact
+weights) to 1e-14 relative; results that pass through the local inverses
 J_K^{-1} carry their rounding amplified by cond(J_K) (up to ~1e4 on these
 meshes), so local inverses, sweeps and V-cycles are held to 1e-11 relative;
 FGMRES solutions at rtol 1e-12 agree to 1e-8 relative.
@@ -23,6 +25,8 @@ CASES = {
     "square_k0_dirichlet": (si.MeshSpec(2, (8, 8), (0.0, 0.0), (1.0, 1.0), 3, si.ALL2), 0, False),
     "square_k2_dirichlet": (si.MeshSpec(2, (6, 4), (0.0, 0.0), (1.0, 0.7), 2, si.ALL2), 2, True),
     "rect_k1_ragged": (si.MeshSpec(2, (10, 6), (0.3, -0.2), (1.3, 0.5), 2, si.FACE_XLO | si.FACE_YHI), 1, True),
+    "square_k3": (si.MeshSpec(2, (4, 4), (0.0, 0.0), (1.0, 1.0), 2, si.ALL2), 3, True),
+    "channel_k4": (si.MeshSpec(2, (4, 2), (0.0, 0.0), (2.2, 0.41), 2, OUT2), 4, True),
     "cube_k0": (si.MeshSpec(3, (4, 4, 2), (0.0,) * 3, (1.0, 1.0, 0.5), 2, si.ALL3), 0, True),
     "cube_k1_outflow": (si.MeshSpec(3, (2, 4, 2), (0.0,) * 3, (0.5, 1.0, 0.5), 2, si.ALL3 & ~si.FACE_XHI), 1, True),
 }
@@ -71,13 +75,18 @@ def consistent_rhs(ref, seed=7):
     return ref.apply(xs)
 
 
+EPS = np.finfo(float).eps
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_jacobian_every_level(name):
     gpu, ref = pair(name)
     for lvl, lev in enumerate(ref.levels):
         x = si.random_vector(lev.N, 11 + lvl)
         y = cpu(gpu.apply_jacobian(torch.from_numpy(x).cuda(), level=lvl))
-        assert rel(y, ref.J[lvl] @ x) < 1e-13, lvl
+        y_ref = ref.J[lvl] @ x
+        bound = 64 * EPS * np.linalg.norm(abs(ref.J[lvl]) @ np.abs(x)) / np.linalg.norm(y_ref)
+        assert rel(y, y_ref) < bound, (lvl, rel(y, y_ref), bound)
 
 
 @pytest.mark.parametrize("name", list(CASES))
