@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -314,7 +316,96 @@ def gpu_arm(args) -> None:
                                "sample": f"oracle full step (assembly, LAPACK local inverses, coarse LU, FGMRES to "
                                          f"1e-8) on the same channel at {o['cells'][0]}x{o['cells'][1]} quads "
                                          f"({o['n_dofs']} DoFs, 4 levels), 1 thread, {t:.1f} s"}
+    if world == 1 and not args.no_warm_start:
+        out["warm_start"] = warm_start_report()
+    if world == 1 and not args.no_batch:
+        out["batched"] = batch_report()
     print(json.dumps(out), flush=True)
+
+
+def batch_report() -> dict:
+    """64 uneven problems (rectangles of 32..256 square cells per side, k in {1, 2}) solved to 1e-8:
+    batched FP32 form (one graph launch per FGMRES iteration for all problems) against the
+    same problems solved one after another in the FP32 form and in the plain FP64 form."""
+    import torch
+
+    from paper_2210_02690_gb300 import Batch, Solver
+
+    probs = si.batch_problems()
+
+    def make(spec, k, sd, **form):
+        w = torch.from_numpy(si.fourier_w(spec, k, seed=sd).ravel()).cuda()
+        s = Solver(spec, k, 1e-3, 0.01, w, nu1=2, nu2=2, **form)
+        b = s.apply_jacobian(torch.from_numpy(si.reference_solution(spec, k, seed=sd + 1)).cuda())
+        return s, b
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    f32 = dict(vcycle_prec="f32", factor_prec="f32")
+    pairs = [make(spec, k, sd, **f32) for spec, k, sd in probs]
+    solvers, rhs = [p[0] for p in pairs], [p[1] for p in pairs]
+    for s, b in pairs:  # warm-up
+        s.gmres_solve(b)
+    seq, t_seq = timed(lambda: [s.gmres_solve(b) for s, b in pairs])
+    batch = Batch(solvers)
+    batch.gmres_solve(rhs)
+    (xs, its_b, rel_b, ok_b), t_batch = timed(lambda: batch.gmres_solve(rhs))
+    batch.close()
+    for s in solvers:
+        s.close()
+    t64, its64 = 0.0, []
+    for spec, k, sd in probs:
+        s, b = make(spec, k, sd)
+        s.gmres_solve(b)
+        (_, it, _, _), t = timed(lambda: s.gmres_solve(b))
+        t64 += t
+        its64.append(it)
+        s.close()
+    dofs = sum(si.n_dofs(2, spec.n, k) for spec, k, _ in probs)
+    return {"workload": f"{len(probs)} rectangles of square cells, n_x, n_y in {{32..256}}, k in {{1, 2}}, "
+                        f"{dofs} space-time DoFs in total; FGMRES to 1e-8 relative",
+            "batched_f32_s": t_batch, "sequential_f32_s": t_seq, "sequential_f64_s": t64,
+            "speedup_batched_vs_sequential_f32": t_seq / t_batch, "speedup_batched_f32_vs_plain_f64": t64 / t_batch,
+            "iters_batched": [int(v) for v in its_b], "iters_f32": [int(r[1]) for r in seq],
+            "iters_f64": its64, "all_converged": bool(ok_b)}
+
+
+def warm_start_report() -> dict:
+    """Time march with the learned warm start (2D channel 128x32, dG(1), 400 slabs; network
+    trained on slabs 1-200, every slab 201-400 solved from three guesses to the absolute
+    tolerances of Sec. 4)."""
+    from paper_2210_02690_gb300.march import March, summary
+
+    cfg = si.MARCH
+    spec, k = cfg["spec"], cfg["k"]
+    t0 = time.perf_counter()
+    m = March(spec, k, cfg["nu"], cfg["tau"], si.march_initial_velocity(spec, pert=cfg["pert"]),
+              si.march_inflow(spec, k), vcycle_prec="f32", factor_prec="f32")
+    m.run(cfg["slabs"])
+    march_s = time.perf_counter() - t0
+    net, sv, losses, train_s = m.train(cfg["channels"], si.cnn_init(cfg["channels"]),
+                                       list(range(2, cfg["train_slabs"])))
+    ev = m.evaluate(list(range(cfg["train_slabs"], cfg["slabs"])), net, sv)
+    out = {"workload": f"channel {spec.n[0]}x{spec.n[1]} quads, dG({k}), tau {cfg['tau']}, {cfg['slabs']} slabs; "
+                       f"network {cfg['channels']} trained on slabs 1-{cfg['train_slabs']}, evaluated on "
+                       f"{cfg['train_slabs'] + 1}-{cfg['slabs']}",
+           "tolerances": "Newton absolute 1e-8, GMRES absolute 1e-9 (Sec. 4), same for every guess",
+           "march_s": march_s, "train_s": train_s, "train_steps": len(losses),
+           "train_loss_first_median_last20": [float(losses[0]), float(np.median(losses[-20:]))]}
+    for name, rows in ev.items():
+        sm = summary(rows)
+        out[name] = {key: sm[key] for key in ("newton_steps", "gmres_iters", "mean_r0", "seconds",
+                                              "max_final_over_tol", "all_converged")}
+    out["gmres_iters_saved_vs_fallback"] = 1.0 - out["network"]["gmres_iters"] / out["fallback"]["gmres_iters"]
+    out["time_to_tol_speedup_vs_fallback"] = out["fallback"]["seconds"] / out["network"]["seconds"]
+    net.close()
+    m.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -351,6 +442,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start report")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve report")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

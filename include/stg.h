@@ -222,9 +222,9 @@ stg_status stg_invert_local_noalloc(int n, long long count, const double* a, dou
 stg_status stg_autotune(stg_ctx* ctx, int* variant, double* sweep_ms);
 
 /* Batched solves of several independent problems (contexts of any mesh size and
- * k, each created with its own non-default stream): the V-cycles of all problems
- * are captured once into a single CUDA graph with one concurrent branch per
- * problem, and stg_batch_gmres_solve runs FGMRES (Sec. 3) on all problems in lock
+ * k, each created with a non-default stream; contexts may share one): the
+ * V-cycles of all problems are captured once into a single CUDA graph with one
+ * concurrent branch per problem, and stg_batch_gmres_solve runs FGMRES (Sec. 3) on all problems in lock
  * step, one graph launch per iteration.  b, x: HOST arrays of n DEVICE pointers
  * (C-ABI order of each problem); iters, rel: host arrays of n entries or NULL.
  * The contexts must not be used elsewhere while they belong to a batch, and the
@@ -234,6 +234,84 @@ stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out);
 stg_status stg_batch_gmres_solve(stg_batch* batch, const double* const* b, double* const* x, int* iters,
                                  double* rel);
 void stg_batch_destroy(stg_batch* batch);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start of the next time slab.  The paper has no learned part: it
+ * time-marches slab problems (Eq. (2.2)) and solves each by Newton (Sec. 3),
+ * and the Newton iteration needs an initial guess X^0 for slab n+1.  The
+ * fallback is stg_slab_initial_guess (slab n's end value at every Radau node).
+ * Here a small convolutional network, trained on the slabs the solver itself
+ * produced, predicts the part of slab n+1's velocity that linear extrapolation
+ * from the end values of slabs n-1 and n misses.
+ *
+ * Network: L = n_layers 3x3 convolutions, zero padding, with bias, tanh after
+ * every layer but the last:
+ *   y[b][o][i][j] = bias[o] + sum_{c,dy,dx} w[o][c][dy][dx] x[b][c][i+dy-1][j+dx-1].
+ * Tensors are FP32 NCHW arrays in DEVICE memory: [batch][channels][height][width].
+ * Parameters: one flat FP32 array, per layer w[c_out][c_in][3][3] then bias[c_out].
+ * Loss: mean of (y - t)^2 over all batch * c_L * height * width outputs.
+ * Training: Adam (Kingma & Ba) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8.
+ * All work runs on the stream given at creation; the network object owns its
+ * buffers and must not be used from two host threads at once.
+ * ------------------------------------------------------------------------ */
+typedef struct stg_cnn stg_cnn;
+typedef struct {
+  int n_layers;      /* 1..8 */
+  int channels[9];   /* channels[0] = input, channels[n_layers] = output; each 1..32 */
+  int height, width; /* image size */
+  int max_batch;     /* largest batch of any later call */
+} stg_cnn_desc;
+
+/* Creates the network with all parameters zero.  stream: cudaStream_t.
+ * STG_EINVAL for a bad descriptor, STG_ENOMEM when device memory runs out. */
+stg_status stg_cnn_create(const stg_cnn_desc* desc, void* stream, stg_cnn** out);
+/* Number of FP32 parameters (host output). */
+stg_status stg_cnn_n_params(const stg_cnn* net, long long* count);
+/* Copies all parameters from / to a HOST array of stg_cnn_n_params floats; set also
+ * resets the Adam moments and step count.  Both synchronise the stream. */
+stg_status stg_cnn_set_params(stg_cnn* net, const float* params);
+stg_status stg_cnn_get_params(stg_cnn* net, float* params);
+/* y[batch][c_L][H][W] = network(x[batch][c_0][H][W]); device pointers; asynchronous. */
+stg_status stg_cnn_forward(stg_cnn* net, const float* x, float* y, int batch);
+/* Gradient of the loss for input x and target t (device, [batch][c_L][H][W]) with
+ * respect to all parameters into grad (device, n_params floats, same layout as the
+ * parameters); loss (host, may be NULL) receives the loss, which synchronises. */
+stg_status stg_cnn_gradients(stg_cnn* net, const float* x, const float* t, int batch, float* grad, double* loss);
+/* One Adam update of the parameters with gradient grad (device). */
+stg_status stg_cnn_adam_step(stg_cnn* net, const float* grad, float lr, float beta1, float beta2, float eps);
+/* n_steps Adam steps with learning rate lr; step s uses the samples
+ * order[s*batch .. s*batch + batch-1] (HOST ints in [0, n_samples)) of the device
+ * arrays x_all[n_samples][c_0][H][W] and t_all[n_samples][c_L][H][W].  losses (host,
+ * n_steps doubles, may be NULL) receives each step's loss before its update.
+ * Synchronises the stream. */
+stg_status stg_cnn_train(stg_cnn* net, const float* x_all, const float* t_all, int n_samples, const int* order,
+                         int batch, int n_steps, float lr, double* losses);
+/* Text of the last error of this network (NULL net: of the last failed create). */
+const char* stg_cnn_last_error(const stg_cnn* net);
+stg_status stg_cnn_destroy(stg_cnn* net);
+
+/* Warm-start data of a 2D slab problem (finest level of ctx; STG_EINVAL in 3D).
+ * Slab vectors X_* are DEVICE arrays in C-ABI order; v_n = velocity of slab n at its
+ * last Radau node (t_n), dv = v_n - v_{n-1}, c_a = Radau nodes on [0, 1].  The image
+ * has height = 2 n_y + 1 and width = 2 n_x + 1 (the Q2 nodes, x fastest).
+ *   stg_warm_features: feat[2d][H][W] = [v_n / scale_v, dv / scale_d] (components in order).
+ *   stg_warm_target:   target[d(k+1)][H][W], channel a*d + comp =
+ *                      (v_{n+1}(t_n + c_a tau) - v_n - c_a dv) / scale_d.
+ *   stg_warm_start:    X0 (device, N doubles): velocity at node a = v_n + c_a dv
+ *                      + scale_d * network(feat)[a*d + comp] (net NULL: the network term
+ *                      is left out; it is also left out at Q2 nodes on Dirichlet faces,
+ *                      whose data is fixed), pressure at node a = p_n + c_a (p_n - p_{n-1});
+ *                      the network must have 2d input and d(k+1) output channels on
+ *                      the H x W grid.  Synchronises both streams when net is given.
+ *   stg_warm_scales:   root mean squares of the entries of v_n and of dv (host outputs,
+ *                      each may be NULL); synchronises. */
+stg_status stg_warm_features(stg_ctx* ctx, const double* X_n, const double* X_prev, float scale_v, float scale_d,
+                             float* feat);
+stg_status stg_warm_target(stg_ctx* ctx, const double* X_n, const double* X_prev, const double* X_next,
+                           float scale_d, float* target);
+stg_status stg_warm_start(stg_ctx* ctx, stg_cnn* net, const double* X_n, const double* X_prev, float scale_v,
+                          float scale_d, double* X0);
+stg_status stg_warm_scales(stg_ctx* ctx, const double* X_n, const double* X_prev, double* rms_v, double* rms_dv);
 
 /* Text of the last error of this context (or of the last failed stg_setup
  * when ctx is NULL).  Valid until the next call on the same context. */

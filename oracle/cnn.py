@@ -141,9 +141,27 @@ def target(lev, X_n, X_nm1, X_np1, scale_d):
     return np.concatenate(out)
 
 
+def dirichlet_node_mask(lev):
+    """(H, W) booleans: Q2 nodes on a face with Dirichlet data (bit 1 << (2 dir + side))."""
+    H, W = lev.nn[1], lev.nn[0]
+    m = np.zeros((H, W), dtype=bool)
+    bits = lev.spec.dirichlet
+    if bits & 1:
+        m[:, 0] = True
+    if bits & 2:
+        m[:, -1] = True
+    if bits & 4:
+        m[0, :] = True
+    if bits & 8:
+        m[-1, :] = True
+    return m
+
+
 def guess(lev, params, X_n, X_nm1, scale_v, scale_d):
     """Initial guess for the next slab: velocity v_n + c_a dv + scale_d * net_a (net = None: 0),
-    pressure p_n + c_a (p_n - p_{n-1}) (linear extrapolation)."""
+    pressure p_n + c_a (p_n - p_{n-1}) (linear extrapolation).  The network term is left out
+    at nodes on Dirichlet faces: the boundary data does not change, and the Nitsche penalty
+    weights a boundary error with gamma / h, far above the weight of an interior error."""
     from .timebasis import radau_nodes
     c = radau_nodes(lev.k)
     d = lev.dim
@@ -153,7 +171,7 @@ def guess(lev, params, X_n, X_nm1, scale_v, scale_d):
     dp = p - _end_pres(lev, X_nm1)
     if params is not None:
         y, _ = forward(params, features(lev, X_n, X_nm1, scale_v, scale_d)[None])
-        y = y[0]
+        y = np.where(dirichlet_node_mask(lev)[None], 0.0, y[0])
     X0 = np.zeros((lev.k + 1, lev.R + lev.S))
     for a in range(lev.k + 1):
         va = v + c[a] * dv

@@ -30,7 +30,10 @@ EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
             "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_newton_slab",
             "stg_slab_initial_guess", "stg_autotune", "stg_batch_create", "stg_batch_gmres_solve",
-            "stg_batch_destroy", "stg_last_error", "stg_destroy")
+            "stg_batch_destroy", "stg_cnn_create", "stg_cnn_n_params", "stg_cnn_set_params",
+            "stg_cnn_get_params", "stg_cnn_forward", "stg_cnn_gradients", "stg_cnn_adam_step", "stg_cnn_train",
+            "stg_cnn_last_error", "stg_cnn_destroy", "stg_warm_features", "stg_warm_target", "stg_warm_start",
+            "stg_warm_scales", "stg_last_error", "stg_destroy")
 
 
 class StgError(RuntimeError):
@@ -52,6 +55,11 @@ class stg_options(ctypes.Structure):
                 ("gamma2", ctypes.c_double), ("factor_prec", ctypes.c_int), ("vcycle_prec", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
                 ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int), ("coarse_refine", ctypes.c_int)]
+
+
+class stg_cnn_desc(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("channels", ctypes.c_int * 9), ("height", ctypes.c_int),
+                ("width", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 _lib = None
@@ -92,6 +100,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_batch_gmres_solve": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I),
                                       ctypes.POINTER(D)]),
         "stg_batch_destroy": (None, [P]),
+        "stg_cnn_create": (I, [ctypes.POINTER(stg_cnn_desc), P, ctypes.POINTER(P)]),
+        "stg_cnn_n_params": (I, [P, ctypes.POINTER(LL)]),
+        "stg_cnn_set_params": (I, [P, P]),
+        "stg_cnn_get_params": (I, [P, P]),
+        "stg_cnn_forward": (I, [P, P, P, I]),
+        "stg_cnn_gradients": (I, [P, P, P, I, P, ctypes.POINTER(D)]),
+        "stg_cnn_adam_step": (I, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "stg_cnn_train": (I, [P, P, P, I, P, I, I, ctypes.c_float, P]),
+        "stg_cnn_last_error": (ctypes.c_char_p, [P]),
+        "stg_cnn_destroy": (I, [P]),
+        "stg_warm_features": (I, [P, P, P, ctypes.c_float, ctypes.c_float, P]),
+        "stg_warm_target": (I, [P, P, P, P, ctypes.c_float, P]),
+        "stg_warm_start": (I, [P, P, P, P, ctypes.c_float, ctypes.c_float, P]),
+        "stg_warm_scales": (I, [P, P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "stg_last_error": (ctypes.c_char_p, [P]),
         "stg_destroy": (None, [P]),
     }
@@ -271,6 +293,43 @@ class Solver:
         self._call(self.lib.stg_slab_initial_guess, self._p(Xp), self._p(X0))
         return X0
 
+    # -- learned warm start of the next slab (2D)
+    def node_grid(self):
+        """(height, width) of the finest level's Q2 node grid."""
+        return 2 * self.spec.n[1] + 1, 2 * self.spec.n[0] + 1
+
+    def warm_features(self, X_n, X_prev, scale_v: float, scale_d: float, out=None):
+        Xn, Xp = self._dev(X_n), self._dev(X_prev)
+        H, W = self.node_grid()
+        f = out if out is not None else self.torch.empty((2 * self.spec.dim, H, W), dtype=self.torch.float32,
+                                                         device=self.device)
+        self._call(self.lib.stg_warm_features, self._p(Xn), self._p(Xp), scale_v, scale_d, self._p(f))
+        return f
+
+    def warm_target(self, X_n, X_prev, X_next, scale_d: float, out=None):
+        Xn, Xp, Xx = self._dev(X_n), self._dev(X_prev), self._dev(X_next)
+        H, W = self.node_grid()
+        t = out if out is not None else self.torch.empty((self.spec.dim * (self.k + 1), H, W),
+                                                         dtype=self.torch.float32, device=self.device)
+        self._call(self.lib.stg_warm_target, self._p(Xn), self._p(Xp), self._p(Xx), scale_d, self._p(t))
+        return t
+
+    def warm_start(self, net, X_n, X_prev, scale_v: float, scale_d: float):
+        """Initial guess for the next slab: linear extrapolation plus the network's correction
+        (net None: linear extrapolation alone)."""
+        Xn, Xp = self._dev(X_n), self._dev(X_prev)
+        X0 = self.torch.empty_like(Xn)
+        self._call(self.lib.stg_warm_start, net.handle if net is not None else None, self._p(Xn), self._p(Xp),
+                   scale_v, scale_d, self._p(X0))
+        return X0
+
+    def warm_scales(self, X_n, X_prev):
+        """(rms of v_n, rms of v_n - v_{n-1}) over the nodal velocity entries."""
+        Xn, Xp = self._dev(X_n), self._dev(X_prev)
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._call(self.lib.stg_warm_scales, self._p(Xn), self._p(Xp), ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
     def local_inverse(self, level: int, cell: int) -> np.ndarray:
         n = self.sizes(level)[2]
         out = np.zeros((n, n))
@@ -351,6 +410,114 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.stg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cnn:
+    """The warm-start network (stg_cnn): 3x3 convolutions with tanh, trained with Adam.
+
+    channels = [c_0, ..., c_L]; tensors are float32 CUDA tensors [batch][c][height][width].
+    """
+
+    def __init__(self, channels, height: int, width: int, max_batch: int):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2210_02690_gb300 needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.lib = load_library()
+        self.channels = list(channels)
+        self.height, self.width = height, width
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.Stream(device=self.device)
+        d = stg_cnn_desc()
+        d.n_layers = len(channels) - 1
+        for i, c in enumerate(channels):
+            d.channels[i] = c
+        d.height, d.width, d.max_batch = height, width, max_batch
+        h = ctypes.c_void_p()
+        st = self.lib.stg_cnn_create(ctypes.byref(d), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != STG_OK:
+            msg = self.lib.stg_cnn_last_error(None) or self.lib.stg_last_error(None)
+            raise StgError(st, msg.decode() if msg else "")
+        self.handle = h
+        n = ctypes.c_longlong()
+        self.lib.stg_cnn_n_params(h, ctypes.byref(n))
+        self.n_params = n.value
+
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _leave(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _call(self, fn, *args):
+        self._enter()
+        try:
+            st = fn(self.handle, *args)
+            if st != STG_OK:
+                msg = self.lib.stg_cnn_last_error(self.handle)
+                raise StgError(st, msg.decode() if msg else "")
+        finally:
+            self._leave()
+
+    def _f32(self, a):
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+        return a.to(device=self.device, dtype=t.float32).contiguous()
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        assert a.size == self.n_params
+        self._call(self.lib.stg_cnn_set_params, a.ctypes.data_as(ctypes.c_void_p))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(self.n_params, dtype=np.float32)
+        self._call(self.lib.stg_cnn_get_params, a.ctypes.data_as(ctypes.c_void_p))
+        return a
+
+    def forward(self, x):
+        x = self._f32(x)
+        y = self.torch.empty((x.shape[0], self.channels[-1], self.height, self.width), dtype=self.torch.float32,
+                             device=self.device)
+        self._call(self.lib.stg_cnn_forward, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                   x.shape[0])
+        return y
+
+    def gradients(self, x, t):
+        """(loss, flat gradient tensor)."""
+        x, t = self._f32(x), self._f32(t)
+        g = self.torch.empty(self.n_params, dtype=self.torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        self._call(self.lib.stg_cnn_gradients, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                   x.shape[0], ctypes.c_void_p(g.data_ptr()), ctypes.byref(loss))
+        return loss.value, g
+
+    def adam_step(self, grad, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+        g = self._f32(grad)
+        self._call(self.lib.stg_cnn_adam_step, ctypes.c_void_p(g.data_ptr()), lr, beta1, beta2, eps)
+
+    def train(self, x_all, t_all, order, batch: int, lr: float):
+        """Adam steps over the sample indices `order` (len = steps * batch); returns the losses."""
+        x, t = self._f32(x_all), self._f32(t_all)
+        order = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        steps = order.size // batch
+        losses = np.zeros(steps)
+        self._call(self.lib.stg_cnn_train, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                   x.shape[0], order.ctypes.data_as(ctypes.c_void_p), batch, steps, lr,
+                   losses.ctypes.data_as(ctypes.c_void_p))
+        return losses
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.stg_cnn_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

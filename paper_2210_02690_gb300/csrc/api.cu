@@ -6,6 +6,7 @@
 #include <new>
 #include <vector>
 
+#include "cnn.cuh"
 #include "coarse.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -215,6 +216,9 @@ struct stg_ctx {
   // damped Newton (finest level, internal layout, FP64)
   double *nb = nullptr, *nX = nullptr, *nr = nullptr, *nC = nullptr, *nXt = nullptr;
   double *nf = nullptr, *ng = nullptr, *rhs_tab = nullptr;
+  // warm start of the next slab: network input and reduction scratch
+  float* wfeat = nullptr;
+  double* wsum = nullptr;
   std::vector<void*> owned;
   std::string err;
   bool pure_dirichlet = false;
@@ -1069,6 +1073,93 @@ stg_status stg_slab_initial_guess(stg_ctx* c, const double* X_prev, double* X0) 
   }
 }
 
+namespace {
+
+// The warm-start calls work on a 2D finest level; the network must map 2d input channels
+// to d(k+1) output channels on the H x W node grid.
+stg_status warm_check(stg_ctx* c, const stg_cnn* net) {
+  const Geom& g = c->lv.back().g;
+  if (g.dim != 2) {
+    c->err = "warm start: the network works on 2D node grids";
+    return STG_EINVAL;
+  }
+  if (net && (net->ch[0] != 2 * g.dim || net->ch[net->L] != g.dim * g.nt || net->H != g.nn[1] ||
+              net->W != g.nn[0])) {
+    c->err = "warm start: network channels or grid do not match the slab problem";
+    return STG_EINVAL;
+  }
+  return STG_OK;
+}
+
+}  // namespace
+
+stg_status stg_warm_features(stg_ctx* c, const double* X_n, const double* X_prev, float scale_v, float scale_d,
+                             float* feat) {
+  if (!c || !X_n || !X_prev || !feat || !(scale_v > 0.f) || !(scale_d > 0.f)) return STG_EINVAL;
+  const stg_status s = warm_check(c, nullptr);
+  if (s != STG_OK) return s;
+  try {
+    warm_features(c->lv.back().g, X_n, X_prev, scale_v, scale_d, feat, c->st);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_warm_target(stg_ctx* c, const double* X_n, const double* X_prev, const double* X_next, float scale_d,
+                           float* target) {
+  if (!c || !X_n || !X_prev || !X_next || !target || !(scale_d > 0.f)) return STG_EINVAL;
+  const stg_status s = warm_check(c, nullptr);
+  if (s != STG_OK) return s;
+  try {
+    warm_target(c->lv.back().g, c->td, X_n, X_prev, X_next, scale_d, target, c->st);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_warm_start(stg_ctx* c, stg_cnn* net, const double* X_n, const double* X_prev, float scale_v,
+                          float scale_d, double* X0) {
+  if (!c || !X_n || !X_prev || !X0 || !(scale_v > 0.f) || !(scale_d > 0.f)) return STG_EINVAL;
+  const stg_status s = warm_check(c, net);
+  if (s != STG_OK) return s;
+  try {
+    const Geom& g = c->lv.back().g;
+    const float* y = nullptr;
+    if (net) {
+      if (!c->wfeat) c->wfeat = dalloc<float>(c, 2LL * g.dim * g.n_nodes);
+      // the network's buffers are used on this context's stream
+      STG_CUDA_OK(cudaStreamSynchronize(net->st));
+      warm_features(g, X_n, X_prev, scale_v, scale_d, c->wfeat, c->st);
+      y = cnn_forward(net, c->wfeat, 1, c->st);
+    }
+    warm_guess(g, c->td, X_n, X_prev, y, scale_d, X0, c->st);
+    if (net) STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_warm_scales(stg_ctx* c, const double* X_n, const double* X_prev, double* rms_v, double* rms_dv) {
+  if (!c || !X_n || !X_prev) return STG_EINVAL;
+  try {
+    const Geom& g = c->lv.back().g;
+    if (!c->wsum) c->wsum = dalloc<double>(c, 514);
+    warm_sums(g, X_n, X_prev, c->wsum, c->st);
+    double h[2];
+    STG_CUDA_OK(cudaMemcpyAsync(h, c->wsum + 512, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    const double R = (double)(g.nvel / g.nt);
+    if (rms_v) *rms_v = std::sqrt(h[0] / R);
+    if (rms_dv) *rms_dv = std::sqrt(h[1] / R);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
 stg_status stg_get_sizes(const stg_ctx* c, int level, long long* n_dofs, long long* n_cells, int* n_patch) {
   if (!c || level < 0 || level >= (int)c->lv.size()) return STG_EINVAL;
   const Geom& g = c->lv[level].g;
@@ -1189,9 +1280,23 @@ struct stg_batch {
   std::vector<stg_ctx*> ctx;
   cudaStream_t main = nullptr;
   cudaGraphExec_t graph = nullptr;
-  long long graph_kernels = 0;
+  std::vector<long long> branch_kernels;  // kernels of each problem's V-cycle
   std::vector<cudaEvent_t> ev;
+  std::vector<cudaStream_t> branch;  // one capture stream per problem
+  cudaGraphConditionalHandle* handles = nullptr;  // device: the IF handle of each branch
+  int* live_dev = nullptr;                        // device: 1 = run the branch in the next launch
+  int* live_host = nullptr;                       // pinned staging of live_dev
 };
+
+namespace stg {
+
+// Head of the batch graph: opens the IF node of every problem still iterating.
+__global__ void set_branch_conditions(const cudaGraphConditionalHandle* h, const int* live, int n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    for (int p = 0; p < n; ++p) cudaGraphSetConditional(h[p], live[p] ? 1u : 0u);
+}
+
+}  // namespace stg
 
 extern "C" {
 
@@ -1203,40 +1308,83 @@ stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out) {
   try {
     for (int p = 0; p < n; ++p) {
       stg_ctx* c = ctxs[p];
-      if (!c || !c->st) throw Error{STG_EINVAL, "every batched context needs its own non-default stream"};
+      if (!c || !c->st) throw Error{STG_EINVAL, "every batched context needs a non-default stream"};
       for (int q = 0; q < p; ++q)
-        if (ctxs[q]->st == c->st) throw Error{STG_EINVAL, "batched contexts must use distinct streams"};
+        if (ctxs[q] == c) throw Error{STG_EINVAL, "a context appears twice in the batch"};
       if (c->prof_on) throw Error{STG_EINVAL, "turn profiling off before batching"};
       B->ctx.push_back(c);
     }
     STG_CUDA_OK(cudaStreamCreateWithFlags(&B->main, cudaStreamNonBlocking));
     B->ev.resize(n + 1);
     for (auto& e : B->ev) STG_CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    B->branch.resize(n, nullptr);
+    for (auto& b : B->branch) STG_CUDA_OK(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+    B->branch_kernels.assign(n, 0);
     for (stg_ctx* c : B->ctx) STG_CUDA_OK(cudaStreamSynchronize(c->st));
-    // one graph: every problem's V-cycle as its own branch (fork from and join into the batch stream)
+    STG_CUDA_OK(cudaMalloc(&B->handles, sizeof(cudaGraphConditionalHandle) * n));
+    STG_CUDA_OK(cudaMalloc(&B->live_dev, sizeof(int) * n));
+    STG_CUDA_OK(cudaMallocHost(&B->live_host, sizeof(int) * n));
+    // One graph: a head kernel that sets the conditions, then every problem's V-cycle as the
+    // body of its own IF node (all bodies depend only on the head, so they run concurrently).
+    // Each body is captured on a stream of its own, so the contexts' streams may coincide.
     cudaGraph_t graph = nullptr;
-    const long long before = launch_counter();
-    STG_CUDA_OK(cudaStreamBeginCapture(B->main, cudaStreamCaptureModeThreadLocal));
+    STG_CUDA_OK(cudaGraphCreate(&graph, 0));
     try {
-      STG_CUDA_OK(cudaEventRecord(B->ev[n], B->main));
+      std::vector<cudaGraphConditionalHandle> hs(n);
+      for (int p = 0; p < n; ++p)
+        STG_CUDA_OK(cudaGraphConditionalHandleCreate(&hs[p], graph, 0, cudaGraphCondAssignDefault));
+      STG_CUDA_OK(cudaMemcpy(B->handles, hs.data(), sizeof(cudaGraphConditionalHandle) * n,
+                             cudaMemcpyHostToDevice));
+      cudaGraphNode_t head = nullptr;
+      cudaKernelNodeParams kp = {};
+      const cudaGraphConditionalHandle* hdev = B->handles;
+      const int* ldev = B->live_dev;
+      int nn = n;
+      void* args[] = {(void*)&hdev, (void*)&ldev, (void*)&nn};
+      kp.func = (void*)set_branch_conditions;
+      kp.gridDim = dim3(1);
+      kp.blockDim = dim3(32);
+      kp.kernelParams = args;
+      STG_CUDA_OK(cudaGraphAddKernelNode(&head, graph, nullptr, 0, &kp));
       for (int p = 0; p < n; ++p) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hs[p];
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        STG_CUDA_OK(cudaGraphAddNode(&node, graph, &head, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
         stg_ctx* c = B->ctx[p];
-        STG_CUDA_OK(cudaStreamWaitEvent(c->st, B->ev[n], 0));
-        vcycle_body(c);
-        STG_CUDA_OK(cudaEventRecord(B->ev[p], c->st));
-        STG_CUDA_OK(cudaStreamWaitEvent(B->main, B->ev[p], 0));
+        const cudaStream_t saved = c->st;
+        c->st = B->branch[p];
+        const long long before = launch_counter();
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0,
+                                                       cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+          try {
+            vcycle_body(c);
+          } catch (...) {
+            cudaGraph_t g2 = nullptr;
+            cudaStreamEndCapture(c->st, &g2);
+            c->st = saved;
+            launch_counter() = before;
+            throw;
+          }
+          cudaGraph_t g2 = nullptr;
+          ce = cudaStreamEndCapture(c->st, &g2);
+        }
+        c->st = saved;
+        B->branch_kernels[p] = launch_counter() - before;
+        launch_counter() = before;  // capturing enqueues nothing; launches are counted per live branch
+        STG_CUDA_OK(ce);
       }
+      STG_CUDA_OK(cudaGraphInstantiate(&B->graph, graph, 0));
     } catch (...) {
-      cudaStreamEndCapture(B->main, &graph);
-      if (graph) cudaGraphDestroy(graph);
+      cudaGraphDestroy(graph);
       throw;
     }
-    STG_CUDA_OK(cudaStreamEndCapture(B->main, &graph));
-    B->graph_kernels = launch_counter() - before;
-    launch_counter() = before;
-    const cudaError_t e = cudaGraphInstantiate(&B->graph, graph, 0);
     cudaGraphDestroy(graph);
-    STG_CUDA_OK(e);
     *out = B;
     return STG_OK;
   } catch (const Error& e) {
@@ -1267,13 +1415,18 @@ stg_status stg_batch_gmres_solve(stg_batch* B, const double* const* b, double* c
         if (!S[p].done) live.push_back(p);
       }
       if (live.empty()) break;
+      for (int p = 0; p < n; ++p) B->live_host[p] = 0;
+      long long kernels = 1;
       for (int p : live) {
         fg_pre(S[p]);
         STG_CUDA_OK(cudaEventRecord(B->ev[p], B->ctx[p]->st));
         STG_CUDA_OK(cudaStreamWaitEvent(B->main, B->ev[p], 0));
+        B->live_host[p] = 1;
+        kernels += B->branch_kernels[p];
       }
-      STG_CUDA_OK(cudaGraphLaunch(B->graph, B->main));  // all problems' V-cycles, concurrently
-      launch_counter() += B->graph_kernels;
+      STG_CUDA_OK(cudaMemcpyAsync(B->live_dev, B->live_host, sizeof(int) * n, cudaMemcpyHostToDevice, B->main));
+      STG_CUDA_OK(cudaGraphLaunch(B->graph, B->main));  // the live problems' V-cycles, concurrently
+      launch_counter() += kernels;
       STG_CUDA_OK(cudaEventRecord(B->ev[n], B->main));
       for (int p : live) {
         STG_CUDA_OK(cudaStreamWaitEvent(B->ctx[p]->st, B->ev[n], 0));
@@ -1306,6 +1459,11 @@ void stg_batch_destroy(stg_batch* B) {
   for (auto& e : B->ev)
     if (e) cudaEventDestroy(e);
   if (B->main) cudaStreamDestroy(B->main);
+  for (auto& b : B->branch)
+    if (b) cudaStreamDestroy(b);
+  cudaFree(B->handles);
+  cudaFree(B->live_dev);
+  if (B->live_host) cudaFreeHost(B->live_host);
   delete B;
 }
 

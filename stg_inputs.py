@@ -198,3 +198,53 @@ def smoothed_dofs_per_cycle(spec: MeshSpec, k: int, nu1: int, nu2: int) -> int:
     """Space-time DoFs smoothed by one V-cycle: sum over levels >= 1 of (nu1 + nu2) N_l."""
     return sum((nu1 + nu2) * n_dofs(spec.dim, spec.cells(l), k) for l in range(1, spec.n_levels))
 
+
+
+# ---------------------------------------------------------------- time march with a learned warm start
+# 2D channel 128x32 -> 16x4, dG(1), tau=0.005, nu=1e-3, 400 slabs; the initial velocity is the
+# Poiseuille profile plus a seeded curl perturbation of amplitude 0.5 (an impulsive start: the
+# perturbation need not satisfy the boundary conditions); inflow data g = Poiseuille profile at
+# every Radau node; the network is trained on slabs 1-200 and evaluated on 201-400.
+MARCH = dict(spec=MeshSpec(2, (128, 32), (0.0, 0.0), (2.2, 0.41), 4, FACE_XLO | FACE_YLO | FACE_YHI), k=1,
+             nu=1e-3, tau=0.005, slabs=400, train_slabs=200, pert=0.5, channels=(4, 16, 16, 4))
+
+
+def march_initial_velocity(spec: MeshSpec, seed: int = BASE_SEED, pert: float = 0.5) -> np.ndarray:
+    """v(0) at the finest Q2 nodes, (R,) in the C-ABI order."""
+    return channel_w(spec, 0, seed=seed, pert=pert)[0].copy()
+
+
+def march_inflow(spec: MeshSpec, k: int) -> np.ndarray:
+    """Dirichlet data g: the Poiseuille profile (u_max = 1.5) at every Radau node, (k+1, R)."""
+    return channel_w(spec, k, pert=0.0)
+
+
+def cnn_init(channels, seed: int = BASE_SEED, last_scale: float = 0.1) -> np.ndarray:
+    """Flat initial parameters of the warm-start network: per layer w[c_out][c_in][3][3] ~
+    N(0, 1/(9 c_in)) (the last layer's scaled by last_scale), then zero biases; float32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for li, (cin, cout) in enumerate(zip(channels[:-1], channels[1:])):
+        w = rng.standard_normal(cout * cin * 9) / np.sqrt(9.0 * cin)
+        if li == len(channels) - 2:
+            w *= last_scale
+        out += [w, np.zeros(cout)]
+    return np.concatenate(out).astype(np.float32)
+
+
+def batch_problems(count: int = 64, seed: int = BASE_SEED):
+    """Uneven batch of 2D problems: n_x, n_y uniform in {32, 64, 128, 256}, k uniform in {1, 2},
+    coarsened by 2 until min(n_x, n_y) = 4, Dirichlet on all faces, tau = 0.01, nu = 1e-3;
+    problem i uses w and x* seeds BASE_SEED + i and BASE_SEED + i + 1 (as square8_k0).  The
+    domain is [0, n_x / m] x [0, n_y / m] with m = max(n_x, n_y), so every cell is a square
+    (on the unit square a 32 x 256 mesh has cells of aspect ratio 8, on which the Vanka
+    V-cycle, in the oracle as on the GPU, stalls).  Returns [(spec, k, seed_i)]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx, ny = (int(v) for v in rng.choice([32, 64, 128, 256], 2))
+        k = int(rng.choice([1, 2]))
+        levels = int(np.log2(min(nx, ny) // 4)) + 1
+        m = max(nx, ny)
+        out.append((MeshSpec(2, (nx, ny), (0.0, 0.0), (nx / m, ny / m), levels, ALL2), k, seed + i))
+    return out

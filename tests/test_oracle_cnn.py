@@ -118,7 +118,20 @@ def test_guess_places_network_channels_at_radau_nodes():
     params = [(np.zeros((6, 4, 3, 3)), bias)]
     base = cnn.guess(lev, None, Xn, Xm, 1.0, 0.5).reshape(3, lev.R + lev.S)
     got = cnn.guess(lev, params, Xn, Xm, 1.0, 0.5).reshape(3, lev.R + lev.S)
+    on_xlo = np.isclose(xy[:, 0], 0.0)          # the only Dirichlet face of this mesh
+    assert on_xlo.sum() == lev.nn[1]
     for a in range(3):
         dv = (got[a, :lev.R] - base[a, :lev.R]).reshape(-1, 2)
-        assert np.allclose(dv, 0.5 * bias[2 * a:2 * a + 2], atol=1e-14)
+        assert np.allclose(dv[~on_xlo], 0.5 * bias[2 * a:2 * a + 2], atol=1e-14)
+        assert np.array_equal(dv[on_xlo], np.zeros((on_xlo.sum(), 2)))
         assert np.array_equal(got[a, lev.R:], base[a, lev.R:])
+
+
+def test_dirichlet_mask_marks_the_faces():
+    import stg_inputs as si
+    from oracle import mesh
+    spec = si.MeshSpec(2, (4, 2), (0.0, 0.0), (1.0, 1.0), 1, si.FACE_XHI | si.FACE_YLO)
+    lev = mesh.Level(spec, 0, 0)
+    m = cnn.dirichlet_node_mask(lev)
+    xy = si.node_coords(spec, 0).reshape(lev.nn[1], lev.nn[0], 2)
+    assert np.array_equal(m, np.isclose(xy[..., 0], 1.0) | np.isclose(xy[..., 1], 0.0))
