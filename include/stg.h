@@ -214,12 +214,19 @@ long long stg_kernel_launches(void);
  * stg_last_error(NULL)) or STG_ECUDA on failure. */
 stg_status stg_invert_local_noalloc(int n, long long count, const double* a, double* a_inv, void* stream);
 
-/* Autotuner: times every variant of the smoother's colour kernel (3 column-batch
- * depths x 3 CTA sizes) on every level >= 1 and keeps the fastest per level; the
+/* Autotuner: times every variant of the smoother's colour kernel (one warp per
+ * patch: 3 column-batch depths x 3 CTA sizes; factors staged in shared memory by
+ * bulk copies: 4 pipeline shapes) on every level >= 1 and keeps the fastest per level; the
  * V-cycle graph is recaptured.  variant (host, may be NULL) receives the finest
  * level's choice, sweep_ms (host, may be NULL) the finest level's time of one
  * sweep's colour kernels.  (Engineering service; the paper has no counterpart.) */
 stg_status stg_autotune(stg_ctx* ctx, int* variant, double* sweep_ms);
+
+/* Colour-kernel variant of level `level` >= 1 (0..12, as timed by stg_autotune):
+ * read it, or set it (the V-cycle graph is recaptured), e.g. to replay a choice
+ * made in another run.  STG_EINVAL for a level or variant out of range. */
+stg_status stg_get_colour_variant(const stg_ctx* ctx, int level, int* variant);
+stg_status stg_set_colour_variant(stg_ctx* ctx, int level, int variant);
 
 /* Batched solves of several independent problems (contexts of any mesh size and
  * k, each created with a non-default stream; contexts may share one): the

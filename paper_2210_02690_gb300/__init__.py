@@ -29,7 +29,8 @@ EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
             "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_newton_slab",
-            "stg_slab_initial_guess", "stg_autotune", "stg_batch_create", "stg_batch_gmres_solve",
+            "stg_slab_initial_guess", "stg_autotune", "stg_get_colour_variant", "stg_set_colour_variant",
+            "stg_batch_create", "stg_batch_gmres_solve",
             "stg_batch_destroy", "stg_cnn_create", "stg_cnn_n_params", "stg_cnn_set_params",
             "stg_cnn_get_params", "stg_cnn_forward", "stg_cnn_gradients", "stg_cnn_adam_step", "stg_cnn_train",
             "stg_cnn_last_error", "stg_cnn_destroy", "stg_warm_features", "stg_warm_target", "stg_warm_start",
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_newton_slab": (I, [P, P, P, P, P, D, D, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "stg_slab_initial_guess": (I, [P, P, P]),
         "stg_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stg_get_colour_variant": (I, [P, I, ctypes.POINTER(I)]),
+        "stg_set_colour_variant": (I, [P, I, I]),
         "stg_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P)]),
         "stg_batch_gmres_solve": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I),
                                       ctypes.POINTER(D)]),
@@ -353,6 +356,20 @@ class Solver:
         v, ms = ctypes.c_int(), ctypes.c_double()
         self._call(self.lib.stg_autotune, ctypes.byref(v), ctypes.byref(ms))
         return v.value, ms.value
+
+    def colour_variants(self):
+        """Colour-kernel variant of every level >= 1 (finest last)."""
+        out = []
+        for level in range(1, self.spec.n_levels):
+            v = ctypes.c_int()
+            _check(self.lib, self.ctx, self.lib.stg_get_colour_variant(self.ctx, level, ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
+    def set_colour_variants(self, variants):
+        """Sets the colour-kernel variant of levels 1.. (as returned by colour_variants)."""
+        for level, v in enumerate(variants, start=1):
+            self._call(self.lib.stg_set_colour_variant, level, int(v))
 
     def kernel_launches(self) -> int:
         return int(self.lib.stg_kernel_launches())

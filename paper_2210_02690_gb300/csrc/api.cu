@@ -178,6 +178,7 @@ struct LevelBufs {
   long long nnzb = 0;
   double *vv = nullptr, *vp = nullptr, *pv = nullptr;
   float *vv32 = nullptr, *vp32 = nullptr, *pv32 = nullptr;
+  float *mk32 = nullptr, *ak32 = nullptr;  // Kronecker-split FP32 velocity rows (levels >= 1, 2D)
   void* jinv = nullptr;
   double* w = nullptr;
   double* asm_tab = nullptr;
@@ -191,6 +192,9 @@ struct stg_ctx {
   int k = 0;
   double nu = 0, tau = 0;
   cudaStream_t st = nullptr;
+  // side stream of the set-up: the coarse factorisation overlaps the finer levels' work
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   TimeData td{};
   std::vector<LevelBufs> lv;
   CoarseSolver<double> coarse64;  // FP64 form
@@ -286,8 +290,20 @@ void linearise_internal(stg_ctx* c) {
       const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
       convert(nvp, L.vp, L.vp32, c->st);
       convert(nvp, L.pv, L.pv32, c->st);
+      if (L.mk32) kron_split(L.g, L.nnzb, L.vv, c->td, L.mk32, L.ak32, c->st);
     }
-    if (l == 0) continue;
+    if (l == 0) {
+      // the coarse factorisation (a chain of small, latency-bound launches) needs only J_0:
+      // it runs on the side stream while the finer levels are assembled and inverted
+      STG_CUDA_OK(cudaEventRecord(c->fork, c->st));
+      STG_CUDA_OK(cudaStreamWaitEvent(c->side, c->fork, 0));
+      if (vc64(c))
+        c->coarse64.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->side);
+      else
+        c->coarse32.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->side);
+      STG_CUDA_OK(cudaEventRecord(c->join, c->side));
+      continue;
+    }
     const int fp = c->opt.factor_prec;
     // FP32/BF16 factors are computed in FP32 on the equilibrated J_K; FP64 factors in FP64
     const int cf32 = fp != STG_F64 ? 1 : 0;
@@ -302,11 +318,7 @@ void linearise_internal(stg_ctx* c) {
                                     (__nv_bfloat16*)L.jinv, cf32, c->status,
                                     c->inv_scratch, c->inv_flags, c->st);
   }
-  LevelBufs& C0 = c->lv[0];
-  if (vc64(c))
-    c->coarse64.factor(C0.rowptr, C0.colidx, C0.vv, C0.vp, C0.pv, c->st);
-  else
-    c->coarse32.factor(C0.rowptr, C0.colidx, C0.vv, C0.vp, C0.pv, c->st);
+  STG_CUDA_OK(cudaStreamWaitEvent(c->st, c->join, 0));
   int hs[4];
   STG_CUDA_OK(cudaMemcpyAsync(hs, c->status, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
   STG_CUDA_OK(cudaStreamSynchronize(c->st));
@@ -349,7 +361,11 @@ void record_event(cudaEvent_t ev, cudaStream_t st) {
 
 template <typename VT>
 void residual(stg_ctx* c, const LevelBufs& L, const VT* x, const VT* b, VT* r) {
-  apply_operator<VT, VT>(L.g, L.rowptr, L.colidx, Ops<VT>::vv(L), Ops<VT>::vp(L), Ops<VT>::pv(L), x, b, r, c->st);
+  if (std::is_same<VT, float>::value && L.mk32)
+    apply_operator_kron(L.g, c->td, L.rowptr, L.mk32, L.ak32, L.vp32, L.pv32, (const float*)x, (const float*)b,
+                        (float*)r, c->st);
+  else
+    apply_operator<VT, VT>(L.g, L.rowptr, L.colidx, Ops<VT>::vv(L), Ops<VT>::vp(L), Ops<VT>::pv(L), x, b, r, c->st);
 }
 
 template <typename VT, typename FT>
@@ -650,6 +666,8 @@ stg_status fg_result(const FgState& S, int* iters_out, double* rel_out) {
   return S.beta <= S.tol || S.bnorm == 0.0 ? STG_OK : STG_ENOCONV;
 }
 
+const char* const kColourTimeout = "a staged smoother kernel gave up waiting for a bulk copy";
+
 stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double* rel_out) {
   FgState S;
   fg_begin(S, c, b, x);
@@ -665,6 +683,7 @@ stg_status fgmres(stg_ctx* c, const double* b, double* x, int* iters_out, double
     prof_collect(c);
     fg_update(S);
   }
+  if (colour_kernel_timed_out(c->st)) throw Error{STG_ETIMEOUT, kColourTimeout};
   return fg_result(S, iters_out, rel_out);
 }
 
@@ -829,6 +848,9 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->nu = nu;
     c->tau = tau;
     c->st = (cudaStream_t)stream;
+    STG_CUDA_OK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    STG_CUDA_OK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    STG_CUDA_OK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
     c->td = time_basis(k);
     c->pure_dirichlet = mesh->dirichlet_faces == (1u << (2 * mesh->dim)) - 1u;
     upload_fe_tables();
@@ -850,6 +872,10 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
         L.vv32 = dalloc<float>(c, L.nnzb * g.NV * g.NV);
         L.vp32 = dalloc<float>(c, nvp);
         L.pv32 = dalloc<float>(c, nvp);
+        if (l > 0 && kron_supported(g)) {
+          L.mk32 = dalloc<float>(c, L.nnzb);
+          L.ak32 = dalloc<float>(c, L.nnzb * g.nt * g.dim * g.dim);
+        }
       }
       L.w = dalloc<double>(c, g.nvel);
       L.asm_tab = dalloc<double>(c, assemble_table_doubles(g.dim, k));
@@ -951,6 +977,7 @@ stg_status stg_vcycle(stg_ctx* c, const double* b, double* x) {
       STG_CUDA_OK(cudaStreamSynchronize(c->st));
       prof_collect(c);
     }
+    if (colour_kernel_timed_out(c->st)) throw Error{STG_ETIMEOUT, kColourTimeout};
     return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -975,6 +1002,7 @@ stg_status stg_smooth(stg_ctx* c, int level, int sweeps, const double* b, double
         smooth_level<float, __nv_bfloat16>(c, level, sweeps, false);
       internal_to_cabi<float>(L.g, (const float*)L.x, x, c->st);
     }
+    if (colour_kernel_timed_out(c->st)) throw Error{STG_ETIMEOUT, kColourTimeout};
     return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);
@@ -1274,6 +1302,28 @@ stg_status stg_autotune(stg_ctx* c, int* variant, double* sweep_ms) {
   }
 }
 
+stg_status stg_get_colour_variant(const stg_ctx* c, int level, int* variant) {
+  if (!c || !variant || level < 1 || level >= (int)c->lv.size()) return STG_EINVAL;
+  *variant = c->lv[level].colour_variant;
+  return STG_OK;
+}
+
+stg_status stg_set_colour_variant(stg_ctx* c, int level, int variant) {
+  if (!c || level < 1 || level >= (int)c->lv.size() || variant < 0 || variant >= kColourVariants)
+    return STG_EINVAL;
+  try {
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    c->lv[level].colour_variant = variant;
+    if (c->graph) {  // recapture with the new variant
+      STG_CUDA_OK(cudaGraphExecDestroy(c->graph));
+      c->graph = nullptr;
+    }
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
 }  // extern "C"
 
 struct stg_batch {
@@ -1445,6 +1495,7 @@ stg_status stg_batch_gmres_solve(stg_batch* B, const double* const* b, double* c
       if (sp != STG_OK) all = sp;
     }
     for (stg_ctx* c : B->ctx) STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    if (colour_kernel_timed_out(B->main)) throw Error{STG_ETIMEOUT, kColourTimeout};
     return all;
   } catch (const Error& e) {
     g_setup_error = e.msg;
@@ -1473,6 +1524,12 @@ void stg_destroy(stg_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto& e : c->prof_ev) cudaEventDestroy(e);
   c->coarse64.release();

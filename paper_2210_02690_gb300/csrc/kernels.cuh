@@ -51,11 +51,27 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
 // One colour phase of the smoother: y_K = J_K^{-1} R_K r for all cells of colour
 // `colour`; accumulate (averaged mode: z += y) or apply (coloured mode: z += omega y).
 // variant = 3 * column-batch index (4, 8, 16 columns in flight) + CTA-size index (128, 256, 512)
-constexpr int kColourVariants = 9;
-constexpr int kColourDefault = 4;  // 8 columns, 256 threads
+// Variants 0..8: one warp per patch, loads straight from global memory (3 column-batch depths x
+// 3 CTA sizes); 9..12: factors staged in shared memory by bulk copies (stages x CTAs per SM).
+constexpr int kColourWarpVariants = 9;
+constexpr int kColourVariants = 13;
+constexpr int kColourWarpDefault = 4;  // 8 columns, 256 threads
+constexpr int kColourDefault = 9;      // 4 stages, 8 CTAs per SM (falls back to the warp form)
 template <typename VT, typename FT>
 void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st,
                   int variant = kColourDefault);
+
+// Kronecker-split FP32 velocity rows (2D, 2..5 Radau nodes): per BCSR slot M_ij and the d x d
+// spatial blocks of every Radau node, split from the FP64 dense blocks.
+bool kron_supported(const Geom& g);
+void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData& td, float* Mk, float* Ak,
+                cudaStream_t st);
+void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, const float* Mk, const float* Ak,
+                         const float* vp, const float* pv, const float* x, const float* b, float* out,
+                         cudaStream_t st);
+
+// True (and the flag cleared) when a staged colour kernel gave up waiting for a copy.
+bool colour_kernel_timed_out(cudaStream_t st);
 
 // d += omega z / p (p = static multiplicity of (S2)); z = 0.
 template <typename VT>

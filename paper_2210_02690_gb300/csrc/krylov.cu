@@ -12,30 +12,35 @@ namespace {
 constexpr int kDotBlocks = 1216;  // 8 x 152 SMs
 constexpr int kMaxVec = 32;
 
+// Inner products of w with the m columns of V; each block writes its partial sums.  MV (>= m)
+// sizes the per-thread accumulators, so short bases keep the register count (and with it the
+// number of loads in flight per SM) where a long basis would not.  The per-element order of
+// the sums does not depend on MV.
+template <int MV>
 __global__ void __launch_bounds__(256) multi_dot_partial(long long n, int m, const double* __restrict__ V,
                                                          long long ldv, const double* __restrict__ w,
                                                          double* __restrict__ partial) {
-  double acc[kMaxVec];
+  double acc[MV];
 #pragma unroll
-  for (int i = 0; i < kMaxVec; ++i) acc[i] = 0.0;
+  for (int i = 0; i < MV; ++i) acc[i] = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   for (; t + stride < n; t += 2 * stride) {  // two independent elements per pass
     const double w0 = w[t], w1 = w[t + stride];
 #pragma unroll
-    for (int i = 0; i < kMaxVec; ++i)
+    for (int i = 0; i < MV; ++i)
       if (i < m) acc[i] += V[i * ldv + t] * w0 + V[i * ldv + t + stride] * w1;
   }
   for (; t < n; t += stride) {
     const double wt = w[t];
 #pragma unroll
-    for (int i = 0; i < kMaxVec; ++i)
+    for (int i = 0; i < MV; ++i)
       if (i < m) acc[i] += V[i * ldv + t] * wt;
   }
   __shared__ double red[8][kMaxVec];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < kMaxVec; ++i) {
+  for (int i = 0; i < MV; ++i) {
     if (i >= m) break;
     double v = acc[i];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -86,8 +91,16 @@ __global__ void axpby_kernel(long long n, double a, const double* __restrict__ x
 void multi_dot(long long n, int m, const double* V, long long ldv, const double* w, double* partial, double* h,
                cudaStream_t st) {
   if (m > kMaxVec) throw Error{STG_EINVAL, "too many vectors in one orthogonalisation step"};
-  multi_dot_partial<<<kDotBlocks, 256, 0, st>>>(n, m, V, ldv, w, partial);
-  STG_LAUNCH_OK();
+  // chunks of at most 8 vectors per launch (79 registers a thread); a vector's sum is the same
+  // whichever chunk carries it
+  for (int c = 0; c < m; c += 8) {
+    const int mc = m - c < 8 ? m - c : 8;
+    if (mc <= 4)
+      multi_dot_partial<4><<<kDotBlocks, 256, 0, st>>>(n, mc, V + c * ldv, ldv, w, partial + c);
+    else
+      multi_dot_partial<8><<<kDotBlocks, 256, 0, st>>>(n, mc, V + c * ldv, ldv, w, partial + c);
+    STG_LAUNCH_OK();
+  }
   multi_dot_final<<<m, 256, 0, st>>>(m, kDotBlocks, partial, h);
   STG_LAUNCH_OK();
 }

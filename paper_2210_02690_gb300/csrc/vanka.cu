@@ -8,6 +8,7 @@
 // pressure DoFs belong to one cell, so one colour's scatters never collide
 // (no atomics, deterministic order).
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -65,6 +66,107 @@ __global__ void __launch_bounds__(256) op_vel_rows(Geom g, const int* __restrict
         for (int m = 0; m <= DIM; ++m) acc += (VT)q[m] * p[m];
       }
   out[t] = b ? b[t] - acc : acc;
+}
+
+// ------------------------------------------------------------------ Kronecker-split FP32 rows (2D)
+// With the Radau rule in time the velocity block of node pair (i, j) is
+//   J[(a,c),(b,e)] = T_ab M_ij delta_ce + delta_ab Ahat_a,ij[c][e],
+// so a slot needs M_ij and, per Radau node a, the d x d spatial block Ahat_a (9 values for
+// 2D k = 1 against 16 in the dense block).  Columns follow the structured stencil.
+
+struct TimeF {
+  float T[5][5];
+};
+
+// Mk[slot] = M_ij, Ak[slot][a][c][e] = Ahat_a,ij[c][e], split from the FP64 dense blocks:
+// M_ij = J[(as,0),(bs,0)] / T_{as,bs} for the largest off-diagonal |T_{as,bs}|.
+__global__ void kron_split_kernel(Geom g, long long nnzb, const double* __restrict__ vv, TimeData td, int as,
+                                  int bs, float* __restrict__ Mk, float* __restrict__ Ak) {
+  const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nnzb) return;
+  const int NV = g.NV, D = g.dim, NT = g.nt;
+  const double* blk = vv + slot * NV * NV;
+  const double M = blk[(as * D) * NV + bs * D] / td.T[as][bs];
+  Mk[slot] = (float)M;
+  float* A = Ak + slot * NT * D * D;
+  for (int a = 0; a < NT; ++a)
+    for (int c = 0; c < D; ++c)
+      for (int e = 0; e < D; ++e)
+        A[(a * D + c) * D + e] = (float)(blk[(a * D + c) * NV + a * D + e] - (c == e ? td.T[a][a] * M : 0.0));
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const int* __restrict__ rowptr,
+                                                        const float* __restrict__ Mk, const float* __restrict__ Ak,
+                                                        const float* __restrict__ vp, const float* __restrict__ x,
+                                                        const float* __restrict__ b, float* __restrict__ out) {
+  constexpr int D = 2, NV = NT * D;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n_nodes) return;
+  const int ix = (int)(node % g.nn[0]), iy = (int)(node / g.nn[0]);
+  int xl, xh, yl, yh;
+  stencil_range(ix, g.nn[0], xl, xh);
+  stencil_range(iy, g.nn[1], yl, yh);
+  float acc[NT][D];
+#pragma unroll
+  for (int a = 0; a < NT; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[a][c] = 0.f;
+  long long slot = rowptr[node];
+  for (int jy = yl; jy <= yh; ++jy) {
+#pragma unroll 5
+    for (int jx = xl; jx <= xh; ++jx, ++slot) {
+      const float2* xj2 = reinterpret_cast<const float2*>(x + ((long long)jy * g.nn[0] + jx) * NV);
+      float xj[NT][D];
+#pragma unroll
+      for (int a = 0; a < NT; ++a) {
+        const float2 v = xj2[a];
+        xj[a][0] = v.x;
+        xj[a][1] = v.y;
+      }
+      const float M = Mk[slot];
+      const float4* A4 = reinterpret_cast<const float4*>(Ak + slot * NT * D * D);
+#pragma unroll
+      for (int a = 0; a < NT; ++a) {
+        const float4 A = A4[a];  // Ahat_a[0][0], [0][1], [1][0], [1][1]
+        float u0 = 0.f, u1 = 0.f;
+#pragma unroll
+        for (int bb = 0; bb < NT; ++bb) {
+          u0 += tf.T[a][bb] * xj[bb][0];
+          u1 += tf.T[a][bb] * xj[bb][1];
+        }
+        acc[a][0] += M * u0 + A.x * xj[a][0] + A.y * xj[a][1];
+        acc[a][1] += M * u1 + A.z * xj[a][0] + A.w * xj[a][1];
+      }
+    }
+  }
+  // pressure coupling of the cells around the node
+  const int cxl = (ix & 1) ? (ix - 1) / 2 : (ix / 2 - 1 < 0 ? 0 : ix / 2 - 1);
+  const int cxh = (ix & 1) ? (ix - 1) / 2 : (ix / 2 > g.n[0] - 1 ? g.n[0] - 1 : ix / 2);
+  const int cyl = (iy & 1) ? (iy - 1) / 2 : (iy / 2 - 1 < 0 ? 0 : iy / 2 - 1);
+  const int cyh = (iy & 1) ? (iy - 1) / 2 : (iy / 2 > g.n[1] - 1 ? g.n[1] - 1 : iy / 2);
+  for (int cy = cyl; cy <= cyh; ++cy)
+    for (int cx = cxl; cx <= cxh; ++cx) {
+      const int il = (ix - 2 * cx) + 3 * (iy - 2 * cy);
+      const long long K = (long long)cy * g.n[0] + cx;
+      const float* q = vp + (K * g.nloc + il) * (long long)(NT * D * (D + 1));
+      const float* p = x + g.nvel + K * g.NP;
+#pragma unroll
+      for (int a = 0; a < NT; ++a) {
+        const float p0 = p[a * 3], p1 = p[a * 3 + 1], p2 = p[a * 3 + 2];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const float* qq = q + (a * D + c) * 3;
+          acc[a][c] += qq[0] * p0 + qq[1] * p1 + qq[2] * p2;
+        }
+      }
+    }
+  float* o = out + node * NV;
+  const float* bb = b ? b + node * NV : nullptr;
+#pragma unroll
+  for (int a = 0; a < NT; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) o[a * D + c] = bb ? bb[a * D + c] - acc[a][c] : acc[a][c];
 }
 
 template <int DIM, typename MT, typename VT>
@@ -551,6 +653,138 @@ __global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, c
   }
 }
 
+// ------------------------------------------------------------------ bulk-copy colour kernel
+// The same y_K = J_K^{-1} R_K r, z += y_K as vanka_colour_kernel, with each patch's factor
+// streamed into shared memory by the bulk-copy engine: one elected thread keeps S patches
+// in flight per CTA (cp.async.bulk completing on an mbarrier per stage) while the CTA, one
+// thread per row, computes the previous patch from shared memory.  Every wait has an
+// iteration limit; a CTA that reaches it raises g_colour_timeout, waits (again with a
+// limit) for its own copies still in flight, and returns.
+
+__device__ int g_colour_timeout;
+
+constexpr long long kBarrierSpins = 1LL << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool barrier_wait(unsigned bar, unsigned phase) {
+  for (long long i = 0; i < kBarrierSpins; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Shared memory: S mbarriers (128 B reserved), the gathered residual (n values, padded to
+// 128 B), then S stages of stage_bytes each (128-byte aligned).
+template <typename VT>
+__host__ __device__ __forceinline__ unsigned bulk_rl_bytes(int n) {
+  return (unsigned)((n * sizeof(VT) + 127) / 128 * 128);
+}
+
+template <typename VT, typename FT, int S>
+__global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int colour, const FT* __restrict__ jinv,
+                                                                 long long stride, const VT* __restrict__ r,
+                                                                 VT* __restrict__ z, VT scale, unsigned bytes,
+                                                                 unsigned stage_bytes) {
+  using AT = typename AccT<VT>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int n = g.npatch;
+  const int tid = threadIdx.x;
+  const long long cnt = g.coff[colour + 1] - g.coff[colour];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+  VT* rl = reinterpret_cast<VT*>(smem_raw + 128);  // two buffers of n values
+  unsigned char* stages = smem_raw + 128 + bulk_rl_bytes<VT>(2 * n);
+  const long long first = blockIdx.x, step = gridDim.x;
+  const FT* base = jinv + g.coff[colour] * stride;
+  const int* cc = g.ccount[colour];
+  auto dof = [&](long long li) {
+    long long rem = li;
+    const int jx = (int)(rem % cc[0]);
+    rem /= cc[0];
+    const int jy = (int)(rem % cc[1]);
+    const int jz = (int)(rem / cc[1]);
+    return patch_dof(g, 2 * jx + (colour & 1), 2 * jy + ((colour >> 1) & 1), 2 * jz + ((colour >> 2) & 1), tid);
+  };
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + s)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // S - 1 patches ahead; iteration it issues patch it + S - 1
+    for (int s = 0; s + 1 < S; ++s) {
+      const long long li = first + s * step;
+      if (li < cnt) bulk_load(smem_u32(stages + s * stage_bytes), base + li * stride, bytes, smem_u32(bar + s));
+    }
+  }
+  __syncthreads();  // no thread may poll a barrier before thread 0 has initialised it
+  long long gi = 0;
+  VT zold = 0;
+  if (tid < n && first < cnt) {
+    gi = dof(first);
+    rl[tid] = r[gi];
+    zold = z[gi];  // no other patch of this colour touches these entries
+  }
+  int it = 0;
+  for (long long li = first; li < cnt; li += step, ++it) {
+    const int s = it % S;
+    const bool ok = barrier_wait(smem_u32(bar + s), (unsigned)((it / S) & 1));
+    // one barrier per patch: publishes rl[it & 1], frees the stage of patch it - 1
+    if (__syncthreads_or(!ok)) {
+      // give up: flag it, let the copies already issued land, then leave
+      if (tid == 0) {
+        atomicExch(&g_colour_timeout, 1);
+        for (int j = it; j < it + S - 1; ++j) {
+          if (first + (long long)j * step >= cnt) break;
+          barrier_wait(smem_u32(bar + (j % S)), (unsigned)((j / S) & 1));
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    if (tid == 0) {
+      const int j = it + S - 1;
+      const long long lj = first + (long long)j * step;
+      if (lj < cnt) bulk_load(smem_u32(stages + (j % S) * stage_bytes), base + lj * stride, bytes, smem_u32(bar + (j % S)));
+    }
+    // gather of the next patch, in flight while this one is computed
+    const long long ln = li + step;
+    long long gn = 0;
+    VT rn = 0, zn = 0;
+    if (tid < n && ln < cnt) {
+      gn = dof(ln);
+      rn = r[gn];
+      zn = z[gn];
+    }
+    if (tid < n) {
+      const FT* A = reinterpret_cast<const FT*>(stages + s * stage_bytes);
+      const VT* rc = rl + (it & 1) * n;
+      AT acc = 0;
+#pragma unroll 6
+      for (int col = 0; col < n; ++col) acc += cvt<AT>(A[col * n + tid]) * (AT)rc[col];
+      z[gi] = zold + scale * (VT)acc;
+      rl[((it + 1) & 1) * n + tid] = rn;
+    }
+    gi = gn;
+    zold = zn;
+  }
+}
+
 template <typename VT>
 __global__ void vanka_update_kernel(Geom g, VT* __restrict__ d, VT* __restrict__ z, double omega) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -581,6 +815,39 @@ void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const M
     STG_LAUNCH_OK();
     op_pres_rows<3, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
   }
+  STG_LAUNCH_OK();
+}
+
+bool kron_supported(const Geom& g) { return g.dim == 2 && g.nt >= 2 && g.nt <= 5; }
+
+void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData& td, float* Mk, float* Ak,
+                cudaStream_t st) {
+  int as = 0, bs = 1;
+  for (int a = 0; a < g.nt; ++a)
+    for (int b = 0; b < g.nt; ++b)
+      if (a != b && std::fabs(td.T[a][b]) > std::fabs(td.T[as][bs])) {
+        as = a;
+        bs = b;
+      }
+  kron_split_kernel<<<grid_for(nnzb, 256), 256, 0, st>>>(g, nnzb, vv, td, as, bs, Mk, Ak);
+  STG_LAUNCH_OK();
+}
+
+void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, const float* Mk, const float* Ak,
+                         const float* vp, const float* pv, const float* x, const float* b, float* out,
+                         cudaStream_t st) {
+  TimeF tf;
+  for (int a = 0; a < 5; ++a)
+    for (int c = 0; c < 5; ++c) tf.T[a][c] = (float)td.T[a][c];
+  const unsigned grid = grid_for(g.n_nodes, 256);
+  switch (g.nt) {
+    case 2: op_vel_rows_kron<2><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    case 3: op_vel_rows_kron<3><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    case 4: op_vel_rows_kron<4><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    default: op_vel_rows_kron<5><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+  }
+  STG_LAUNCH_OK();
+  op_pres_rows<2, float, float><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
   STG_LAUNCH_OK();
 }
 
@@ -672,11 +939,77 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     launch(double{});
 }
 
+namespace {
+
+struct BulkShape {
+  int stages, ctas_per_sm;
+};
+constexpr BulkShape kBulkShapes[kColourVariants - kColourWarpVariants] = {{4, 32}, {3, 32}, {2, 32}, {6, 32}};
+
+template <typename VT, typename FT, int S>
+bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st,
+                 int ctas_per_sm) {
+  const int n = g.npatch;
+  const long long cnt = g.coff[colour + 1] - g.coff[colour];
+  const long long stride = patch_stride(n);
+  const unsigned bytes = (unsigned)((n * n * sizeof(FT) + 15) / 16 * 16);  // <= stride * sizeof(FT)
+  const unsigned stage_bytes = (bytes + 127) / 128 * 128;
+  const size_t smem = 128 + bulk_rl_bytes<VT>(2 * n) + (size_t)S * stage_bytes;
+  const int threads = (n + 31) / 32 * 32;
+  if (smem > 200 * 1024 || threads > 1024) return false;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    STG_CUDA_OK(cudaGetDevice(&dev));
+    STG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  if (smem > 48 * 1024)
+    STG_CUDA_OK(cudaFuncSetAttribute(vanka_colour_bulk_kernel<VT, FT, S>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  // every CTA resident at once: the grid is capped by the occupancy the launch can reach
+  int resident = 0;
+  STG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, vanka_colour_bulk_kernel<VT, FT, S>,
+                                                            threads, smem));
+  if (resident < 1) return false;
+  const long long want = (long long)sms * std::min(ctas_per_sm, resident);
+  const unsigned grid = (unsigned)(cnt < want ? cnt : want);
+  vanka_colour_bulk_kernel<VT, FT, S><<<grid, threads, smem, st>>>(g, colour, jinv, stride, r, z, scale, bytes,
+                                                                    stage_bytes);
+  STG_LAUNCH_OK();
+  return true;
+}
+
+}  // namespace
+
+bool colour_kernel_timed_out(cudaStream_t st) {
+  int h = 0;
+  STG_CUDA_OK(cudaMemcpyFromSymbolAsync(&h, g_colour_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  STG_CUDA_OK(cudaStreamSynchronize(st));
+  if (h) {
+    const int zero = 0;
+    STG_CUDA_OK(cudaMemcpyToSymbolAsync(g_colour_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    STG_CUDA_OK(cudaStreamSynchronize(st));
+  }
+  return h != 0;
+}
+
 template <typename VT, typename FT>
 void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st,
                   int variant) {
   const long long cnt = g.coff[colour + 1] - g.coff[colour];
   if (cnt == 0) return;
+  if (variant >= kColourWarpVariants) {
+    const BulkShape b = kBulkShapes[(variant - kColourWarpVariants) % (kColourVariants - kColourWarpVariants)];
+    bool done = false;
+    if (b.stages == 2)
+      done = launch_bulk<VT, FT, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+    else if (b.stages == 4)
+      done = launch_bulk<VT, FT, 4>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+    else
+      done = launch_bulk<VT, FT, 6>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+    if (done) return;
+    variant = kColourWarpDefault;  // patch too large for the staged form
+  }
   const int n = g.npatch;
   const long long stride = patch_stride(n);
   const int cb_idx = (variant / 3) % 3, th_idx = variant % 3;
