@@ -222,6 +222,15 @@ stg_status stg_invert_local_noalloc(int n, long long count, const double* a, dou
  * sweep's colour kernels.  (Engineering service; the paper has no counterpart.) */
 stg_status stg_autotune(stg_ctx* ctx, int* variant, double* sweep_ms);
 
+/* Fault-injection hook for the bounded waits (engineering service): sets the
+ * iteration limit with which the staged smoother kernels wait for a factor
+ * copy (default 2^22; the value applies to every context of the process and to
+ * captured graphs).  A kernel that reaches the limit lets its copies in flight
+ * land, returns, and the next synchronising call of the context reports
+ * STG_ETIMEOUT; 0 makes every such wait give up at once.  STG_EINVAL for a
+ * negative limit. */
+stg_status stg_set_wait_limit(long long spins);
+
 /* Colour-kernel variant of level `level` >= 1 (0..12, as timed by stg_autotune):
  * read it, or set it (the V-cycle graph is recaptured), e.g. to replay a choice
  * made in another run.  STG_EINVAL for a level or variant out of range. */

@@ -29,7 +29,8 @@ EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
             "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_newton_slab",
-            "stg_slab_initial_guess", "stg_autotune", "stg_get_colour_variant", "stg_set_colour_variant",
+            "stg_slab_initial_guess", "stg_autotune", "stg_set_wait_limit", "stg_get_colour_variant",
+            "stg_set_colour_variant",
             "stg_batch_create", "stg_batch_gmres_solve",
             "stg_batch_destroy", "stg_cnn_create", "stg_cnn_n_params", "stg_cnn_set_params",
             "stg_cnn_get_params", "stg_cnn_forward", "stg_cnn_gradients", "stg_cnn_adam_step", "stg_cnn_train",
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_newton_slab": (I, [P, P, P, P, P, D, D, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "stg_slab_initial_guess": (I, [P, P, P]),
         "stg_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "stg_set_wait_limit": (I, [LL]),
         "stg_get_colour_variant": (I, [P, I, ctypes.POINTER(I)]),
         "stg_set_colour_variant": (I, [P, I, I]),
         "stg_batch_create": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P)]),
@@ -157,6 +159,14 @@ def _check(lib, ctx, status: int):
         msg = lib.stg_last_error(ctx)
         raise StgError(status, msg.decode() if msg else "")
     return status
+
+
+def set_wait_limit(spins: int) -> None:
+    """Iteration limit of the staged smoother's waits (fault injection; default 2**22)."""
+    lib = load_library()
+    st = lib.stg_set_wait_limit(int(spins))
+    if st != STG_OK:
+        raise StgError(st, "stg_set_wait_limit")
 
 
 class Solver:

@@ -178,7 +178,7 @@ struct LevelBufs {
   long long nnzb = 0;
   double *vv = nullptr, *vp = nullptr, *pv = nullptr;
   float *vv32 = nullptr, *vp32 = nullptr, *pv32 = nullptr;
-  float *mk32 = nullptr, *ak32 = nullptr;  // Kronecker-split FP32 velocity rows (levels >= 1, 2D)
+  float *mk32 = nullptr, *ak32 = nullptr;  // Kronecker-split FP32 velocity rows (F32 form, levels >= 1, 2D)
   void* jinv = nullptr;
   double* w = nullptr;
   double* asm_tab = nullptr;
@@ -368,6 +368,12 @@ void residual(stg_ctx* c, const LevelBufs& L, const VT* x, const VT* b, VT* r) {
     apply_operator<VT, VT>(L.g, L.rowptr, L.colidx, Ops<VT>::vv(L), Ops<VT>::vp(L), Ops<VT>::pv(L), x, b, r, c->st);
 }
 
+// J x (b null) or b - J x with the FP64 operator of level L.  The dense blocks stay: on GB300
+// the FP64 rows are bound by FP64 throughput, and the dense block needs the fewest operations.
+void apply64(stg_ctx* c, const LevelBufs& L, const double* x, const double* b, double* y) {
+  apply_operator<double, double>(L.g, L.rowptr, L.colidx, L.vv, L.vp, L.pv, x, b, y, c->st);
+}
+
 template <typename VT, typename FT>
 void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
   LevelBufs& L = c->lv[l];
@@ -427,7 +433,7 @@ void coarse_solve64(stg_ctx* c, const double* b, double* x) {
   const LevelBufs& L = c->lv[0];
   c->coarse32.solve(b, x, c->st);
   for (int it = 0; it < c->opt.coarse_refine; ++it) {
-    apply_operator<double, double>(L.g, L.rowptr, L.colidx, L.vv, L.vp, L.pv, x, b, c->cr64, c->st);
+    apply64(c, L, x, b, c->cr64);
     c->coarse32.solve(c->cr64, c->cd64, c->st);
     axpby(L.g.N, 1.0, c->cd64, 1.0, x, c->st);
   }
@@ -536,10 +542,7 @@ void level_to_internal(stg_ctx* c, int l, const double* in, VT* out) {
   cabi_to_internal<VT>(c->lv[l].g, in, out, c->st);
 }
 
-void apply_fine64(stg_ctx* c, const double* x, double* y) {
-  const LevelBufs& F = c->lv.back();
-  apply_operator<double, double>(F.g, F.rowptr, F.colidx, F.vv, F.vp, F.pv, x, nullptr, y, c->st);
-}
+void apply_fine64(stg_ctx* c, const double* x, double* y) { apply64(c, c->lv.back(), x, nullptr, y); }
 
 double dot_host(stg_ctx* c, const double* a, const double* b) {
   const long long n = c->lv.back().g.N;
@@ -575,6 +578,7 @@ void fg_begin(FgState& S, stg_ctx* c, const double* b, double* x) {
   S.gv.assign(S.m + 1, 0.0);
   S.y.assign(S.m, 0.0);
   S.bnorm = std::sqrt(dot_host(c, b, b));
+  if (!std::isfinite(S.bnorm)) throw Error{STG_EINVAL, "right-hand side contains NaN or Inf"};
   S.tol = std::max(c->opt.gmres_rtol * S.bnorm, c->opt.gmres_atol);
   S.its = 0;
   S.active = false;
@@ -704,6 +708,7 @@ stg_status newton(stg_ctx* c, double* X, double rtol, double atol, int maxit, in
   LevelBufs& F = c->lv.back();
   const long long n = F.g.N;
   double nr = neg_residual(c, X, c->nr);
+  if (!std::isfinite(nr)) throw Error{STG_EINVAL, "slab residual is NaN or Inf (check X, f, g and v_prev)"};
   const double tol = std::max(rtol * nr, atol);
   int steps = 0, gits = 0;
   stg_status st = STG_OK;
@@ -952,7 +957,7 @@ stg_status stg_apply_level_jacobian(stg_ctx* c, int level, const double* x, doub
   try {
     const LevelBufs& L = c->lv[level];
     cabi_to_internal<double>(L.g, x, c->tmp_a, c->st);
-    apply_operator<double, double>(L.g, L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->tmp_a, nullptr, c->tmp_b, c->st);
+    apply64(c, L, c->tmp_a, nullptr, c->tmp_b);
     internal_to_cabi<double>(L.g, c->tmp_b, y, c->st);
     STG_CUDA_OK(cudaGetLastError());
     return STG_OK;
@@ -1299,6 +1304,17 @@ stg_status stg_autotune(stg_ctx* c, int* variant, double* sweep_ms) {
     return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);
+  }
+}
+
+stg_status stg_set_wait_limit(long long spins) {
+  if (spins < 0) return STG_EINVAL;
+  try {
+    set_colour_wait_limit(spins);
+    return STG_OK;
+  } catch (const Error& e) {
+    g_setup_error = e.msg;
+    return e.st;
   }
 }
 

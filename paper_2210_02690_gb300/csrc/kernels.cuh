@@ -72,6 +72,8 @@ void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, c
 
 // True (and the flag cleared) when a staged colour kernel gave up waiting for a copy.
 bool colour_kernel_timed_out(cudaStream_t st);
+// Iteration limit of the staged colour kernel's waits for a factor copy.
+void set_colour_wait_limit(long long spins);
 
 // d += omega z / p (p = static multiplicity of (S2)); z = 0.
 template <typename VT>

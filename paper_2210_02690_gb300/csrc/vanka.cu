@@ -78,8 +78,8 @@ struct TimeF {
   float T[5][5];
 };
 
-// Mk[slot] = M_ij, Ak[slot][a][c][e] = Ahat_a,ij[c][e], split from the FP64 dense blocks:
-// M_ij = J[(as,0),(bs,0)] / T_{as,bs} for the largest off-diagonal |T_{as,bs}|.
+// Mk[slot] = M_ij, Ak[slot][a][c][e] = Ahat_a,ij[c][e], split (in FP64, then rounded) from the
+// FP64 dense blocks: M_ij = J[(as,0),(bs,0)] / T_{as,bs} for the largest off-diagonal |T_{as,bs}|.
 __global__ void kron_split_kernel(Geom g, long long nnzb, const double* __restrict__ vv, TimeData td, int as,
                                   int bs, float* __restrict__ Mk, float* __restrict__ Ak) {
   const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,49 +95,35 @@ __global__ void kron_split_kernel(Geom g, long long nnzb, const double* __restri
         A[(a * D + c) * D + e] = (float)(blk[(a * D + c) * NV + a * D + e] - (c == e ? td.T[a][a] * M : 0.0));
 }
 
+// b - J x (or J x) on the velocity rows of the FP32 level operators from the Kronecker split,
+// one thread per row (a, c) of a node: per slot the mass term M_ij ((T (x) I) x_j)[a][c] and the
+// row of Ahat_a,ij, 4 + 4 (k+1) d^2 / NV bytes of matrix per row instead of 4 NV.
 template <int NT>
 __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const int* __restrict__ rowptr,
                                                         const float* __restrict__ Mk, const float* __restrict__ Ak,
                                                         const float* __restrict__ vp, const float* __restrict__ x,
                                                         const float* __restrict__ b, float* __restrict__ out) {
   constexpr int D = 2, NV = NT * D;
-  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= g.n_nodes) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nvel) return;
+  const long long node = t / NV;
+  const int r = (int)(t - node * NV), a = r / D, c = r - a * D;
   const int ix = (int)(node % g.nn[0]), iy = (int)(node / g.nn[0]);
   int xl, xh, yl, yh;
   stencil_range(ix, g.nn[0], xl, xh);
   stencil_range(iy, g.nn[1], yl, yh);
-  float acc[NT][D];
-#pragma unroll
-  for (int a = 0; a < NT; ++a)
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[a][c] = 0.f;
+  float acc = 0.f;
   long long slot = rowptr[node];
   for (int jy = yl; jy <= yh; ++jy) {
 #pragma unroll 5
     for (int jx = xl; jx <= xh; ++jx, ++slot) {
-      const float2* xj2 = reinterpret_cast<const float2*>(x + ((long long)jy * g.nn[0] + jx) * NV);
-      float xj[NT][D];
+      const float* xj = x + ((long long)jy * g.nn[0] + jx) * NV;
+      const float2 xa = reinterpret_cast<const float2*>(xj)[a];
+      float ym = 0.f;
 #pragma unroll
-      for (int a = 0; a < NT; ++a) {
-        const float2 v = xj2[a];
-        xj[a][0] = v.x;
-        xj[a][1] = v.y;
-      }
-      const float M = Mk[slot];
-      const float4* A4 = reinterpret_cast<const float4*>(Ak + slot * NT * D * D);
-#pragma unroll
-      for (int a = 0; a < NT; ++a) {
-        const float4 A = A4[a];  // Ahat_a[0][0], [0][1], [1][0], [1][1]
-        float u0 = 0.f, u1 = 0.f;
-#pragma unroll
-        for (int bb = 0; bb < NT; ++bb) {
-          u0 += tf.T[a][bb] * xj[bb][0];
-          u1 += tf.T[a][bb] * xj[bb][1];
-        }
-        acc[a][0] += M * u0 + A.x * xj[a][0] + A.y * xj[a][1];
-        acc[a][1] += M * u1 + A.z * xj[a][0] + A.w * xj[a][1];
-      }
+      for (int bb = 0; bb < NT; ++bb) ym += tf.T[a][bb] * xj[bb * D + c];
+      const float2 A = reinterpret_cast<const float2*>(Ak + slot * NT * D * D)[a * D + c];  // Ahat_a[c][0..1]
+      acc += Mk[slot] * ym + A.x * xa.x + A.y * xa.y;
     }
   }
   // pressure coupling of the cells around the node
@@ -149,24 +135,11 @@ __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const 
     for (int cx = cxl; cx <= cxh; ++cx) {
       const int il = (ix - 2 * cx) + 3 * (iy - 2 * cy);
       const long long K = (long long)cy * g.n[0] + cx;
-      const float* q = vp + (K * g.nloc + il) * (long long)(NT * D * (D + 1));
-      const float* p = x + g.nvel + K * g.NP;
-#pragma unroll
-      for (int a = 0; a < NT; ++a) {
-        const float p0 = p[a * 3], p1 = p[a * 3 + 1], p2 = p[a * 3 + 2];
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const float* qq = q + (a * D + c) * 3;
-          acc[a][c] += qq[0] * p0 + qq[1] * p1 + qq[2] * p2;
-        }
-      }
+      const float* q = vp + ((K * g.nloc + il) * NT * D + r) * (D + 1);
+      const float* p = x + g.nvel + K * g.NP + a * (D + 1);
+      acc += q[0] * p[0] + q[1] * p[1] + q[2] * p[2];
     }
-  float* o = out + node * NV;
-  const float* bb = b ? b + node * NV : nullptr;
-#pragma unroll
-  for (int a = 0; a < NT; ++a)
-#pragma unroll
-    for (int c = 0; c < D; ++c) o[a * D + c] = bb ? bb[a * D + c] - acc[a][c] : acc[a][c];
+  out[t] = b ? b[t] - acc : acc;
 }
 
 template <int DIM, typename MT, typename VT>
@@ -664,13 +637,16 @@ __global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, c
 __device__ int g_colour_timeout;
 
 constexpr long long kBarrierSpins = 1LL << 22;
+// limit of the waits for a patch's factor (read at run time, so graph replays see changes);
+// the waits for copies still in flight after giving up always use kBarrierSpins
+__device__ long long g_colour_wait_spins = kBarrierSpins;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ bool barrier_wait(unsigned bar, unsigned phase) {
-  for (long long i = 0; i < kBarrierSpins; ++i) {
+__device__ __forceinline__ bool barrier_wait(unsigned bar, unsigned phase, long long spins) {
+  for (long long i = 0; i < spins; ++i) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -715,6 +691,7 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
   const long long first = blockIdx.x, step = gridDim.x;
   const FT* base = jinv + g.coff[colour] * stride;
   const int* cc = g.ccount[colour];
+  const long long spins = g_colour_wait_spins;
   auto dof = [&](long long li) {
     long long rem = li;
     const int jx = (int)(rem % cc[0]);
@@ -743,7 +720,7 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
   int it = 0;
   for (long long li = first; li < cnt; li += step, ++it) {
     const int s = it % S;
-    const bool ok = barrier_wait(smem_u32(bar + s), (unsigned)((it / S) & 1));
+    const bool ok = barrier_wait(smem_u32(bar + s), (unsigned)((it / S) & 1), spins);
     // one barrier per patch: publishes rl[it & 1], frees the stage of patch it - 1
     if (__syncthreads_or(!ok)) {
       // give up: flag it, let the copies already issued land, then leave
@@ -751,7 +728,7 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
         atomicExch(&g_colour_timeout, 1);
         for (int j = it; j < it + S - 1; ++j) {
           if (first + (long long)j * step >= cnt) break;
-          barrier_wait(smem_u32(bar + (j % S)), (unsigned)((j / S) & 1));
+          barrier_wait(smem_u32(bar + (j % S)), (unsigned)((j / S) & 1), kBarrierSpins);
         }
       }
       __syncthreads();
@@ -839,7 +816,7 @@ void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, c
   TimeF tf;
   for (int a = 0; a < 5; ++a)
     for (int c = 0; c < 5; ++c) tf.T[a][c] = (float)td.T[a][c];
-  const unsigned grid = grid_for(g.n_nodes, 256);
+  const unsigned grid = grid_for(g.nvel, 256);
   switch (g.nt) {
     case 2: op_vel_rows_kron<2><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
     case 3: op_vel_rows_kron<3><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
@@ -980,6 +957,10 @@ bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, 
 }
 
 }  // namespace
+
+void set_colour_wait_limit(long long spins) {
+  STG_CUDA_OK(cudaMemcpyToSymbol(g_colour_wait_spins, &spins, sizeof(spins)));
+}
 
 bool colour_kernel_timed_out(cudaStream_t st) {
   int h = 0;

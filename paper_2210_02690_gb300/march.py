@@ -136,6 +136,44 @@ class March:
                 out[name].append(dict(slab=n + 1, r0=r0, tol=tol, steps=steps, its=its, res=res, ok=ok, sec=sec))
         return out
 
+    # -- checkpoint / resume
+    # Flat binary: 8-byte magic, int64 header [version, dim, n_x, n_y, k, N, slab n, n_params],
+    # float64 [scale_v], float64 X_{n-1}, float64 X_n, float32 network parameters (n_params).
+    MAGIC = b"STGMARCH"
+
+    def save(self, path, net=None, scale_v=1.0):
+        """Writes the last two slab vectors, the slab index and the network's parameters."""
+        n = len(self.X) - 1
+        if n < 1:
+            raise ValueError("nothing to checkpoint before the first slab")
+        params = net.get_params() if net is not None else np.zeros(0, np.float32)
+        hdr = np.array([1, self.spec.dim, *self.spec.n[:2], self.k, self.N, n, params.size], dtype=np.int64)
+        with open(path, "wb") as f:
+            f.write(self.MAGIC)
+            hdr.tofile(f)
+            np.array([scale_v], dtype=np.float64).tofile(f)
+            for X in (self.X[n - 1], self.X[n]):
+                X.detach().cpu().numpy().astype(np.float64).tofile(f)
+            params.astype(np.float32).tofile(f)
+
+    def load(self, path):
+        """Restores a checkpoint of the same problem; returns (slab index n, parameters, scale_v).
+        The march continues with slab n + 1 exactly as the saved run would have."""
+        with open(path, "rb") as f:
+            if f.read(8) != self.MAGIC:
+                raise ValueError(f"{path}: not a march checkpoint")
+            hdr = np.fromfile(f, dtype=np.int64, count=8)
+            version, dim, nx, ny, k, N, n, n_params = (int(v) for v in hdr)
+            if version != 1 or (dim, nx, ny, k, N) != (self.spec.dim, *self.spec.n[:2], self.k, self.N):
+                raise ValueError(f"{path}: checkpoint of another problem")
+            scale_v = float(np.fromfile(f, dtype=np.float64, count=1)[0])
+            Xm = np.fromfile(f, dtype=np.float64, count=N)
+            Xn = np.fromfile(f, dtype=np.float64, count=N)
+            params = np.fromfile(f, dtype=np.float32, count=n_params)
+        self.X = [None] * (n - 1) + [self.torch.from_numpy(Xm).cuda(), self.torch.from_numpy(Xn).cuda()]
+        self.stats = []
+        return n, params, scale_v
+
     def close(self):
         self.solver.close()
 
