@@ -96,35 +96,107 @@ __global__ void kron_split_kernel(Geom g, long long nnzb, const double* __restri
 }
 
 // b - J x (or J x) on the velocity rows of the FP32 level operators from the Kronecker split,
-// one thread per row (a, c) of a node: per slot the mass term M_ij ((T (x) I) x_j)[a][c] and the
-// row of Ahat_a,ij, 4 + 4 (k+1) d^2 / NV bytes of matrix per row instead of 4 NV.
+// one thread per (node, Radau node a): per slot the mass term M_ij ((T (x) I) x_j)[a] and the
+// 2 x 2 block Ahat_a,ij, 4 + 4 (k+1) d^2 bytes of matrix per slot instead of 4 NV^2.  A stencil
+// row (3 or 5 slots) is unrolled with pointer increments, so each slot costs three loads (x_j,
+// Ahat_a as one float4, M_ij) and few integer operations.
+template <int NT>
+struct XNode {
+  float v[NT * 2];
+};
+
+template <int NT>
+__device__ __forceinline__ XNode<NT> load_node(const float* p) {
+  XNode<NT> r;
+  if (NT % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NT / 2; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(p)[i];
+      r.v[4 * i] = q.x;
+      r.v[4 * i + 1] = q.y;
+      r.v[4 * i + 2] = q.z;
+      r.v[4 * i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+      const float2 q = reinterpret_cast<const float2*>(p)[i];
+      r.v[2 * i] = q.x;
+      r.v[2 * i + 1] = q.y;
+    }
+  }
+  return r;
+}
+
+template <int NT, int W>
+__device__ __forceinline__ void kron_stencil_row(const float* __restrict__ xj, const float4* __restrict__ Ap,
+                                                 const float* __restrict__ Mp, const float (&tr)[NT], int a,
+                                                 float& acc0, float& acc1) {
+  constexpr int D = 2, NV = NT * D;
+  XNode<NT> xs[W];
+  float4 As[W];
+  float Ms[W];
+#pragma unroll
+  for (int u = 0; u < W; ++u) {
+    xs[u] = load_node<NT>(xj + u * NV);
+    As[u] = Ap[u * NT];
+    Ms[u] = Mp[u];
+  }
+#pragma unroll
+  for (int u = 0; u < W; ++u) {
+    float y0 = 0.f, y1 = 0.f, xa0 = 0.f, xa1 = 0.f;
+#pragma unroll
+    for (int bb = 0; bb < NT; ++bb) {
+      y0 += tr[bb] * xs[u].v[bb * D];
+      y1 += tr[bb] * xs[u].v[bb * D + 1];
+      if (bb == a) {
+        xa0 = xs[u].v[bb * D];
+        xa1 = xs[u].v[bb * D + 1];
+      }
+    }
+    acc0 += Ms[u] * y0 + As[u].x * xa0 + As[u].y * xa1;
+    acc1 += Ms[u] * y1 + As[u].z * xa0 + As[u].w * xa1;
+  }
+}
+
+// One thread per (node, Radau node a): both velocity rows (a, 0), (a, 1).
 template <int NT>
 __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const int* __restrict__ rowptr,
                                                         const float* __restrict__ Mk, const float* __restrict__ Ak,
                                                         const float* __restrict__ vp, const float* __restrict__ x,
                                                         const float* __restrict__ b, float* __restrict__ out) {
   constexpr int D = 2, NV = NT * D;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.nvel) return;
-  const long long node = t / NV;
-  const int r = (int)(t - node * NV), a = r / D, c = r - a * D;
-  const int ix = (int)(node % g.nn[0]), iy = (int)(node / g.nn[0]);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (node, a) pairs < 2^31 (checked by the caller)
+  if (t >= g.n_nodes * NT) return;
+  const int node = t / NT;
+  const int a = t - node * NT;
+  const int nx = g.nn[0];
+  const int ix = node % nx, iy = node / nx;
   int xl, xh, yl, yh;
-  stencil_range(ix, g.nn[0], xl, xh);
+  stencil_range(ix, nx, xl, xh);
   stencil_range(iy, g.nn[1], yl, yh);
-  float acc = 0.f;
-  long long slot = rowptr[node];
-  for (int jy = yl; jy <= yh; ++jy) {
-#pragma unroll 5
-    for (int jx = xl; jx <= xh; ++jx, ++slot) {
-      const float* xj = x + ((long long)jy * g.nn[0] + jx) * NV;
-      const float2 xa = reinterpret_cast<const float2*>(xj)[a];
-      float ym = 0.f;
+  float tr[NT];
 #pragma unroll
-      for (int bb = 0; bb < NT; ++bb) ym += tf.T[a][bb] * xj[bb * D + c];
-      const float2 A = reinterpret_cast<const float2*>(Ak + slot * NT * D * D)[a * D + c];  // Ahat_a[c][0..1]
-      acc += Mk[slot] * ym + A.x * xa.x + A.y * xa.y;
-    }
+  for (int bb = 0; bb < NT; ++bb) {
+    float v = tf.T[0][bb];
+#pragma unroll
+    for (int aa = 1; aa < NT; ++aa)
+      if (aa == a) v = tf.T[aa][bb];
+    tr[bb] = v;
+  }
+  float acc0 = 0.f, acc1 = 0.f;
+  const int s0 = rowptr[node];
+  const float* Mp = Mk + s0;
+  const float4* Ap = reinterpret_cast<const float4*>(Ak) + (long long)s0 * NT + a;  // Ahat_a (2 x 2)
+  const int wx = xh - xl + 1;
+  for (int jy = yl; jy <= yh; ++jy) {
+    const float* xj = x + ((long long)jy * nx + xl) * NV;
+    if (wx == 5)
+      kron_stencil_row<NT, 5>(xj, Ap, Mp, tr, a, acc0, acc1);
+    else
+      kron_stencil_row<NT, 3>(xj, Ap, Mp, tr, a, acc0, acc1);
+    Mp += wx;
+    Ap += wx * NT;
   }
   // pressure coupling of the cells around the node
   const int cxl = (ix & 1) ? (ix - 1) / 2 : (ix / 2 - 1 < 0 ? 0 : ix / 2 - 1);
@@ -135,11 +207,19 @@ __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const 
     for (int cx = cxl; cx <= cxh; ++cx) {
       const int il = (ix - 2 * cx) + 3 * (iy - 2 * cy);
       const long long K = (long long)cy * g.n[0] + cx;
-      const float* q = vp + ((K * g.nloc + il) * NT * D + r) * (D + 1);
+      const float* q = vp + ((K * g.nloc + il) * NT + a) * D * (D + 1);
       const float* p = x + g.nvel + K * g.NP + a * (D + 1);
-      acc += q[0] * p[0] + q[1] * p[1] + q[2] * p[2];
+      acc0 += q[0] * p[0] + q[1] * p[1] + q[2] * p[2];
+      acc1 += q[3] * p[0] + q[4] * p[1] + q[5] * p[2];
     }
-  out[t] = b ? b[t] - acc : acc;
+  const long long o = (long long)node * NV + a * D;
+  if (b) {
+    out[o] = b[o] - acc0;
+    out[o + 1] = b[o + 1] - acc1;
+  } else {
+    out[o] = acc0;
+    out[o + 1] = acc1;
+  }
 }
 
 template <int DIM, typename MT, typename VT>
@@ -813,10 +893,11 @@ void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData&
 void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, const float* Mk, const float* Ak,
                          const float* vp, const float* pv, const float* x, const float* b, float* out,
                          cudaStream_t st) {
+  if (g.n_nodes * g.nt >= (1LL << 31)) throw Error{STG_EINVAL, "level too large for 32-bit row indices"};
   TimeF tf;
   for (int a = 0; a < 5; ++a)
     for (int c = 0; c < 5; ++c) tf.T[a][c] = (float)td.T[a][c];
-  const unsigned grid = grid_for(g.nvel, 256);
+  const unsigned grid = grid_for(g.n_nodes * g.nt, 256);
   switch (g.nt) {
     case 2: op_vel_rows_kron<2><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
     case 3: op_vel_rows_kron<3><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
