@@ -178,6 +178,7 @@ struct LevelBufs {
   long long nnzb = 0;
   double *vv = nullptr, *vp = nullptr, *pv = nullptr;
   float *vv32 = nullptr, *vp32 = nullptr, *pv32 = nullptr;
+  double* vconst = nullptr;  // the w = 0 assembly (time coupling, viscous, Nitsche), built once
   float *mk32 = nullptr, *ak32 = nullptr;  // Kronecker-split FP32 velocity rows (F32 form, levels >= 1, 2D)
   void* jinv = nullptr;
   double* w = nullptr;
@@ -284,7 +285,7 @@ void linearise_internal(stg_ctx* c) {
   STG_CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
   for (int l = 0; l < nl; ++l) {
     LevelBufs& L = c->lv[l];
-    assemble_level(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vv, L.nnzb, L.vp, L.pv, c->st);
+    assemble_level_w(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vconst, L.vv, L.nnzb, c->st);
     if (!vc64(c)) {
       convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, c->st);
       const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
@@ -697,7 +698,7 @@ double neg_residual(stg_ctx* c, const double* X, double* r) {
   LevelBufs& F = c->lv.back();
   AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, 0};
   // the velocity part of an internal vector is laid out exactly like an internal w
-  assemble_level(F.g, c->td, cf, X, F.rowptr, F.asm_tab, F.vv, F.nnzb, F.vp, F.pv, c->st);
+  assemble_level_w(F.g, c->td, cf, X, F.rowptr, F.asm_tab, F.vconst, F.vv, F.nnzb, c->st);
   apply_operator<double, double>(F.g, F.rowptr, F.colidx, F.vv, F.vp, F.pv, X, c->nb, r, c->st);
   return std::sqrt(dot_host(c, r, r));
 }
@@ -884,6 +885,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       }
       L.w = dalloc<double>(c, g.nvel);
       L.asm_tab = dalloc<double>(c, assemble_table_doubles(g.dim, k));
+      L.vconst = dalloc<double>(c, L.nnzb * g.NV * g.NV);
       L.b = dalloc<char>(c, (long long)vts * g.N);
       L.x = dalloc<char>(c, (long long)vts * g.N);
       L.r = dalloc<char>(c, (long long)vts * g.N);
@@ -928,6 +930,17 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->rhs_tab = dalloc<double>(c, rhs_table_doubles(mesh->dim));
     c->hd = dalloc<double>(c, 160);
     STG_CUDA_OK(cudaMallocHost(&c->hh, sizeof(double) * 160));
+    // the part of every level's operator that does not depend on w: assembled once (with w = 0),
+    // together with the element tables and the velocity-pressure blocks
+    {
+      const AsmCoef cf0{nu, tau, c->opt.gamma1, c->opt.gamma2, 0};
+      for (LevelBufs& L : c->lv) {
+        STG_CUDA_OK(cudaMemsetAsync(L.w, 0, sizeof(double) * L.g.nvel, c->st));
+        assemble_level(L.g, c->td, cf0, L.w, L.rowptr, L.asm_tab, L.vv, L.nnzb, L.vp, L.pv, c->st);
+        STG_CUDA_OK(cudaMemcpyAsync(L.vconst, L.vv, sizeof(double) * L.nnzb * L.g.NV * L.g.NV,
+                                    cudaMemcpyDeviceToDevice, c->st));
+      }
+    }
     linearise(c, w);
     *out = c;
     return STG_OK;

@@ -241,7 +241,10 @@ __global__ void diag_blocks(Geom g, TimeData td, AsmCoef cf, const double* __res
 // Per-cell assembly: the convection (and Newton) matrices from w_a at the cell's
 // nodes, combined with the class constants, the time matrix T_ab and the factor
 // tau w_a, added into the BCSR blocks of the cell's node pairs.
-template <int DIM>
+// WONLY: add only the terms that depend on w (convection, Newton) to the time-diagonal
+// blocks of an operator that already holds the rest (a copy of the w = 0 assembly); the
+// velocity-pressure blocks do not depend on w and are left alone.
+template <int DIM, bool WONLY>
 __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
                                                       const double* __restrict__ w, const int* __restrict__ rowptr,
                                                       const double* __restrict__ tab, const double* __restrict__ K,
@@ -344,9 +347,38 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
     __syncthreads();
   }
 
-  const long long nvv = (long long)NL * NL * NV * NV;
   const long long kper = (long long)ND * ND;
   const int ncls = 1 << (2 * DIM);
+  if (WONLY) {
+    // time-diagonal entries only: (i, j, a, c, e)
+    const int nd = NL * NL * nt * DIM * DIM;
+    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+      const int e = t % DIM, c = (t / DIM) % DIM, a = (t / (DIM * DIM)) % nt;
+      const int j = (t / (DIM * DIM * nt)) % NL, i = t / (DIM * DIM * nt * NL);
+      double val;
+      if (DIM == 2) {
+        val = cf.newton ? nm[a % NTC][i][j][c][e] : 0.0;
+        if (c == e) val += cm[a % NTC][i][j];
+      } else {
+        double extra = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+          double term = 0.0;
+          if (c == e) {
+            double u = 0.0;
+            for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
+            term += u * phi[q][i];
+          }
+          if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
+          extra += qwd[q] * term;
+        }
+        val = cf.tau * td.w[a] * extra;
+      }
+      const int r = a * DIM + c, sc = a * DIM + e;
+      vv[(long long)slots[i * NL + j] * NV * NV + (long long)r * NV + sc] += val;
+    }
+    return;
+  }
+  const long long nvv = (long long)NL * NL * NV * NV;
 #pragma unroll 2
   for (long long t = threadIdx.x; t < nvv; t += blockDim.x) {
     const int s = (int)(t % NV), r = (int)((t / NV) % NV);
@@ -526,9 +558,26 @@ void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const 
     const long long cnt = g.coff[col + 1] - g.coff[col];
     if (cnt == 0) continue;
     if (g.dim == 2)
-      assemble_cells<2><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
+      assemble_cells<2, false><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
     else
-      assemble_cells<3><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
+      assemble_cells<3, false><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
+    STG_LAUNCH_OK();
+  }
+}
+
+void assemble_level_w(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
+                      const double* tab, const double* vconst, double* vv, long long nnzb, cudaStream_t st) {
+  STG_CUDA_OK(cudaMemcpyAsync(vv, vconst, sizeof(double) * nnzb * g.NV * g.NV, cudaMemcpyDeviceToDevice, st));
+  const double* K = tab + assemble_table_doubles(g.dim, -1);
+  for (int col = 0; col < (1 << g.dim); ++col) {
+    const long long cnt = g.coff[col + 1] - g.coff[col];
+    if (cnt == 0) continue;
+    if (g.dim == 2)
+      assemble_cells<2, true><<<(unsigned)cnt, 128, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, nullptr,
+                                                           nullptr);
+    else
+      assemble_cells<3, true><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, nullptr,
+                                                           nullptr);
     STG_LAUNCH_OK();
   }
 }

@@ -26,6 +26,11 @@ void upload_fe_tables();
 long long assemble_table_doubles(int dim, int k);
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                     double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
+// vv = vconst (the w = 0 assembly: time coupling, viscous, Nitsche terms) plus the terms that
+// depend on w (convection, Newton when cf.newton) on the time-diagonal blocks; needs the tables
+// of a previous assemble_level; leaves vp, pv as they are (they do not depend on w).
+void assemble_level_w(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
+                      const double* tab, const double* vconst, double* vv, long long nnzb, cudaStream_t st);
 
 // right-hand side of Eq. (2.2) from nodal f, g (internal velocity layout) and v_prev ([node][c]);
 // the mass matrix comes from the assembly table of the level (assemble_level first)
