@@ -854,7 +854,11 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->nu = nu;
     c->tau = tau;
     c->st = (cudaStream_t)stream;
-    STG_CUDA_OK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    // highest priority: the coarse factorisation is a chain of small launches whose CTAs should
+    // not queue behind the finer levels' large grids
+    int prio_lo = 0, prio_hi = 0;
+    STG_CUDA_OK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    STG_CUDA_OK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
     c->td = time_basis(k);
