@@ -81,10 +81,14 @@ typedef struct {
   double gmres_atol;       /* (defaults 1e-8 and 0; the paper's absolute 1e-9: set    */
                            /*  rtol = 0, atol = 1e-9)                                  */
   int use_graph;           /* capture the V-cycle in a CUDA graph (default 1)         */
-  int coarse_refine;       /* FP32 V-cycle only: the coarse factors are FP32 and each  */
-                           /* coarse solve adds this many steps of iterative          */
-                           /* refinement with FP64 residuals (default 1); the FP64    */
-                           /* V-cycle uses FP64 coarse factors                        */
+  int coarse_refine;       /* FP32 V-cycle with FP32 coarse factors: each coarse      */
+                           /* solve adds this many steps of iterative refinement      */
+                           /* with FP64 residuals (default 1)                         */
+  int coarse_prec;         /* FP32 V-cycle only: precision of the coarse factors,     */
+                           /* STG_F32 (default; refined as above) or STG_F64 (one    */
+                           /* FP64 solve per cycle, no refinement, but an FP64       */
+                           /* factorisation ~20x slower on GB300); the FP64 V-cycle  */
+                           /* always uses FP64 coarse factors                         */
 } stg_options;
 
 /* Fills the defaults listed above.  Returns STG_EINVAL for a null pointer. */

@@ -56,7 +56,8 @@ class stg_options(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("gamma1", ctypes.c_double),
                 ("gamma2", ctypes.c_double), ("factor_prec", ctypes.c_int), ("vcycle_prec", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
-                ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int), ("coarse_refine", ctypes.c_int)]
+                ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int), ("coarse_refine", ctypes.c_int),
+                ("coarse_prec", ctypes.c_int)]
 
 
 class stg_cnn_desc(ctypes.Structure):
@@ -144,7 +145,7 @@ def make_options(**kw) -> stg_options:
     o = stg_options()
     lib.stg_options_default(ctypes.byref(o))
     for key, val in kw.items():
-        if key in ("factor_prec", "vcycle_prec") and isinstance(val, str):
+        if key in ("factor_prec", "vcycle_prec", "coarse_prec") and isinstance(val, str):
             val = PREC[val]
         if key == "smoother" and isinstance(val, str):
             val = {"averaged": STG_VANKA_AVERAGED, "coloured": STG_VANKA_COLOURED}[val]

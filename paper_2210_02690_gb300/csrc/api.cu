@@ -275,6 +275,8 @@ void build_pattern(stg_ctx* c, LevelBufs& L) {
 }
 
 bool vc64(const stg_ctx* c) { return c->opt.vcycle_prec == STG_F64; }
+// FP64 coarse factors: always with the FP64 V-cycle, on request with the FP32 one
+bool coarse64(const stg_ctx* c) { return vc64(c) || c->opt.coarse_prec == STG_F64; }
 
 // Assemble every level for the finest-level linearisation velocity in F.w (internal
 // layout), invert the local matrices, factor the coarse system.
@@ -298,7 +300,7 @@ void linearise_internal(stg_ctx* c) {
       // it runs on the side stream while the finer levels are assembled and inverted
       STG_CUDA_OK(cudaEventRecord(c->fork, c->st));
       STG_CUDA_OK(cudaStreamWaitEvent(c->side, c->fork, 0));
-      if (vc64(c))
+      if (coarse64(c))
         c->coarse64.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->side);
       else
         c->coarse32.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->side);
@@ -324,7 +326,7 @@ void linearise_internal(stg_ctx* c) {
   STG_CUDA_OK(cudaMemcpyAsync(hs, c->status, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
   STG_CUDA_OK(cudaStreamSynchronize(c->st));
   if (hs[0]) throw Error{STG_ESINGULAR, "singular local matrix J_K of cell " + std::to_string(hs[0] - 1)};
-  const int cs = vc64(c) ? c->coarse64.read_status(c->st) : c->coarse32.read_status(c->st);
+  const int cs = coarse64(c) ? c->coarse64.read_status(c->st) : c->coarse32.read_status(c->st);
   if (cs > 0) throw Error{STG_ESINGULAR, "singular block in the coarse solver (block " + std::to_string(cs - 1) + ")"};
   if (cs < 0) throw Error{STG_ECUDA, "coarse matrix coupling outside the slab block structure"};
 }
@@ -427,7 +429,7 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
 // FP32 factors followed by coarse_refine steps of iterative refinement with the
 // residual b - J_0 x computed in FP64.
 void coarse_solve64(stg_ctx* c, const double* b, double* x) {
-  if (vc64(c)) {
+  if (coarse64(c)) {
     c->coarse64.solve(b, x, c->st);
     return;
   }
@@ -804,6 +806,8 @@ stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
   if (o->gmres_restart < 1 || o->gmres_restart > 30) throw Error{STG_EINVAL, "gmres_restart must be in 1..30"};
   if (o->smoother != STG_VANKA_AVERAGED && o->smoother != STG_VANKA_COLOURED) throw Error{STG_EINVAL, "bad smoother"};
   if (o->coarse_refine < 0 || o->coarse_refine > 20) throw Error{STG_EINVAL, "coarse_refine must be in 0..20"};
+  if (o->coarse_prec != STG_F64 && o->coarse_prec != STG_F32)
+    throw Error{STG_EINVAL, "coarse_prec must be STG_F64 or STG_F32"};
   return STG_OK;
 }
 
@@ -835,6 +839,7 @@ stg_status stg_options_default(stg_options* o) {
   o->gmres_atol = 0.0;
   o->use_graph = 1;
   o->coarse_refine = 1;
+  o->coarse_prec = STG_F32;
   return STG_OK;
 }
 
@@ -904,7 +909,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     }
     if (scratch) c->inv_scratch = dalloc<char>(c, (long long)scratch);
     c->inv_flags = dalloc<int>(c, c->lv.back().g.n_cells);
-    if (f64)
+    if (f64 || opt->coarse_prec == STG_F64)
       c->coarse64.init(c->lv[0].g, c->pure_dirichlet);
     else
       c->coarse32.init(c->lv[0].g, c->pure_dirichlet);

@@ -168,11 +168,11 @@ def test_fgmres(name):
     assert rel(x, x_ref) < 1e-8
 
 
-@pytest.mark.parametrize("prec", [("f32", "f32"), ("f32", "bf16")])
+@pytest.mark.parametrize("prec", [("f32", "f32", "f64"), ("f32", "f32", "f32"), ("f32", "bf16", "f64")])
 def test_reduced_precision_forms_converge(prec):
-    vprec, fprec = prec
+    vprec, fprec, cprec = prec
     gpu64, ref = pair("channel_k1_newton")
-    gpu, _ = pair("channel_k1_newton", vcycle_prec=vprec, factor_prec=fprec)
+    gpu, _ = pair("channel_k1_newton", vcycle_prec=vprec, factor_prec=fprec, coarse_prec=cprec)
     b = consistent_rhs(ref)
     x64, its64, _, ok64 = gpu64.gmres_solve(torch.from_numpy(b).cuda())
     x, its, relres, ok = gpu.gmres_solve(torch.from_numpy(b).cuda())
@@ -234,8 +234,14 @@ def test_update_linearisation_matches_fresh_setup():
                                   "rect_k1_ragged", "square_k0_dirichlet"])
 def test_f32_vcycle_close_to_oracle(name):
     """The FP32 V-cycle (FP32 factors, FP32 level operators in the Kronecker-split form for
-    k >= 1) against the FP64 oracle: FP32 rounding amplified by cond(J_K) stays below 1e-4."""
-    gpu, ref = pair(name, vcycle_prec="f32", factor_prec="f32")
+    k >= 1; FP64 coarse factors, or FP32 ones with one refinement step) against the FP64
+    oracle: FP32 rounding amplified by cond(J_K) stays below 1e-4."""
+    for cprec in ("f64", "f32"):
+        _check_f32_vcycle(name, cprec)
+
+
+def _check_f32_vcycle(name, cprec):
+    gpu, ref = pair(name, vcycle_prec="f32", factor_prec="f32", coarse_prec=cprec)
     b = consistent_rhs(ref)
     x = cpu(gpu.vcycle(torch.from_numpy(b).cuda()))
     x_ref = ref.vcycle(b)
