@@ -216,12 +216,13 @@ def gpu_arm(args) -> None:
     xs_np = si.reference_solution(spec, k, seed=seed + 1)
     opts = dict(nu1=cfg["nu1"], nu2=cfg["nu2"], linearisation="newton")
     w = torch.from_numpy(w_np.ravel()).cuda()
-    forms = {"f32": dict(vcycle_prec="f32", factor_prec="f32"), "f64": dict(vcycle_prec="f64", factor_prec="f64")}
+    forms = {"f32": dict(vcycle_prec="f32", factor_prec="f32"), "f64": dict(vcycle_prec="f64", factor_prec="f64"),
+             "bf16": dict(vcycle_prec="f32", factor_prec="bf16")}
     n_dofs = si.n_dofs(2, spec.n, k)
     per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
     results = {}
     main = None
-    for name in ("f32", "f64"):
+    for name in ("f32", "f64", "bf16"):
         solver = Solver(spec, k, cfg["nu"], cfg["tau"], w, **opts, **forms[name])
         b = solver.apply_jacobian(torch.from_numpy(xs_np).cuda())
         x = torch.zeros_like(b)
@@ -339,6 +340,8 @@ def gpu_arm(args) -> None:
         "time_to_tol_ms": r32["time_to_tol_ms"],
         "f64_form": {k_: results["f64"][k_] for k_ in ("value", "ms_per_step", "iters", "setup_ms", "time_to_tol_ms",
                                                         "rel_res", "autotune")},
+        "bf16_factor_form": {k_: results["bf16"][k_] for k_ in ("value", "ms_per_step", "iters", "setup_ms",
+                                                                 "time_to_tol_ms", "rel_res", "autotune")},
         "speedup_time_to_tol_f32_vs_f64": results["f64"]["time_to_tol_ms"] / r32["time_to_tol_ms"],
         "speedup_step_f32_vs_f64": results["f64"]["ms_per_step"] / r32["ms_per_step"],
         "roofline": roofline, "e2e": r32["e2e"], "gpu_launches": r32["gpu_launches"], "clocks": r32["clocks"],
@@ -481,15 +484,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start report")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve report")
-    ap.add_argument("--colour-variants", default=None, metavar="F32;F64",
+    ap.add_argument("--colour-variants", default=None, metavar="F32;F64;BF16",
                     help="skip the autotuner and set the colour-kernel variants of levels 1.. per form, "
-                         "e.g. '11,11,11;4,4,4' (the 'variants' a plain run reports), for profiler runs")
+                         "e.g. '11,11,11;4,4,4;11,11,11' (the 'variants' a plain run reports), for "
+                         "profiler runs")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the finest mesh by this factor (small cases for profiler captures)")
     args = ap.parse_args()
     if args.colour_variants:
         parts = args.colour_variants.split(";")
-        args.colour_variants = {"f32": parts[0], "f64": parts[-1]}
+        args.colour_variants = {"f32": parts[0], "f64": parts[min(1, len(parts) - 1)],
+                                "bf16": parts[min(2, len(parts) - 1)]}
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
