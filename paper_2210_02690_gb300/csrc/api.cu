@@ -939,13 +939,12 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->rhs_tab = dalloc<double>(c, rhs_table_doubles(mesh->dim));
     c->hd = dalloc<double>(c, 160);
     STG_CUDA_OK(cudaMallocHost(&c->hh, sizeof(double) * 160));
-    // the part of every level's operator that does not depend on w: assembled once (with w = 0),
-    // together with the element tables and the velocity-pressure blocks
+    // the part of every level's operator that does not depend on w: assembled once, together
+    // with the element tables and the velocity-pressure blocks
     {
       const AsmCoef cf0{nu, tau, c->opt.gamma1, c->opt.gamma2, 0};
       for (LevelBufs& L : c->lv) {
-        STG_CUDA_OK(cudaMemsetAsync(L.w, 0, sizeof(double) * L.g.nvel, c->st));
-        assemble_level(L.g, c->td, cf0, L.w, L.rowptr, L.asm_tab, L.vv, L.nnzb, L.vp, L.pv, c->st);
+        assemble_level(L.g, c->td, cf0, nullptr, L.rowptr, L.asm_tab, L.vv, L.nnzb, L.vp, L.pv, c->st);
         STG_CUDA_OK(cudaMemcpyAsync(L.vconst, L.vv, sizeof(double) * L.nnzb * L.g.NV * L.g.NV,
                                     cudaMemcpyDeviceToDevice, c->st));
       }

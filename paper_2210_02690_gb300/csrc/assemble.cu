@@ -241,9 +241,10 @@ __global__ void diag_blocks(Geom g, TimeData td, AsmCoef cf, const double* __res
 // Per-cell assembly: the convection (and Newton) matrices from w_a at the cell's
 // nodes, combined with the class constants, the time matrix T_ab and the factor
 // tau w_a, added into the BCSR blocks of the cell's node pairs.
-// WONLY: add only the terms that depend on w (convection, Newton) to the time-diagonal
-// blocks of an operator that already holds the rest (a copy of the w = 0 assembly); the
-// velocity-pressure blocks do not depend on w and are left alone.
+// WONLY = false: the part of the operator that does not depend on w (time coupling, viscous,
+// Nitsche terms, velocity-pressure blocks); w is not read.  WONLY = true: add the terms that
+// depend on w (convection, Newton) to the time-diagonal blocks of an operator that already
+// holds that part.
 template <int DIM, bool WONLY>
 __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
                                                       const double* __restrict__ w, const int* __restrict__ rowptr,
@@ -299,85 +300,101 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
                               2 * cy + (j / 3) % 3, 2 * cz + j / 9);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nt * NQ * DIM; t += blockDim.x) {
-    const int a = t / (NQ * DIM), q = (t / DIM) % NQ, c = t % DIM;
-    double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
-    for (int i = 0; i < NL; ++i) {
-      const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
-      const double wi = w[nd * NV + a * DIM + c];
-      v += phi[q][i] * wi;
-      for (int e = 0; e < DIM; ++e) gr[e] += dphi[q][i][e] * wi;
-    }
-    wq[a][q][c] = v;
-    for (int e = 0; e < DIM; ++e) gw[a][q][c][e] = gr[e];
-  }
-  __syncthreads();
-  if (DIM == 2) {
-    // u_j(q) = w_a(q) . grad phi_j(q)
-    for (int t = threadIdx.x; t < nt * NQ * NL; t += blockDim.x) {
-      const int a = t / (NQ * NL), q = (t / NL) % NQ, j = t % NL;
-      double u = 0.0;
-      for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
-      uq[a % NTC][q][j] = u;
+  if (WONLY) {
+    for (int t = threadIdx.x; t < nt * NQ * DIM; t += blockDim.x) {
+      const int a = t / (NQ * DIM), q = (t / DIM) % NQ, c = t % DIM;
+      double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
+      for (int i = 0; i < NL; ++i) {
+        const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
+        const double wi = w[nd * NV + a * DIM + c];
+        v += phi[q][i] * wi;
+        for (int e = 0; e < DIM; ++e) gr[e] += dphi[q][i][e] * wi;
+      }
+      wq[a][q][c] = v;
+      for (int e = 0; e < DIM; ++e) gw[a][q][c][e] = gr[e];
     }
     __syncthreads();
-    // convection (w_a . grad phi_j, phi_i) = sum_q W phi_i u_j; Newton phi_i phi_j d_e w_a,c (symmetric in i, j)
-    for (int t = threadIdx.x; t < nt * NL * NL; t += blockDim.x) {
-      const int a = t / (NL * NL), i = (t / NL) % NL, j = t % NL;
-      const double sa = cf.tau * td.w[a];
-      double conv = 0.0;
-      for (int q = 0; q < NQ; ++q) conv += pq[q][i] * uq[a % NTC][q][j];
-      cm[a % NTC][i][j] = sa * conv;
-      if (cf.newton && i <= j) {
-        double nw[DIM][DIM];
-        for (int c = 0; c < DIM; ++c)
-          for (int e = 0; e < DIM; ++e) nw[c][e] = 0.0;
-        for (int q = 0; q < NQ; ++q) {
-          const double pp = ppq[q][i * NL + j];
+    if (DIM == 2) {
+      // u_j(q) = w_a(q) . grad phi_j(q)
+      for (int t = threadIdx.x; t < nt * NQ * NL; t += blockDim.x) {
+        const int a = t / (NQ * NL), q = (t / NL) % NQ, j = t % NL;
+        double u = 0.0;
+        for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
+        uq[a % NTC][q][j] = u;
+      }
+      __syncthreads();
+      // convection (w_a . grad phi_j, phi_i) = sum_q W phi_i u_j; Newton phi_i phi_j d_e w_a,c (symmetric in i, j)
+      for (int t = threadIdx.x; t < nt * NL * NL; t += blockDim.x) {
+        const int a = t / (NL * NL), i = (t / NL) % NL, j = t % NL;
+        const double sa = cf.tau * td.w[a];
+        double conv = 0.0;
+        for (int q = 0; q < NQ; ++q) conv += pq[q][i] * uq[a % NTC][q][j];
+        cm[a % NTC][i][j] = sa * conv;
+        if (cf.newton && i <= j) {
+          double nw[DIM][DIM];
           for (int c = 0; c < DIM; ++c)
-            for (int e = 0; e < DIM; ++e) nw[c][e] += pp * gw[a][q][c][e];
+            for (int e = 0; e < DIM; ++e) nw[c][e] = 0.0;
+          for (int q = 0; q < NQ; ++q) {
+            const double pp = ppq[q][i * NL + j];
+            for (int c = 0; c < DIM; ++c)
+              for (int e = 0; e < DIM; ++e) nw[c][e] += pp * gw[a][q][c][e];
+          }
+          for (int c = 0; c < DIM; ++c)
+            for (int e = 0; e < DIM; ++e) {
+              nm[a % NTC][i][j][c][e] = sa * nw[c][e];
+              nm[a % NTC][j][i][c][e] = sa * nw[c][e];
+            }
         }
+      }
+      __syncthreads();
+    }
+
+    if (DIM == 2) {
+      // time-diagonal entries only: (i, j, a, c, e)
+      const int nd = NL * NL * nt * DIM * DIM;
+      for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+        const int e = t % DIM, c = (t / DIM) % DIM, a = (t / (DIM * DIM)) % nt;
+        const int j = (t / (DIM * DIM * nt)) % NL, i = t / (DIM * DIM * nt * NL);
+        double val = cf.newton ? nm[a % NTC][i][j][c][e] : 0.0;
+        if (c == e) val += cm[a % NTC][i][j];
+        const int r = a * DIM + c, sc = a * DIM + e;
+        vv[(long long)slots[i * NL + j] * NV * NV + (long long)r * NV + sc] += val;
+      }
+    } else {
+      // one task per (i, j, a): the convection value and the d x d Newton block over the
+      // quadrature points, then the d x d entries of block (a, a) of node pair (i, j)
+      for (int t = threadIdx.x; t < NL * NL * nt; t += blockDim.x) {
+        const int a = t % nt, j = (t / nt) % NL, i = t / (nt * NL);
+        double conv = 0.0, newt[DIM][DIM];
+        for (int c = 0; c < DIM; ++c)
+          for (int e = 0; e < DIM; ++e) newt[c][e] = 0.0;
+        for (int q = 0; q < NQ; ++q) {
+          double u = 0.0;
+          for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
+          const double wpi = qwd[q] * phi[q][i];
+          conv += wpi * u;
+          if (cf.newton) {
+            const double pp = wpi * phi[q][j];
+            for (int c = 0; c < DIM; ++c)
+              for (int e = 0; e < DIM; ++e) newt[c][e] += pp * gw[a][q][c][e];
+          }
+        }
+        const double sa = cf.tau * td.w[a];
+        double* blk = vv + (long long)slots[i * NL + j] * NV * NV;
         for (int c = 0; c < DIM; ++c)
           for (int e = 0; e < DIM; ++e) {
-            nm[a % NTC][i][j][c][e] = sa * nw[c][e];
-            nm[a % NTC][j][i][c][e] = sa * nw[c][e];
+            double val = cf.newton ? newt[c][e] : 0.0;
+            if (c == e) val += conv;
+            blk[(long long)(a * DIM + c) * NV + a * DIM + e] += sa * val;
           }
       }
-    }
-    __syncthreads();
-  }
-
-  const long long kper = (long long)ND * ND;
-  const int ncls = 1 << (2 * DIM);
-  if (WONLY) {
-    // time-diagonal entries only: (i, j, a, c, e)
-    const int nd = NL * NL * nt * DIM * DIM;
-    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
-      const int e = t % DIM, c = (t / DIM) % DIM, a = (t / (DIM * DIM)) % nt;
-      const int j = (t / (DIM * DIM * nt)) % NL, i = t / (DIM * DIM * nt * NL);
-      double val;
-      if (DIM == 2) {
-        val = cf.newton ? nm[a % NTC][i][j][c][e] : 0.0;
-        if (c == e) val += cm[a % NTC][i][j];
-      } else {
-        double extra = 0.0;
-        for (int q = 0; q < NQ; ++q) {
-          double term = 0.0;
-          if (c == e) {
-            double u = 0.0;
-            for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
-            term += u * phi[q][i];
-          }
-          if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
-          extra += qwd[q] * term;
-        }
-        val = cf.tau * td.w[a] * extra;
-      }
-      const int r = a * DIM + c, sc = a * DIM + e;
-      vv[(long long)slots[i * NL + j] * NV * NV + (long long)r * NV + sc] += val;
     }
     return;
   }
+  // constant part (the operator at w = 0): time coupling, viscous and Nitsche terms from the
+  // class tables, the velocity-pressure blocks
+  const long long kper = (long long)ND * ND;
+  const int ncls = 1 << (2 * DIM);
   const long long nvv = (long long)NL * NL * NV * NV;
 #pragma unroll 2
   for (long long t = threadIdx.x; t < nvv; t += blockDim.x) {
@@ -387,23 +404,6 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
     double val;
     if (a == b) {
       val = K[((long long)a * ncls + cls) * kper + (i * DIM + c) * ND + j * DIM + e];
-      if (DIM == 2) {
-        if (c == e) val += cm[a % NTC][i][j];
-        if (cf.newton) val += nm[a % NTC][i][j][c][e];
-      } else {
-        double extra = 0.0;
-        for (int q = 0; q < NQ; ++q) {
-          double term = 0.0;
-          if (c == e) {
-            double u = 0.0;
-            for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
-            term += u * phi[q][i];
-          }
-          if (cf.newton) term += phi[q][i] * phi[q][j] * gw[a][q][c][e];
-          extra += qwd[q] * term;
-        }
-        val += cf.tau * td.w[a] * extra;
-      }
     } else {
       val = c == e ? td.T[a][b] * mass[i * NL + j] : 0.0;
     }

@@ -120,6 +120,110 @@ __global__ void __launch_bounds__(1024) bgj_kernel(int m, T* const* As, int* sta
     for (long long t = tid; t < (long long)m * m; t += nth) G[t] = A[t];
 }
 
+// Gauss-Jordan for matrices too large for shared memory: each pivot step is two launches over
+// the whole batch, so the rank-one updates (O(m^2) per step) spread over all SMs instead of one
+// CTA per matrix.  Same operations and order as bgj_kernel (first maximal pivot, saved pivot
+// column, row interchange, scaled pivot row, update, columns swapped back at the end).
+template <typename T>
+__global__ void __launch_bounds__(256) gj_pivot_kernel(int m, int j, T* const* As, T* __restrict__ col,
+                                                       int* __restrict__ perm, int* __restrict__ fail) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  if (fail[b]) return;
+  T* A = As[b];
+  T* cj = col + (long long)b * m;
+  __shared__ T s_best[256];
+  __shared__ int s_idx[256];
+  __shared__ int s_pr, s_bad;
+  __shared__ T s_pv, s_ajj;
+  T best = -1;
+  int bi = m;
+  for (int i = j + tid; i < m; i += blockDim.x) {
+    const T v = fabs(A[(long long)i * m + j]);
+    if (v > best || (v == best && i < bi)) {
+      best = v;
+      bi = i;
+    }
+  }
+  s_best[tid] = best;
+  s_idx[tid] = bi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+      const T ob = s_best[tid + w];
+      const int oi = s_idx[tid + w];
+      if (ob > s_best[tid] || (ob == s_best[tid] && oi < s_idx[tid])) {
+        s_best[tid] = ob;
+        s_idx[tid] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const int pr = s_idx[0];
+    const T pv = pr < m ? A[(long long)pr * m + j] : (T)0;
+    s_pr = pr;
+    s_pv = pv;
+    s_ajj = A[(long long)j * m + j];
+    s_bad = (!(fabs(pv) > (T)0) || isinf(pv)) ? 1 : 0;
+    if (s_bad) fail[b] = 1;
+    perm[(long long)b * m + j] = pr;
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const int pr = s_pr;
+  const T inv = (T)1 / s_pv;
+  for (int i = tid; i < m; i += blockDim.x) cj[i] = i == j ? s_pv : (i == pr ? s_ajj : A[(long long)i * m + j]);
+  __syncthreads();
+  for (int l = tid; l < m; l += blockDim.x) {
+    const T vj = A[(long long)j * m + l], vp = A[(long long)pr * m + l];
+    A[(long long)j * m + l] = l == j ? inv : vp * inv;
+    if (pr != j) A[(long long)pr * m + l] = vj;
+  }
+}
+
+// A[i][l] = (l == j ? 0 : A[i][l]) - col[i] A[j][l] for all i != j; 32 columns x 32 rows a block
+template <typename T>
+__global__ void __launch_bounds__(256) gj_update_kernel(int m, int j, T* const* As, const T* __restrict__ col,
+                                                        const int* __restrict__ fail) {
+  const int b = blockIdx.z;
+  if (fail[b]) return;
+  T* A = As[b];
+  const T* cj = col + (long long)b * m;
+  const int l = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (l >= m) return;
+  const T rj = A[(long long)j * m + l];
+  const int i0 = blockIdx.y * 32 + (threadIdx.x >> 5);
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + 8 * r;
+    if (i >= m || i == j) continue;
+    T* ai = A + (long long)i * m + l;
+    *ai = (l == j ? (T)0 : *ai) - cj[i] * rj;
+  }
+}
+
+// columns swapped back (last interchange first); the status records the first failed matrix
+template <typename T>
+__global__ void __launch_bounds__(1024) gj_unpermute_kernel(int m, T* const* As, const int* __restrict__ perm,
+                                                            const int* __restrict__ fail, int* status) {
+  const int b = blockIdx.x;
+  if (fail[b]) {
+    if (threadIdx.x == 0) atomicCAS(status, 0, 1 + b);
+    return;
+  }
+  T* A = As[b];
+  const int* pm = perm + (long long)b * m;
+  for (int j = m - 1; j >= 0; --j) {
+    const int pj = pm[j];
+    if (pj != j)
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const T t = A[(long long)i * m + j];
+        A[(long long)i * m + j] = A[(long long)i * m + pj];
+        A[(long long)i * m + pj] = t;
+      }
+    __syncthreads();
+  }
+}
+
 // C = alpha A B + beta C, row-major, batched through pointer arrays; 32x32 tiles.
 template <typename T>
 __global__ void __launch_bounds__(256) bgemm_kernel(int M, int N, int K, T alpha, const T* const* As, int lda,
@@ -416,6 +520,14 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   alloc(&GU, nsv * mV * mV);
   alloc(&TL, nsv * mV * mV);
   alloc(&bV, nsv * mV);
+  {
+    const long long nb = std::max(nsi, nsv), mm = std::max(mI, mV);
+    alloc(&gj_scr, nb * mm);
+    STG_CUDA_OK(cudaMalloc(&gj_perm, sizeof(int) * nb * mm));
+    owned.push_back(gj_perm);
+    STG_CUDA_OK(cudaMalloc(&gj_fail, sizeof(int) * nb));
+    owned.push_back(gj_fail);
+  }
   alloc(&tV, nsv * mV);
   alloc(&xV, nsv * mV);
   alloc(&bI, nsi * mI);
@@ -563,8 +675,10 @@ void CoarseSolver<T>::release() {
   owned.clear();
 }
 
+// Batched in-place inverses.  scratch: batch * m values of T, perm: batch * m ints, fail: batch
+// ints (used only for matrices of 512 rows or more, which take the multi-launch form).
 template <typename T>
-static void gj(int m, T* const* A, int batch, int* status, cudaStream_t st) {
+static void gj(int m, T* const* A, int batch, int* status, T* scratch, int* perm, int* fail, cudaStream_t st) {
   if (batch <= 0 || m <= 0) return;
   const size_t tail = sizeof(T) * m + sizeof(int) * m;
   const size_t full = sizeof(T) * (size_t)m * m + tail;
@@ -572,11 +686,25 @@ static void gj(int m, T* const* A, int batch, int* status, cudaStream_t st) {
     STG_CUDA_OK(cudaFuncSetAttribute(bgj_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)std::max<size_t>(full, 48 * 1024)));
     bgj_kernel<T, true><<<batch, 1024, full, st>>>(m, A, status);
-  } else {
+    STG_LAUNCH_OK();
+    return;
+  }
+  if (m < 512) {  // one CTA per matrix in global memory: faster than 2m launches at this size
     STG_CUDA_OK(cudaFuncSetAttribute(bgj_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)std::max<size_t>(tail, 48 * 1024)));
     bgj_kernel<T, false><<<batch, 1024, tail, st>>>(m, A, status);
+    STG_LAUNCH_OK();
+    return;
   }
+  STG_CUDA_OK(cudaMemsetAsync(fail, 0, sizeof(int) * batch, st));
+  const dim3 ugrid((m + 31) / 32, (m + 31) / 32, batch);
+  for (int j = 0; j < m; ++j) {
+    gj_pivot_kernel<T><<<batch, 256, 0, st>>>(m, j, A, scratch, perm, fail);
+    STG_LAUNCH_OK();
+    gj_update_kernel<T><<<ugrid, 256, 0, st>>>(m, j, A, scratch, fail);
+    STG_LAUNCH_OK();
+  }
+  gj_unpermute_kernel<T><<<batch, 1024, 0, st>>>(m, A, perm, fail, status);
   STG_LAUNCH_OK();
 }
 
@@ -618,7 +746,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
   pin_diag<T><<<1, 32, 0, st>>>(v);
   STG_LAUNCH_OK();
   // interiors: A_II^{-1}, W = A_II^{-1} A_IV, C = A_VI W, S = A_VV - C (scattered)
-  gj<T>((int)mI, d_AII, (int)nsi, v.status, st);
+  gj<T>((int)mI, d_AII, (int)nsi, v.status, gj_scr, gj_perm, gj_fail, st);
   const T one = 1, zero = 0, mone = -1;
   gemm<T>((int)mI, (int)(2 * mV), (int)mI, one, d_AII, (int)mI, d_AIV, (int)(2 * mV), zero, d_W, (int)(2 * mV),
           (int)nsi, st);
@@ -629,7 +757,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
   // block cyclic reduction of the vertex-plane system
   const int m = (int)mV;
   for (const auto& lv : levels) {
-    gj<T>(m, lv.oD, lv.n_odd, v.status, st);
+    gj<T>(m, lv.oD, lv.n_odd, v.status, gj_scr, gj_perm, gj_fail, st);
     gemm<T>(m, m, m, one, lv.oD, m, lv.oL, m, zero, lv.oGL, m, lv.n_odd, st);
     gemm<T>(m, m, m, one, lv.oD, m, lv.oU, m, zero, lv.oGU, m, lv.n_odd, st);
     // D_j -= L_j GU_{j-st} + U_j GL_{j+st}
@@ -644,7 +772,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
     gemm<T>(m, m, m, mone, lv.rU, m, lv.rGU, m, zero, lv.rT, m, lv.n_right, st);
     copy_ptrs<T>(lv.rT, lv.rU, lv.n_right, (long long)m * m, st);
   }
-  gj<T>(m, d_top, 1, v.status, st);
+  gj<T>(m, d_top, 1, v.status, gj_scr, gj_perm, gj_fail, st);
 }
 
 template <typename T>

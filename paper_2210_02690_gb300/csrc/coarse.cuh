@@ -34,6 +34,8 @@ struct CoarseSolver {
   T **d_AII = nullptr, **d_AIV = nullptr, **d_AVI = nullptr, **d_W = nullptr, **d_C = nullptr;
   T **d_bI = nullptr, **d_gI = nullptr, **d_cI = nullptr, **d_xVs = nullptr, **d_xI = nullptr;
   T **d_top = nullptr, **d_topb = nullptr, **d_topx = nullptr;
+  T* gj_scr = nullptr;  // Gauss-Jordan scratch for blocks too large for shared memory
+  int *gj_perm = nullptr, *gj_fail = nullptr;
   std::vector<CrLevel<T>> levels;
   std::vector<void*> owned;
 

@@ -24,6 +24,8 @@ struct AsmCoef {
 void upload_fe_tables();
 // doubles of the per-level table of w-independent element matrices (mass + one set per face class)
 long long assemble_table_doubles(int dim, int k);
+// vv, vp, pv = the part of the operator that does not depend on w (time coupling, viscous and
+// Nitsche terms, velocity-pressure blocks), and the level's element tables; w is not read
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                     double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st);
 // vv = vconst (the w = 0 assembly: time coupling, viscous, Nitsche terms) plus the terms that

@@ -27,6 +27,8 @@ CASES = {
     "rect_k1_ragged": (si.MeshSpec(2, (10, 6), (0.3, -0.2), (1.3, 0.5), 2, si.FACE_XLO | si.FACE_YHI), 1, True),
     "square_k3": (si.MeshSpec(2, (4, 4), (0.0, 0.0), (1.0, 1.0), 2, si.ALL2), 3, True),
     "channel_k4": (si.MeshSpec(2, (4, 2), (0.0, 0.0), (2.2, 0.41), 2, OUT2), 4, True),
+    # coarse 4x16: interior slab blocks of 226 unknowns, too large for shared memory in FP64
+    "tall_k1_coarse_global": (si.MeshSpec(2, (8, 32), (0.0, 0.0), (0.5, 2.0), 2, OUT2), 1, True),
     "cube_k0": (si.MeshSpec(3, (4, 4, 2), (0.0,) * 3, (1.0, 1.0, 0.5), 2, si.ALL3), 0, True),
     "cube_k1_outflow": (si.MeshSpec(3, (2, 4, 2), (0.0,) * 3, (0.5, 1.0, 0.5), 2, si.ALL3 & ~si.FACE_XHI), 1, True),
 }
@@ -122,6 +124,30 @@ def test_coarse_solve(name):
     if ref.singular:
         x = multigrid.normalise_pressure(lev0, x)
     assert rel(x, ref.coarse_solve(b) if not ref.singular else multigrid.normalise_pressure(lev0, ref.coarse_solve(b))) < 1e-9
+
+
+def test_coarse_solve_large_slab_blocks():
+    """Coarse mesh 2x64 at k = 2: slab blocks of 1347 and 777 unknowns, inverted by the
+    multi-launch Gauss-Jordan.  Explicit inverses of such blocks carry rounding that grows like
+    n_b eps cond(block): the backward error is held to 1e-9 (observed 6e-11) and the forward
+    error to cond(J_0) times that (cond(J_0) = 9.4e4)."""
+    from paper_2210_02690_gb300 import Solver
+    import oracle
+    spec = si.MeshSpec(2, (4, 128), (0.0, 0.0), (0.25, 8.0), 2, OUT2)
+    w = si.channel_w(spec, 2)
+    gpu = Solver(spec, 2, NU, TAU, torch.from_numpy(w.ravel()).cuda(), nu1=2, nu2=2, linearisation="newton")
+    ref = oracle.Hierarchy(spec, 2, NU, TAU, w, newton=True, nu1=2, nu2=2)
+    xs = si.reference_solution(spec, 2, seed=5, level=0)
+    b = ref.J[0] @ xs
+    x = cpu(gpu.coarse_solve(torch.from_numpy(b).cuda()))
+    assert rel(ref.J[0] @ x, b) < 1e-9
+    cond = np.linalg.cond(ref.J[0].toarray())
+    assert rel(x, ref.coarse_solve(b)) < cond * 1e-9
+    # the whole solver still converges to the FP64 oracle's solution of the fine system
+    bf = consistent_rhs(ref)
+    xf, its, relres, ok = gpu.gmres_solve(torch.from_numpy(bf).cuda())
+    assert ok and relres <= 1e-8 and rel(ref.apply(cpu(xf)), bf) < 1.01e-8
+    gpu.close()
 
 
 @pytest.mark.parametrize("name", list(CASES))
