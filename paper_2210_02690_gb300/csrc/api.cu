@@ -196,6 +196,11 @@ struct stg_ctx {
   // side stream of the set-up: the coarse factorisation overlaps the finer levels' work
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // aux stream of the set-up: the patch inversions (FP32 pipes) of one level overlap the
+  // assembly (FP64 pipe) of the level assembled after it
+  cudaStream_t aux = nullptr;
+  std::vector<cudaEvent_t> lev_ev;
+  cudaEvent_t aux_done = nullptr;
   TimeData td{};
   std::vector<LevelBufs> lv;
   CoarseSolver<double> coarse64;  // FP64 form
@@ -285,7 +290,10 @@ void linearise_internal(stg_ctx* c) {
   for (int l = nl - 1; l > 0; --l) inject_w(c->lv[l - 1].g, c->lv[l].g, c->lv[l].w, c->lv[l - 1].w, c->st);
   AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, c->opt.linearisation == STG_NEWTON ? 1 : 0};
   STG_CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
-  for (int l = 0; l < nl; ++l) {
+  // level order 0, nl - 1, nl - 2, ..., 1: the coarse factorisation starts first, and the
+  // largest inversion (finest level) overlaps the assembly of the intermediate levels
+  for (int i = 0; i < nl; ++i) {
+    const int l = i == 0 ? 0 : nl - i;
     LevelBufs& L = c->lv[l];
     assemble_level_w(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vconst, L.vv, L.nnzb, c->st);
     if (!vc64(c)) {
@@ -307,20 +315,26 @@ void linearise_internal(stg_ctx* c) {
       STG_CUDA_OK(cudaEventRecord(c->join, c->side));
       continue;
     }
+    // the inversion of this level runs on the aux stream (one level at a time: the scratch and
+    // the flags are shared) while the main stream assembles the next level
+    STG_CUDA_OK(cudaEventRecord(c->lev_ev[l], c->st));
+    STG_CUDA_OK(cudaStreamWaitEvent(c->aux, c->lev_ev[l], 0));
     const int fp = c->opt.factor_prec;
     // FP32/BF16 factors are computed in FP32 on the equilibrated J_K; FP64 factors in FP64
     const int cf32 = fp != STG_F64 ? 1 : 0;
     if (fp == STG_F64)
       invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, nullptr, nullptr, nullptr, (double*)L.jinv, 0, c->status, c->inv_scratch,
-                             c->inv_flags, c->st);
+                             c->inv_flags, c->aux);
     else if (fp == STG_F32)
       invert_patches<float>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32, (float*)L.jinv, cf32, c->status, c->inv_scratch,
-                            c->inv_flags, c->st);
+                            c->inv_flags, c->aux);
     else
       invert_patches<__nv_bfloat16>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32,
                                     (__nv_bfloat16*)L.jinv, cf32, c->status,
-                                    c->inv_scratch, c->inv_flags, c->st);
+                                    c->inv_scratch, c->inv_flags, c->aux);
   }
+  STG_CUDA_OK(cudaEventRecord(c->aux_done, c->aux));
+  STG_CUDA_OK(cudaStreamWaitEvent(c->st, c->aux_done, 0));
   STG_CUDA_OK(cudaStreamWaitEvent(c->st, c->join, 0));
   int hs[4];
   STG_CUDA_OK(cudaMemcpyAsync(hs, c->status, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
@@ -866,6 +880,10 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     STG_CUDA_OK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+    STG_CUDA_OK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    STG_CUDA_OK(cudaEventCreateWithFlags(&c->aux_done, cudaEventDisableTiming));
+    c->lev_ev.assign(mesh->n_levels, nullptr);
+    for (auto& e : c->lev_ev) STG_CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->td = time_basis(k);
     c->pure_dirichlet = mesh->dirichlet_faces == (1u << (2 * mesh->dim)) - 1u;
     upload_fe_tables();
@@ -1567,6 +1585,13 @@ void stg_destroy(stg_ctx* c) {
   }
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+  }
+  if (c->aux_done) cudaEventDestroy(c->aux_done);
+  for (auto& e : c->lev_ev)
+    if (e) cudaEventDestroy(e);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto& e : c->prof_ev) cudaEventDestroy(e);
   c->coarse64.release();

@@ -530,14 +530,15 @@ __global__ void __launch_bounds__(256) invert_warp_kernel(Geom g, const int* __r
 // so the pivot column is always register 0 and the elimination loop needs no
 // dynamic register indexing; after n steps the columns are back in order.
 template <int N, int PPB, typename MT, typename FT>
-__global__ void __launch_bounds__(N * PPB) invert_rows_kernel(Geom g, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(N * PPB, N == 42 ? 6 : 1) invert_rows_kernel(Geom g, const int* __restrict__ rowptr,
                                                               const MT* __restrict__ vv, const MT* __restrict__ vp,
                                                               const MT* __restrict__ pv, FT* __restrict__ jinv,
                                                               long long stride, int* __restrict__ flags) {
   constexpr int DIM = 2, NL = 9, NT = N / 21, NV = NT * DIM, NP = NT * (DIM + 1), VOFF = NL * NV;
   static_assert(VOFF + NP == N, "2D Q2/P1disc patch");
+  constexpr int NR = (N + 3) / 4 * 4;  // pivot-row stride: float4 reads
   __shared__ float s_abs[PPB][N][N + 1];
-  __shared__ float s_row[PPB][N];
+  __shared__ __align__(16) float s_row[2][PPB][NR];  // double-buffered pivot row
   __shared__ float s_cs[PPB][N];
   __shared__ float s_rs[PPB][N];
   __shared__ int s_bad[PPB];
@@ -600,30 +601,43 @@ __global__ void __launch_bounds__(N * PPB) invert_rows_kernel(Geom g, const int*
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < N; ++l) a[l] *= s_cs[pl][l];
-    // elimination; column j sits in register 0 at step j
+    // elimination; column j sits in register 0 at step j.  The pivot row of step j goes to
+    // buffer j & 1: the next step writes the other buffer, so one barrier per step suffices
+    // (a thread that reaches step j + 2's write has passed step j + 1's barrier, which every
+    // thread reaches only after its reads of step j).
     for (int j = 0; j < N; ++j) {
       const bool isp = row == j;
+      float* sr = s_row[j & 1][pl];
       if (isp) {
         const float piv = a[0];
         if (!(fabsf(piv) > 1e-3f) || isinf(piv)) s_bad[pl] = 1;
         const float inv = 1.f / piv;
-        s_row[pl][0] = inv;
+        sr[0] = inv;
 #pragma unroll
-        for (int l = 1; l < N; ++l) s_row[pl][l] = a[l] * inv;
+        for (int l = 1; l < N; ++l) sr[l] = a[l] * inv;
       }
       __syncthreads();
       const float f = a[0];
+      float rv0 = 0.f;
+      // a[l] <- pivot row[l + 1] (pivot thread) or a[l + 1] - f row[l + 1], four entries a read;
+      // a[l + 1] is read before it is overwritten
 #pragma unroll
-      for (int l = 0; l < N - 1; ++l) {
-        const float rv = s_row[pl][l + 1];
-        a[l] = isp ? rv : fmaf(-f, rv, a[l + 1]);
+      for (int l4 = 0; l4 < NR / 4; ++l4) {
+        const float4 q = reinterpret_cast<const float4*>(sr)[l4];
+        const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = 4 * l4 + u;  // pivot-row column; updates a[c - 1]
+          if (c == 0) {
+            rv0 = qv[u];
+          } else if (c < N) {
+            a[c - 1] = isp ? qv[u] : fmaf(-f, qv[u], a[c]);
+          }
+        }
       }
-      {
-        const float rv = s_row[pl][0];
-        a[N - 1] = isp ? rv : -f * rv;
-      }
-      __syncthreads();
+      a[N - 1] = isp ? rv0 : -f * rv0;
     }
+    __syncthreads();
     if (live) {
       if (s_bad[pl]) {
         if (row == 0) flags[p] = 1;
@@ -942,11 +956,11 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     };
     if (vv32) {
       if (n == 21) run(invert_rows_kernel<21, 8, float, FT>, 8, 21 * 8, vv32, vp32, pv32);
-      else if (n == 42) run(invert_rows_kernel<42, 4, float, FT>, 4, 42 * 4, vv32, vp32, pv32);
+      else if (n == 42) run(invert_rows_kernel<42, 2, float, FT>, 2, 42 * 2, vv32, vp32, pv32);
       else run(invert_rows_kernel<63, 2, float, FT>, 2, 63 * 2, vv32, vp32, pv32);
     } else {
       if (n == 21) run(invert_rows_kernel<21, 8, double, FT>, 8, 21 * 8, vv, vp, pv);
-      else if (n == 42) run(invert_rows_kernel<42, 4, double, FT>, 4, 42 * 4, vv, vp, pv);
+      else if (n == 42) run(invert_rows_kernel<42, 2, double, FT>, 2, 42 * 2, vv, vp, pv);
       else run(invert_rows_kernel<63, 2, double, FT>, 2, 63 * 2, vv, vp, pv);
     }
     only = flags;
