@@ -196,10 +196,9 @@ struct stg_ctx {
   // side stream of the set-up: the coarse factorisation overlaps the finer levels' work
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
-  // aux stream of the set-up: the patch inversions (FP32 pipes) of one level overlap the
-  // assembly (FP64 pipe) of the level assembled after it
+  // aux stream of the set-up: the intermediate levels (assembly and inversion) run beside the
+  // finest level's chain
   cudaStream_t aux = nullptr;
-  std::vector<cudaEvent_t> lev_ev;
   cudaEvent_t aux_done = nullptr;
   TimeData td{};
   std::vector<LevelBufs> lv;
@@ -209,6 +208,9 @@ struct stg_ctx {
   int* status = nullptr;
   void* inv_scratch = nullptr;
   int* inv_flags = nullptr;  // per patch: redo with pivoting
+  // the same for the intermediate levels, which are inverted concurrently with the finest
+  void* inv_scratch2 = nullptr;
+  int* inv_flags2 = nullptr;
   // FGMRES (finest level, internal layout, FP64)
   double *V = nullptr, *Z = nullptr, *wv = nullptr, *rv = nullptr, *partial = nullptr, *hd = nullptr;
   double *vin = nullptr, *vout = nullptr, *tmp_a = nullptr, *tmp_b = nullptr;
@@ -290,49 +292,50 @@ void linearise_internal(stg_ctx* c) {
   for (int l = nl - 1; l > 0; --l) inject_w(c->lv[l - 1].g, c->lv[l].g, c->lv[l].w, c->lv[l - 1].w, c->st);
   AsmCoef cf{c->nu, c->tau, c->opt.gamma1, c->opt.gamma2, c->opt.linearisation == STG_NEWTON ? 1 : 0};
   STG_CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->st));
-  // level order 0, nl - 1, nl - 2, ..., 1: the coarse factorisation starts first, and the
-  // largest inversion (finest level) overlaps the assembly of the intermediate levels
+  // three chains once w is on every level: the finest level on the main stream; the coarse
+  // level and its factorisation (a chain of small, latency-bound launches) on the side stream;
+  // the intermediate levels on the aux stream.  The finest chain is enqueued first; the other
+  // two have the higher stream priority, so their smaller grids do not queue behind it.
+  STG_CUDA_OK(cudaEventRecord(c->fork, c->st));
+  STG_CUDA_OK(cudaStreamWaitEvent(c->side, c->fork, 0));
+  STG_CUDA_OK(cudaStreamWaitEvent(c->aux, c->fork, 0));
   for (int i = 0; i < nl; ++i) {
-    const int l = i == 0 ? 0 : nl - i;
+    const int l = i == 0 ? nl - 1 : i - 1;
     LevelBufs& L = c->lv[l];
-    assemble_level_w(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vconst, L.vv, L.nnzb, c->st);
+    cudaStream_t s = l == 0 ? c->side : (l == nl - 1 ? c->st : c->aux);
+    assemble_level_w(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vconst, L.vv, L.nnzb, s);
     if (!vc64(c)) {
-      convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, c->st);
+      if (L.vv32) convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, s);
       const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
-      convert(nvp, L.vp, L.vp32, c->st);
-      convert(nvp, L.pv, L.pv32, c->st);
-      if (L.mk32) kron_split(L.g, L.nnzb, L.vv, c->td, L.mk32, L.ak32, c->st);
+      convert(nvp, L.vp, L.vp32, s);
+      convert(nvp, L.pv, L.pv32, s);
+      if (L.mk32) kron_split(L.g, L.nnzb, L.vv, c->td, L.mk32, L.ak32, s);
     }
     if (l == 0) {
-      // the coarse factorisation (a chain of small, latency-bound launches) needs only J_0:
-      // it runs on the side stream while the finer levels are assembled and inverted
-      STG_CUDA_OK(cudaEventRecord(c->fork, c->st));
-      STG_CUDA_OK(cudaStreamWaitEvent(c->side, c->fork, 0));
       if (coarse64(c))
-        c->coarse64.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->side);
+        c->coarse64.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, s);
       else
-        c->coarse32.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, c->side);
-      STG_CUDA_OK(cudaEventRecord(c->join, c->side));
+        c->coarse32.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, s);
       continue;
     }
-    // the inversion of this level runs on the aux stream (one level at a time: the scratch and
-    // the flags are shared) while the main stream assembles the next level
-    STG_CUDA_OK(cudaEventRecord(c->lev_ev[l], c->st));
-    STG_CUDA_OK(cudaStreamWaitEvent(c->aux, c->lev_ev[l], 0));
+    // the finest level and the intermediate ones are inverted concurrently: separate flags
+    // and scratch (the intermediate levels share theirs, in level order on the aux stream)
+    int* flags = l == nl - 1 ? c->inv_flags : c->inv_flags2;
+    void* scr = l == nl - 1 ? c->inv_scratch : c->inv_scratch2;
     const int fp = c->opt.factor_prec;
     // FP32/BF16 factors are computed in FP32 on the equilibrated J_K; FP64 factors in FP64
     const int cf32 = fp != STG_F64 ? 1 : 0;
     if (fp == STG_F64)
-      invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, nullptr, nullptr, nullptr, (double*)L.jinv, 0, c->status, c->inv_scratch,
-                             c->inv_flags, c->aux);
+      invert_patches<double>(L.g, L.rowptr, L.vv, L.vp, L.pv, nullptr, nullptr, nullptr, (double*)L.jinv, 0, c->status,
+                             scr, flags, s);
     else if (fp == STG_F32)
-      invert_patches<float>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32, (float*)L.jinv, cf32, c->status, c->inv_scratch,
-                            c->inv_flags, c->aux);
+      invert_patches<float>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32, (float*)L.jinv, cf32, c->status,
+                            scr, flags, s);
     else
       invert_patches<__nv_bfloat16>(L.g, L.rowptr, L.vv, L.vp, L.pv, L.vv32, L.vp32, L.pv32,
-                                    (__nv_bfloat16*)L.jinv, cf32, c->status,
-                                    c->inv_scratch, c->inv_flags, c->aux);
+                                    (__nv_bfloat16*)L.jinv, cf32, c->status, scr, flags, s);
   }
+  STG_CUDA_OK(cudaEventRecord(c->join, c->side));
   STG_CUDA_OK(cudaEventRecord(c->aux_done, c->aux));
   STG_CUDA_OK(cudaStreamWaitEvent(c->st, c->aux_done, 0));
   STG_CUDA_OK(cudaStreamWaitEvent(c->st, c->join, 0));
@@ -873,23 +876,21 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->nu = nu;
     c->tau = tau;
     c->st = (cudaStream_t)stream;
-    // highest priority: the coarse factorisation is a chain of small launches whose CTAs should
-    // not queue behind the finer levels' large grids
+    // highest priority: the coarse factorisation and the intermediate levels are chains of
+    // smaller launches whose CTAs should not queue behind the finest level's large grids
     int prio_lo = 0, prio_hi = 0;
     STG_CUDA_OK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
     STG_CUDA_OK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi));
+    STG_CUDA_OK(cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_hi));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
-    STG_CUDA_OK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     STG_CUDA_OK(cudaEventCreateWithFlags(&c->aux_done, cudaEventDisableTiming));
-    c->lev_ev.assign(mesh->n_levels, nullptr);
-    for (auto& e : c->lev_ev) STG_CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     c->td = time_basis(k);
     c->pure_dirichlet = mesh->dirichlet_faces == (1u << (2 * mesh->dim)) - 1u;
     upload_fe_tables();
     const int nl = mesh->n_levels;
     c->lv.resize(nl);
-    size_t scratch = 0;
+    size_t scratch = 0, scratch2 = 0;
     const bool f64 = vc64(c);
     const size_t vts = f64 ? 8 : 4;
     for (int l = 0; l < nl; ++l) {
@@ -902,12 +903,15 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       L.vp = dalloc<double>(c, nvp);
       L.pv = dalloc<double>(c, nvp);
       if (!f64) {
-        L.vv32 = dalloc<float>(c, L.nnzb * g.NV * g.NV);
         L.vp32 = dalloc<float>(c, nvp);
         L.pv32 = dalloc<float>(c, nvp);
         if (l > 0 && kron_supported(g)) {
+          // the FP32 residual takes the Kronecker form, and the patch inversion rounds the
+          // FP64 blocks as it gathers them: no FP32 copy of the dense blocks
           L.mk32 = dalloc<float>(c, L.nnzb);
           L.ak32 = dalloc<float>(c, L.nnzb * g.nt * g.dim * g.dim);
+        } else {
+          L.vv32 = dalloc<float>(c, L.nnzb * g.NV * g.NV);
         }
       }
       L.w = dalloc<double>(c, g.nvel);
@@ -922,11 +926,16 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       if (l > 0) {
         L.jinv = dalloc<char>(c, (long long)fsize(opt->factor_prec) * patch_stride(g.npatch) * g.n_cells);
         const int cf32 = opt->factor_prec != STG_F64 ? 1 : 0;
-        scratch = std::max(scratch, invert_scratch_bytes(g, cf32));
+        if (l == mesh->n_levels - 1)
+          scratch = invert_scratch_bytes(g, cf32);
+        else
+          scratch2 = std::max(scratch2, invert_scratch_bytes(g, cf32));
       }
     }
     if (scratch) c->inv_scratch = dalloc<char>(c, (long long)scratch);
+    if (scratch2) c->inv_scratch2 = dalloc<char>(c, (long long)scratch2);
     c->inv_flags = dalloc<int>(c, c->lv.back().g.n_cells);
+    if (mesh->n_levels > 2) c->inv_flags2 = dalloc<int>(c, c->lv[mesh->n_levels - 2].g.n_cells);
     if (f64 || opt->coarse_prec == STG_F64)
       c->coarse64.init(c->lv[0].g, c->pure_dirichlet);
     else
@@ -1590,8 +1599,6 @@ void stg_destroy(stg_ctx* c) {
     cudaStreamDestroy(c->aux);
   }
   if (c->aux_done) cudaEventDestroy(c->aux_done);
-  for (auto& e : c->lev_ev)
-    if (e) cudaEventDestroy(e);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto& e : c->prof_ev) cudaEventDestroy(e);
   c->coarse64.release();

@@ -946,11 +946,10 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
   if (compute_f32 && g.dim == 2 && n <= 63 && flags) {
     // register-resident pivot-free pass, then the pivoting kernel for flagged patches only
     STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
+    // one CTA per PPB patches (not a resident-capped grid): the set-up runs this beside other
+    // streams' kernels, and a static split over resident CTAs would wait for the busiest SM
     auto run = [&](auto kern, int ppb, int nthreads, auto* V, auto* VP, auto* PV) {
-      const long long want = (g.n_cells + ppb - 1) / ppb;
-      int per_sm = 0;
-      STG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, 0));
-      const long long grid = std::max<long long>(1, std::min<long long>(want, (long long)sms * std::max(per_sm, 1)));
+      const long long grid = std::max<long long>(1, std::min<long long>((g.n_cells + ppb - 1) / ppb, 0x7fffffffLL));
       kern<<<(unsigned)grid, nthreads, 0, st>>>(g, rowptr, V, VP, PV, jinv, stride, flags);
       STG_LAUNCH_OK();
     };
