@@ -105,7 +105,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -209,8 +209,8 @@ def gpu_arm(args) -> None:
     world, rank, local = dist_setup()
     cfg = si.WORKLOADS[WORKLOAD]
     spec, k = cfg["spec"], cfg["k"]
-    if args.scale > 1:  # smaller copy of the workload, for profiler captures only
-        spec = si.scaled(spec, args.scale)
+    if args.scale > 1 or args.levels:  # smaller copy of the workload, for profiler captures only
+        spec = si.scaled(spec, args.scale, args.levels or None)
     seed = si.BASE_SEED + rank
     w_np = si.channel_w(spec, k, seed=seed)
     xs_np = si.reference_solution(spec, k, seed=seed + 1)
@@ -479,7 +479,7 @@ def main():
         return
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -491,6 +491,9 @@ def main():
                          "profiler runs")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the finest mesh by this factor (small cases for profiler captures)")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="with --scale: number of levels of the smaller copy (e.g. --scale 4 --levels 2 "
+                         "keeps the 88x16 coarse level)")
     args = ap.parse_args()
     if args.colour_variants:
         parts = args.colour_variants.split(";")
