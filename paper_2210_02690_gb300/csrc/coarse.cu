@@ -469,6 +469,37 @@ __global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, T alpha, const
   if (lane == 0) y[row] = alpha * acc + (beta == (T)0 ? (T)0 : beta * y[row]);
 }
 
+// y = alpha (A0 x0 + A1 x1) + c + beta y, batched, one warp per row; a null A0/A1 (per item)
+// drops its term, a null c array drops c.  A0 is M x N0, A1 is M x N1, both row-major.
+template <typename T>
+__global__ void __launch_bounds__(256) bgemv2_kernel(int M, int N0, int N1, T alpha, const T* const* A0s,
+                                                     const T* const* x0s, const T* const* A1s,
+                                                     const T* const* x1s, const T* const* cs, T beta,
+                                                     T* const* ys) {
+  const int b = blockIdx.y;
+  const int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (row >= M) return;
+  const T* A0 = A0s ? A0s[b] : nullptr;
+  const T* A1 = A1s ? A1s[b] : nullptr;
+  T acc = 0;
+  if (A0) {
+    const T* x = x0s[b];
+    for (int c = lane; c < N0; c += 32) acc += A0[(long long)row * N0 + c] * x[c];
+  }
+  if (A1) {
+    const T* x = x1s[b];
+    for (int c = lane; c < N1; c += 32) acc += A1[(long long)row * N1 + c] * x[c];
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) {
+    T* y = ys[b];
+    T val = alpha * acc;
+    if (cs) val += cs[b][row];
+    if (beta != (T)0) val += beta * y[row];
+    y[row] = val;
+  }
+}
+
 template <typename T>
 __global__ void copy_kernel(long long n, const T* __restrict__ a, T* __restrict__ b) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -852,6 +883,34 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
     lv.bGU = upload_ptrs(bGU, owned);
     lv.bxr = upload_ptrs(bxr, owned);
     lv.bx2 = upload_ptrs(bx2, owned);
+    // fused lists (the products of the separate left/right lists, item by item)
+    std::vector<T*> eA0, ex0, eA1, ex1, ey, qA1, qx1;
+    {
+      int ql = 0, qr = 0;
+      for (long long j = 0; j < nsv; j += 2 * st_) {
+        const bool has_l = j - st_ >= 0, has_r = j + st_ < nsv;
+        if (!has_l && !has_r) continue;
+        eA0.push_back(has_l ? sL[ql] : nullptr);
+        ex0.push_back(has_l ? tV + (j - st_) * mV : nullptr);
+        eA1.push_back(has_r ? sU[qr] : nullptr);
+        ex1.push_back(has_r ? tV + (j + st_) * mV : nullptr);
+        ey.push_back(bV + j * mV);
+        ql += has_l ? 1 : 0;
+        qr += has_r ? 1 : 0;
+      }
+      for (long long i = st_; i < nsv; i += 2 * st_) {
+        qA1.push_back(i + st_ < nsv ? blk(GU, i) : nullptr);
+        qx1.push_back(i + st_ < nsv ? xV + (i + st_) * mV : nullptr);
+      }
+    }
+    lv.n_even = (int)ey.size();
+    lv.eA0 = upload_ptrs(eA0, owned);
+    lv.ex0 = upload_ptrs(ex0, owned);
+    lv.eA1 = upload_ptrs(eA1, owned);
+    lv.ex1 = upload_ptrs(ex1, owned);
+    lv.ey = upload_ptrs(ey, owned);
+    lv.qA1 = upload_ptrs(qA1, owned);
+    lv.qx1 = upload_ptrs(qx1, owned);
     levels.push_back(lv);
   }
   std::vector<T*> top{v.D}, topb{bV}, topx{xV};
@@ -954,6 +1013,15 @@ static void gemv(int M, int N, T alpha, const T* const* A, int lda, const T* con
 }
 
 template <typename T>
+static void gemv2(int M, int N0, int N1, T alpha, const T* const* A0, const T* const* x0, const T* const* A1,
+                  const T* const* x1, const T* const* c, T beta, T* const* y, int batch, cudaStream_t st) {
+  if (batch <= 0) return;
+  dim3 grid((M + 7) / 8, batch);
+  bgemv2_kernel<T><<<grid, 256, 0, st>>>(M, N0, N1, alpha, A0, x0, A1, x1, c, beta, y);
+  STG_LAUNCH_OK();
+}
+
+template <typename T>
 void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double* vv, const double* vp,
                              const double* pv, cudaStream_t st) {
   const Geom& g = v.g;
@@ -1016,21 +1084,18 @@ void CoarseSolver<T>::solve(const double* b, double* x, cudaStream_t st) {
   STG_LAUNCH_OK();
   const int m = (int)mV;
   for (const auto& lv : levels) {
+    // t_i = D_i^{-1} b_i (odd planes), then b_j -= L_j t_{j-st} + U_j t_{j+st} in one launch
     gemv<T>(m, m, one, lv.oD, m, lv.ob, zero, lv.ot, lv.n_odd, st);
-    gemv<T>(m, m, mone, lv.sL, m, lv.lt, one, lv.lb, lv.n_left, st);
-    gemv<T>(m, m, mone, lv.sU, m, lv.rt, one, lv.rb, lv.n_right, st);
+    gemv2<T>(m, m, m, mone, lv.eA0, lv.ex0, lv.eA1, lv.ex1, nullptr, one, lv.ey, lv.n_even, st);
   }
   gemv<T>(m, m, one, d_top, m, d_topb, zero, d_topx, 1, st);
   for (auto it = levels.rbegin(); it != levels.rend(); ++it) {
     const auto& lv = *it;
-    copy_ptrs<T>(lv.bt, lv.bx, lv.n_odd, mV, st);
-    gemv<T>(m, m, mone, lv.bGL, m, lv.bxl, one, lv.bx, lv.n_odd, st);
-    gemv<T>(m, m, mone, lv.bGU, m, lv.bxr, one, lv.bx2, lv.n_bright, st);
+    // x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}
+    gemv2<T>(m, m, m, mone, lv.bGL, lv.bxl, lv.qA1, lv.qx1, lv.bt, zero, lv.bx, lv.n_odd, st);
   }
   // x_I = g_I - W [x_V,s ; x_V,s+1]
-  copy_kernel<T><<<grid_for(nsi * mI, 256), 256, 0, st>>>(nsi * mI, gI, xI);
-  STG_LAUNCH_OK();
-  gemv<T>((int)mI, (int)(2 * mV), mone, d_W, (int)(2 * mV), d_xVs, one, d_xI, (int)nsi, st);
+  gemv2<T>((int)mI, (int)(2 * mV), 0, mone, d_W, d_xVs, nullptr, nullptr, d_gI, zero, d_xI, (int)nsi, st);
   scatter_sol<T><<<grid_for(g.N, 256), 256, 0, st>>>(v, xV, xI, x);
   STG_LAUNCH_OK();
 }

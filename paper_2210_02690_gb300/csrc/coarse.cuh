@@ -24,6 +24,11 @@ struct CrLevel {
   T **lD, **lL, **lGU, **lGL, **lT, **lb, **lt, **sL;
   T **rD, **rU, **rGL, **rGU, **rT, **rb, **rt, **sU;
   T **bx, **bt, **bGL, **bxl, **bGU, **bxr, **bx2;
+  // fused solve lists: even planes with a neighbour (b_j -= L_j t_{j-st} + U_j t_{j+st}) and odd
+  // planes (x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}); absent terms are null pointers
+  int n_even;
+  T **eA0, **ex0, **eA1, **ex1, **ey;
+  T **qA1, **qx1;
 };
 
 template <typename T>
