@@ -23,9 +23,6 @@
 
 namespace stg {
 
-template <typename T>
-void copy_ptrs(T* const* src, T* const* dst, int batch, long long n, cudaStream_t st);
-
 namespace {
 
 // ---------------------------------------------------------------- batched dense kernels
@@ -415,45 +412,6 @@ __global__ void __launch_bounds__(32 * NW, 1) rgj_kernel(int m, float* const* As
 #undef RGJ_SET
 }
 
-// C = alpha A B + beta C, row-major, batched through pointer arrays; 32x32 tiles.
-template <typename T>
-__global__ void __launch_bounds__(256) bgemm_kernel(int M, int N, int K, T alpha, const T* const* As, int lda,
-                                                    const T* const* Bs, int ldb, T beta, T* const* Cs, int ldc) {
-  const T* A = As[blockIdx.z];
-  const T* B = Bs[blockIdx.z];
-  T* C = Cs[blockIdx.z];
-  __shared__ T sa[32][33], sb[32][33];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  T acc[2][2] = {{0, 0}, {0, 0}};
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int t = threadIdx.x; t < 32 * 32; t += 256) {
-      const int i = t / 32, kk = t % 32;
-      sa[i][kk] = (r0 + i < M && k0 + kk < K) ? A[(long long)(r0 + i) * lda + k0 + kk] : (T)0;
-      sb[i][kk] = (k0 + i < K && c0 + kk < N) ? B[(long long)(k0 + i) * ldb + c0 + kk] : (T)0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const T a0 = sa[ty * 2][kk], a1 = sa[ty * 2 + 1][kk];
-      const T b0 = sb[kk][tx * 2], b1 = sb[kk][tx * 2 + 1];
-      acc[0][0] += a0 * b0;
-      acc[0][1] += a0 * b1;
-      acc[1][0] += a1 * b0;
-      acc[1][1] += a1 * b1;
-    }
-    __syncthreads();
-  }
-  for (int u = 0; u < 2; ++u)
-    for (int v = 0; v < 2; ++v) {
-      const int r = r0 + ty * 2 + u, c = c0 + tx * 2 + v;
-      if (r < M && c < N) {
-        T* p = C + (long long)r * ldc + c;
-        *p = alpha * acc[u][v] + (beta == (T)0 ? (T)0 : beta * *p);
-      }
-    }
-}
-
 // y = alpha A x + beta y, batched; one warp per row.
 template <typename T>
 __global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, T alpha, const T* const* As, int lda,
@@ -467,6 +425,67 @@ __global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, T alpha, const
   for (int c = lane; c < N; c += 32) acc += A[(long long)row * lda + c] * x[c];
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
   if (lane == 0) y[row] = alpha * acc + (beta == (T)0 ? (T)0 : beta * y[row]);
+}
+
+// C = alpha (A0 B0 + A1 B1) + beta C, batched through pointer arrays, row-major (A: M x K, B:
+// K x N, C: M x N); a null A0/A1 (per item) drops its product.  64 x 64 tiles, 16-deep k slices
+// staged in shared memory, 4 x 4 outputs per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) bgemm2_kernel(int M, int N, int K, T alpha, const T* const* A0s,
+                                                     const T* const* B0s, const T* const* A1s,
+                                                     const T* const* B1s, T beta, T* const* Cs) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ __align__(16) T sa[BK][BM + 4];
+  __shared__ __align__(16) T sb[BK][BN + 4];
+  const int b = blockIdx.z, tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int pr = 0; pr < 2; ++pr) {
+    const T* const* As = pr == 0 ? A0s : A1s;
+    const T* const* Bs = pr == 0 ? B0s : B1s;
+    const T* A = As ? As[b] : nullptr;
+    if (!A) continue;  // the same for the whole CTA
+    const T* B = Bs[b];
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int t = tid; t < BM * BK; t += 256) {
+        const int i = t / BK, kk = t % BK, r = r0 + i, k = k0 + kk;
+        sa[kk][i] = (r < M && k < K) ? A[(long long)r * K + k] : (T)0;
+      }
+      for (int t = tid; t < BK * BN; t += 256) {
+        const int kk = t / BN, j = t % BN, k = k0 + kk, c = c0 + j;
+        sb[kk][j] = (k < K && c < N) ? B[(long long)k * N + c] : (T)0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = sa[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = sb[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+      }
+      __syncthreads();
+    }
+  }
+  T* C = Cs[b];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (r < M && c < N) {
+        T* p = C + (long long)r * N + c;
+        *p = alpha * acc[i][j] + (beta == (T)0 ? (T)0 : beta * *p);
+      }
+    }
 }
 
 // y = alpha (A0 x0 + A1 x1) + c + beta y, batched, one warp per row; a null A0/A1 (per item)
@@ -740,7 +759,6 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   alloc(&v.U, nsv * mV * mV);
   alloc(&GL, nsv * mV * mV);
   alloc(&GU, nsv * mV * mV);
-  alloc(&TL, nsv * mV * mV);
   alloc(&bV, nsv * mV);
   {
     const long long nb = std::max(nsi, nsv), mm = std::max(mI, mV);
@@ -786,132 +804,110 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   d_xVs = upload_ptrs(pxVs, owned);
   d_xI = upload_ptrs(pxI, owned);
 
-  // cyclic-reduction schedule over the nsv vertex planes
+  // cyclic-reduction schedule over the nsv vertex planes.  curL/curU: the block each plane's L/U
+  // currently lives in (level 0: the extracted blocks; later levels: the previous level's output)
   levels.clear();
   auto blk = [&](T* base, long long i) { return base + i * mV * mV; };
+  std::vector<T*> curL(nsv), curU(nsv);
+  for (long long j = 0; j < nsv; ++j) {
+    curL[j] = blk(v.L, j);
+    curU[j] = blk(v.U, j);
+  }
   for (long long st_ = 1; st_ < nsv; st_ *= 2) {
-    CrLevel<T> lv;
+    CrLevel<T> lv{};
     lv.stride = st_;
-    std::vector<T*> oD, oL, oU, oGL, oGU, ob, ot;
+    // odd planes: D_i^{-1} (in place), GL_i, GU_i; forward t_i = D_i^{-1} b_i
+    std::vector<T*> oD, ob, ot, gA, gB, gC;
     for (long long i = st_; i < nsv; i += 2 * st_) {
       oD.push_back(blk(v.D, i));
-      oL.push_back(blk(v.L, i));
-      oU.push_back(blk(v.U, i));
-      oGL.push_back(blk(GL, i));
-      oGU.push_back(blk(GU, i));
       ob.push_back(bV + i * mV);
       ot.push_back(tV + i * mV);
     }
     lv.n_odd = (int)oD.size();
+    for (int pass = 0; pass < 2; ++pass)
+      for (long long i = st_; i < nsv; i += 2 * st_) {
+        gA.push_back(blk(v.D, i));
+        gB.push_back(pass == 0 ? curL[i] : curU[i]);
+        gC.push_back(blk(pass == 0 ? GL : GU, i));
+      }
     lv.oD = upload_ptrs(oD, owned);
-    lv.oL = upload_ptrs(oL, owned);
-    lv.oU = upload_ptrs(oU, owned);
-    lv.oGL = upload_ptrs(oGL, owned);
-    lv.oGU = upload_ptrs(oGU, owned);
     lv.ob = upload_ptrs(ob, owned);
     lv.ot = upload_ptrs(ot, owned);
-    // even j with a left neighbour j - st (always odd) and/or a right neighbour j + st
-    std::vector<T*> lD, lL, lGU, lGL, lT, lb, lt;
-    std::vector<T*> rD, rU, rGL, rGU, rT, rb, rt;
+    lv.gA = upload_ptrs(gA, owned);
+    lv.gB = upload_ptrs(gB, owned);
+    lv.gC = upload_ptrs(gC, owned);
+    // even planes with a neighbour: D update and the forward right-hand-side update share the
+    // products' left factors (this level's L_j, U_j); new L/U blocks for the next level
+    std::vector<T*> eA0, ex0, eA1, ex1, ey, dB0, dB1, dC, uA, uB, uC;
+    std::vector<T*> newL(curL), newU(curU);
+    int n_left = 0, n_right = 0;
+    std::vector<T*> uAr, uBr, uCr;
     for (long long j = 0; j < nsv; j += 2 * st_) {
-      if (j - st_ >= 0) {
-        lD.push_back(blk(v.D, j));
-        lL.push_back(blk(v.L, j));
-        lGU.push_back(blk(GU, j - st_));
-        lGL.push_back(blk(GL, j - st_));
-        lT.push_back(blk(TL, j));
-        lb.push_back(bV + j * mV);
-        lt.push_back(tV + (j - st_) * mV);
+      const bool has_l = j - st_ >= 0, has_r = j + st_ < nsv;
+      if (!has_l && !has_r) continue;
+      eA0.push_back(has_l ? curL[j] : nullptr);
+      ex0.push_back(has_l ? tV + (j - st_) * mV : nullptr);
+      dB0.push_back(has_l ? blk(GU, j - st_) : nullptr);
+      eA1.push_back(has_r ? curU[j] : nullptr);
+      ex1.push_back(has_r ? tV + (j + st_) * mV : nullptr);
+      dB1.push_back(has_r ? blk(GL, j + st_) : nullptr);
+      ey.push_back(bV + j * mV);
+      dC.push_back(blk(v.D, j));
+      if (has_l) {
+        T* p = nullptr;
+        alloc(&p, mV * mV);
+        uA.push_back(curL[j]);
+        uB.push_back(blk(GL, j - st_));
+        uC.push_back(p);
+        newL[j] = p;
+        ++n_left;
       }
-      if (j + st_ < nsv) {
-        rD.push_back(blk(v.D, j));
-        rU.push_back(blk(v.U, j));
-        rGL.push_back(blk(GL, j + st_));
-        rGU.push_back(blk(GU, j + st_));
-        rT.push_back(blk(TL, j));
-        rb.push_back(bV + j * mV);
-        rt.push_back(tV + (j + st_) * mV);
-      }
-    }
-    lv.n_left = (int)lD.size();
-    lv.n_right = (int)rD.size();
-    std::vector<T*> sL, sU;
-    for (int q = 0; q < lv.n_left; ++q) {
-      T* p = nullptr;
-      alloc(&p, mV * mV);
-      sL.push_back(p);
-    }
-    for (int q = 0; q < lv.n_right; ++q) {
-      T* p = nullptr;
-      alloc(&p, mV * mV);
-      sU.push_back(p);
-    }
-    lv.sL = upload_ptrs(sL, owned);
-    lv.sU = upload_ptrs(sU, owned);
-    lv.lD = upload_ptrs(lD, owned);
-    lv.lL = upload_ptrs(lL, owned);
-    lv.lGU = upload_ptrs(lGU, owned);
-    lv.lGL = upload_ptrs(lGL, owned);
-    lv.lT = upload_ptrs(lT, owned);
-    lv.lb = upload_ptrs(lb, owned);
-    lv.lt = upload_ptrs(lt, owned);
-    lv.rD = upload_ptrs(rD, owned);
-    lv.rU = upload_ptrs(rU, owned);
-    lv.rGL = upload_ptrs(rGL, owned);
-    lv.rGU = upload_ptrs(rGU, owned);
-    lv.rT = upload_ptrs(rT, owned);
-    lv.rb = upload_ptrs(rb, owned);
-    lv.rt = upload_ptrs(rt, owned);
-    // back substitution of the odd blocks: x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}
-    std::vector<T*> bx, bGL, bxl, bGU, bxr, bx2, bt;
-    for (long long i = st_; i < nsv; i += 2 * st_) {
-      bx.push_back(xV + i * mV);
-      bt.push_back(tV + i * mV);
-      bGL.push_back(blk(GL, i));
-      bxl.push_back(xV + (i - st_) * mV);
-      if (i + st_ < nsv) {
-        bGU.push_back(blk(GU, i));
-        bxr.push_back(xV + (i + st_) * mV);
-        bx2.push_back(xV + i * mV);
+      if (has_r) {
+        T* p = nullptr;
+        alloc(&p, mV * mV);
+        uAr.push_back(curU[j]);
+        uBr.push_back(blk(GU, j + st_));
+        uCr.push_back(p);
+        newU[j] = p;
+        ++n_right;
       }
     }
-    lv.bx = upload_ptrs(bx, owned);
-    lv.bt = upload_ptrs(bt, owned);
-    lv.bGL = upload_ptrs(bGL, owned);
-    lv.bxl = upload_ptrs(bxl, owned);
-    lv.n_bright = (int)bGU.size();
-    lv.bGU = upload_ptrs(bGU, owned);
-    lv.bxr = upload_ptrs(bxr, owned);
-    lv.bx2 = upload_ptrs(bx2, owned);
-    // fused lists (the products of the separate left/right lists, item by item)
-    std::vector<T*> eA0, ex0, eA1, ex1, ey, qA1, qx1;
-    {
-      int ql = 0, qr = 0;
-      for (long long j = 0; j < nsv; j += 2 * st_) {
-        const bool has_l = j - st_ >= 0, has_r = j + st_ < nsv;
-        if (!has_l && !has_r) continue;
-        eA0.push_back(has_l ? sL[ql] : nullptr);
-        ex0.push_back(has_l ? tV + (j - st_) * mV : nullptr);
-        eA1.push_back(has_r ? sU[qr] : nullptr);
-        ex1.push_back(has_r ? tV + (j + st_) * mV : nullptr);
-        ey.push_back(bV + j * mV);
-        ql += has_l ? 1 : 0;
-        qr += has_r ? 1 : 0;
-      }
-      for (long long i = st_; i < nsv; i += 2 * st_) {
-        qA1.push_back(i + st_ < nsv ? blk(GU, i) : nullptr);
-        qx1.push_back(i + st_ < nsv ? xV + (i + st_) * mV : nullptr);
-      }
-    }
+    uA.insert(uA.end(), uAr.begin(), uAr.end());
+    uB.insert(uB.end(), uBr.begin(), uBr.end());
+    uC.insert(uC.end(), uCr.begin(), uCr.end());
+    lv.n_left = n_left;
+    lv.n_right = n_right;
     lv.n_even = (int)ey.size();
     lv.eA0 = upload_ptrs(eA0, owned);
     lv.ex0 = upload_ptrs(ex0, owned);
     lv.eA1 = upload_ptrs(eA1, owned);
     lv.ex1 = upload_ptrs(ex1, owned);
     lv.ey = upload_ptrs(ey, owned);
+    lv.dB0 = upload_ptrs(dB0, owned);
+    lv.dB1 = upload_ptrs(dB1, owned);
+    lv.dC = upload_ptrs(dC, owned);
+    lv.uA = upload_ptrs(uA, owned);
+    lv.uB = upload_ptrs(uB, owned);
+    lv.uC = upload_ptrs(uC, owned);
+    // back substitution of the odd planes: x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}
+    std::vector<T*> bx, bt, bGL, bxl, qA1, qx1;
+    for (long long i = st_; i < nsv; i += 2 * st_) {
+      bx.push_back(xV + i * mV);
+      bt.push_back(tV + i * mV);
+      bGL.push_back(blk(GL, i));
+      bxl.push_back(xV + (i - st_) * mV);
+      qA1.push_back(i + st_ < nsv ? blk(GU, i) : nullptr);
+      qx1.push_back(i + st_ < nsv ? xV + (i + st_) * mV : nullptr);
+    }
+    lv.bx = upload_ptrs(bx, owned);
+    lv.bt = upload_ptrs(bt, owned);
+    lv.bGL = upload_ptrs(bGL, owned);
+    lv.bxl = upload_ptrs(bxl, owned);
     lv.qA1 = upload_ptrs(qA1, owned);
     lv.qx1 = upload_ptrs(qx1, owned);
     levels.push_back(lv);
+    curL.swap(newL);
+    curU.swap(newU);
   }
   std::vector<T*> top{v.D}, topb{bV}, topx{xV};
   d_top = upload_ptrs(top, owned);
@@ -995,20 +991,20 @@ static void gj(int m, T* const* A, int batch, int* status, T* scratch, int* perm
 }
 
 template <typename T>
-static void gemm(int M, int N, int K, T alpha, const T* const* A, int lda, const T* const* B, int ldb, T beta,
-                 T* const* C, int ldc, int batch, cudaStream_t st) {
-  if (batch <= 0) return;
-  dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
-  bgemm_kernel<T><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  STG_LAUNCH_OK();
-}
-
-template <typename T>
 static void gemv(int M, int N, T alpha, const T* const* A, int lda, const T* const* x, T beta, T* const* y,
                  int batch, cudaStream_t st) {
   if (batch <= 0) return;
   dim3 grid((M + 7) / 8, batch);
   bgemv_kernel<T><<<grid, 256, 0, st>>>(M, N, alpha, A, lda, x, beta, y);
+  STG_LAUNCH_OK();
+}
+
+template <typename T>
+static void gemm2(int M, int N, int K, T alpha, const T* const* A0, const T* const* B0, const T* const* A1,
+                  const T* const* B1, T beta, T* const* C, int batch, cudaStream_t st) {
+  if (batch <= 0) return;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  bgemm2_kernel<T><<<grid, 256, 0, st>>>(M, N, K, alpha, A0, B0, A1, B1, beta, C);
   STG_LAUNCH_OK();
 }
 
@@ -1043,29 +1039,20 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
   // interiors: A_II^{-1}, W = A_II^{-1} A_IV, C = A_VI W, S = A_VV - C (scattered)
   gj<T>((int)mI, d_AII, (int)nsi, v.status, gj_scr, gj_perm, gj_fail, st);
   const T one = 1, zero = 0, mone = -1;
-  gemm<T>((int)mI, (int)(2 * mV), (int)mI, one, d_AII, (int)mI, d_AIV, (int)(2 * mV), zero, d_W, (int)(2 * mV),
-          (int)nsi, st);
-  gemm<T>((int)(2 * mV), (int)(2 * mV), (int)mI, one, d_AVI, (int)mI, d_W, (int)(2 * mV), zero, d_C, (int)(2 * mV),
-          (int)nsi, st);
+  gemm2<T>((int)mI, (int)(2 * mV), (int)mI, one, d_AII, d_AIV, nullptr, nullptr, zero, d_W, (int)nsi, st);
+  gemm2<T>((int)(2 * mV), (int)(2 * mV), (int)mI, one, d_AVI, d_W, nullptr, nullptr, zero, d_C, (int)nsi, st);
   schur_combine<T><<<grid_for(nsv * mV * mV, 256), 256, 0, st>>>(v, C);
   STG_LAUNCH_OK();
   // block cyclic reduction of the vertex-plane system
   const int m = (int)mV;
   for (const auto& lv : levels) {
     gj<T>(m, lv.oD, lv.n_odd, v.status, gj_scr, gj_perm, gj_fail, st);
-    gemm<T>(m, m, m, one, lv.oD, m, lv.oL, m, zero, lv.oGL, m, lv.n_odd, st);
-    gemm<T>(m, m, m, one, lv.oD, m, lv.oU, m, zero, lv.oGU, m, lv.n_odd, st);
+    // [GL_i | GU_i] = D_i^{-1} [L_i | U_i]
+    gemm2<T>(m, m, m, one, lv.gA, lv.gB, nullptr, nullptr, zero, lv.gC, 2 * lv.n_odd, st);
     // D_j -= L_j GU_{j-st} + U_j GL_{j+st}
-    gemm<T>(m, m, m, mone, lv.lL, m, lv.lGU, m, one, lv.lD, m, lv.n_left, st);
-    gemm<T>(m, m, m, mone, lv.rU, m, lv.rGL, m, one, lv.rD, m, lv.n_right, st);
-    // L_j <- -L_j GL_{j-st}; U_j <- -U_j GU_{j+st} (through TL)
-    // the solve needs this level's L_j, U_j: keep copies before they are replaced
-    copy_ptrs<T>(lv.lL, lv.sL, lv.n_left, (long long)m * m, st);
-    copy_ptrs<T>(lv.rU, lv.sU, lv.n_right, (long long)m * m, st);
-    gemm<T>(m, m, m, mone, lv.lL, m, lv.lGL, m, zero, lv.lT, m, lv.n_left, st);
-    copy_ptrs<T>(lv.lT, lv.lL, lv.n_left, (long long)m * m, st);
-    gemm<T>(m, m, m, mone, lv.rU, m, lv.rGU, m, zero, lv.rT, m, lv.n_right, st);
-    copy_ptrs<T>(lv.rT, lv.rU, lv.n_right, (long long)m * m, st);
+    gemm2<T>(m, m, m, mone, lv.eA0, lv.dB0, lv.eA1, lv.dB1, one, lv.dC, lv.n_even, st);
+    // L_j <- -L_j GL_{j-st}, U_j <- -U_j GU_{j+st}, into new blocks
+    gemm2<T>(m, m, m, mone, lv.uA, lv.uB, nullptr, nullptr, zero, lv.uC, lv.n_left + lv.n_right, st);
   }
   gj<T>(m, d_top, 1, v.status, gj_scr, gj_perm, gj_fail, st);
 }
@@ -1107,24 +1094,6 @@ int CoarseSolver<T>::read_status(cudaStream_t st) {
   STG_CUDA_OK(cudaStreamSynchronize(st));
   if (h[1]) return -1;
   return h[0];
-}
-
-namespace {
-template <typename T>
-__global__ void copy_ptrs_kernel(const T* const* src, T* const* dst, long long n) {
-  const T* s = src[blockIdx.y];
-  T* d = dst[blockIdx.y];
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    d[t] = s[t];
-}
-}  // namespace
-
-template <typename T>
-void copy_ptrs(T* const* src, T* const* dst, int batch, long long n, cudaStream_t st) {
-  if (batch <= 0) return;
-  dim3 grid((unsigned)((n + 255) / 256 < 64 ? (n + 255) / 256 : 64), batch);
-  copy_ptrs_kernel<T><<<grid, 256, 0, st>>>(src, dst, n);
-  STG_LAUNCH_OK();
 }
 
 template struct CoarseSolver<double>;

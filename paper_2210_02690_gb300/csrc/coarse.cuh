@@ -19,22 +19,24 @@ struct CoarseView {
 template <typename T>
 struct CrLevel {
   long long stride;
-  int n_odd, n_left, n_right, n_bright;
-  T **oD, **oL, **oU, **oGL, **oGU, **ob, **ot;
-  T **lD, **lL, **lGU, **lGL, **lT, **lb, **lt, **sL;
-  T **rD, **rU, **rGL, **rGU, **rT, **rb, **rt, **sU;
-  T **bx, **bt, **bGL, **bxl, **bGU, **bxr, **bx2;
+  int n_odd, n_left, n_right;
+  T **oD, **ob, **ot;
+  T **bx, **bt, **bGL, **bxl;
   // fused solve lists: even planes with a neighbour (b_j -= L_j t_{j-st} + U_j t_{j+st}) and odd
   // planes (x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}); absent terms are null pointers
   int n_even;
   T **eA0, **ex0, **eA1, **ex1, **ey;
   T **qA1, **qx1;
+  // factorisation lists: [GL_i | GU_i] = D_i^{-1} [L_i | U_i] (2 n_odd items); D_j -= L_j GU_{j-st}
+  // + U_j GL_{j+st} (n_even items, A = eA0 / eA1); new L_j = -L_j GL_{j-st}, new U_j = -U_j GU_{j+st}
+  // (n_left + n_right items, written to this level's own blocks: the solve keeps reading the old)
+  T **gA, **gB, **gC, **dB0, **dB1, **dC, **uA, **uB, **uC;
 };
 
 template <typename T>
 struct CoarseSolver {
   CoarseView<T> v{};
-  T *W = nullptr, *C = nullptr, *GL = nullptr, *GU = nullptr, *TL = nullptr;
+  T *W = nullptr, *C = nullptr, *GL = nullptr, *GU = nullptr;
   T *bV = nullptr, *tV = nullptr, *xV = nullptr, *bI = nullptr, *gI = nullptr, *cI = nullptr, *xI = nullptr;
   T **d_AII = nullptr, **d_AIV = nullptr, **d_AVI = nullptr, **d_W = nullptr, **d_C = nullptr;
   T **d_bI = nullptr, **d_gI = nullptr, **d_cI = nullptr, **d_xVs = nullptr, **d_xI = nullptr;
