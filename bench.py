@@ -109,6 +109,13 @@ class ClockSampler:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # the sampler's start-up (NVML initialisation) stays out of the timed region: wait for its
+        # first sample (at most 3 s)
+        t_end = time.perf_counter() + 3.0
+        while self.proc and time.perf_counter() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):

@@ -245,6 +245,12 @@ __global__ void diag_blocks(Geom g, TimeData td, AsmCoef cf, const double* __res
 // Nitsche terms, velocity-pressure blocks); w is not read.  WONLY = true: add the terms that
 // depend on w (convection, Newton) to the time-diagonal blocks of an operator that already
 // holds that part.
+// index of the unordered pair {a, b} of 1D Q2 nodes: (0,0) 0, (0,1) 1, (0,2) 2, (1,1) 3, (1,2) 4, (2,2) 5
+__device__ __forceinline__ int pair3(int a, int b) {
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
 template <int DIM, bool WONLY>
 __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeData td, AsmCoef cf,
                                                       const double* __restrict__ w, const int* __restrict__ rowptr,
@@ -262,10 +268,15 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
   __shared__ double wq[NTMAX][NQ][DIM];
   __shared__ double gw[NTMAX][NQ][DIM][DIM];
   __shared__ double cm[NTC][NL][NL];
-  __shared__ double nm[NTC][NL][NL][DIM][DIM];
-  __shared__ double uq[NTC][NQ][NL];             // w_a . grad phi_j at q
-  __shared__ double pq[DIM == 2 ? NQ : 1][DIM == 2 ? NL : 1];  // W_q |det| phi_i(q)
-  __shared__ double ppq[DIM == 2 ? NQ : 1][DIM == 2 ? NL * NL : 1];
+  // 2D sum factorisation (see below): 1D weighted products per Gauss point, contractions over
+  // one direction, and the Newton blocks per pair of 1D index pairs
+  constexpr int S2 = DIM == 2 ? 1 : 0;  // 3D: size-1 placeholders, indices scaled by S2
+  constexpr int N3 = DIM == 2 ? 3 : 1, N5 = DIM == 2 ? 5 : 1, N6 = DIM == 2 ? 6 : 1;
+  __shared__ double wll[2][N3][6];           // W_q L_a(q) L_b(q), per direction, pair (a, b)
+  __shared__ double wld[2][N3][3][3];        // W_q L_a(q) D_b(q), per direction
+  __shared__ double sfp[NTC][N5][3][6];      // P_f(q1; p2), f = w_x, g_xx, g_xy, g_yx, g_yy
+  __shared__ double sfq[NTC][N3][6];         // Q(q2; p1) for w_y
+  __shared__ double nmp[NTC][N6][6][DIM * DIM];
   __shared__ int slots[NL * NL];
 
   const int nt = g.nt, NV = g.NV;
@@ -287,11 +298,17 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
       for (int e = 0; e < DIM; ++e) dphi[q][i][e] = x[NQ * NL + t * DIM + e];
     }
     for (int q = threadIdx.x; q < NQ; q += blockDim.x) qwd[q] = x[NQ * NL * (1 + DIM) + q];
-    if (DIM == 2) {
-      for (int t = threadIdx.x; t < NQ * NL * NL; t += blockDim.x)
-        ppq[t / (NL * NL)][t % (NL * NL)] = x[NQ * NL * (1 + DIM) + NQ + t];
-      for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x)
-        pq[t / NL][t % NL] = x[NQ * NL * (1 + DIM) + t / NL] * x[t];
+    if (DIM == 2 && WONLY) {
+      // 1D tables of the tensor-product rule: direction d, Gauss point q, local 1D nodes a, b
+      for (int t = threadIdx.x; t < 2 * 3 * 6; t += blockDim.x) {
+        const int d = t / 18, q = (t / 6) % 3, pr = t % 6;
+        const int pa = pr < 3 ? 0 : (pr < 5 ? 1 : 2), pb = pr < 3 ? pr : (pr < 5 ? pr - 2 : 2);  // inverse of pair3
+        wll[d][q * S2][pr] = c_GW[q] * g.h[d] / 2.0 * c_L1[q][pa] * c_L1[q][pb];
+      }
+      for (int t = threadIdx.x; t < 2 * 27; t += blockDim.x) {
+        const int d = t / 27, q = (t / 9) % 3, a = (t / 3) % 3, b = t % 3;
+        wld[d][q * S2][a][b] = c_GW[q] * g.h[d] / 2.0 * c_L1[q][a] * (2.0 / g.h[d] * c_D1[q][b]);
+      }
     }
   }
   for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) {
@@ -315,37 +332,48 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
     }
     __syncthreads();
     if (DIM == 2) {
-      // u_j(q) = w_a(q) . grad phi_j(q)
-      for (int t = threadIdx.x; t < nt * NQ * NL; t += blockDim.x) {
-        const int a = t / (NQ * NL), q = (t / NL) % NQ, j = t % NL;
-        double u = 0.0;
-        for (int f = 0; f < DIM; ++f) u += wq[a][q][f] * dphi[q][j][f];
-        uq[a % NTC][q][j] = u;
+      // Sum factorisation over the tensor-product basis phi_i(q) = L_i1(q1) L_i2(q2) and the
+      // 3 x 3 Gauss rule W_q = W_q1 W_q2 (x fastest in i and q).  With the contraction over q2
+      //   P_f(q1; i2 j2) = sum_q2 W_q2 L_i2 L_j2 (q2) f(q1, q2),  f in {w_x, d_e w_c},
+      // and over q1 for w_y, Q(q2; i1 j1) = sum_q1 W_q1 L_i1 L_j1 (q1) w_y(q1, q2):
+      //   convection (w_a . grad phi_j, phi_i) = sum_q1 W L_i1 D^x_j1 (q1) P_wx(q1; i2 j2)
+      //                                          + sum_q2 W L_i2 D^y_j2 (q2) Q(q2; i1 j1),
+      //   Newton (phi_j d_e w_c, phi_i) = sum_q1 W L_i1 L_j1 (q1) P_{g_ce}(q1; i2 j2),
+      // the latter a function of the unordered pairs {i1, j1}, {i2, j2} only (6 x 6 values).
+      for (int t = threadIdx.x; t < nt * 5 * 3 * 6; t += blockDim.x) {
+        const int a = t / 90, f = (t / 18) % 5, q1 = (t / 6) % 3, pr = t % 6;
+        double sum = 0.0;
+        for (int q2 = 0; q2 < 3; ++q2) {
+          const int q = q1 + 3 * q2;
+          const double fv = f == 0 ? wq[a][q][0] : gw[a][q][(f - 1) / 2][(f - 1) % 2];
+          sum += wll[1][q2 * S2][pr] * fv;
+        }
+        sfp[a % NTC][f * S2][q1][pr] = sum;
+      }
+      for (int t = threadIdx.x; t < nt * 3 * 6; t += blockDim.x) {
+        const int a = t / 18, q2 = (t / 6) % 3, pr = t % 6;
+        double sum = 0.0;
+        for (int q1 = 0; q1 < 3; ++q1) sum += wll[0][q1 * S2][pr] * wq[a][q1 + 3 * q2][1];
+        sfq[a % NTC][q2 * S2][pr] = sum;
       }
       __syncthreads();
-      // convection (w_a . grad phi_j, phi_i) = sum_q W phi_i u_j; Newton phi_i phi_j d_e w_a,c (symmetric in i, j)
       for (int t = threadIdx.x; t < nt * NL * NL; t += blockDim.x) {
         const int a = t / (NL * NL), i = (t / NL) % NL, j = t % NL;
-        const double sa = cf.tau * td.w[a];
+        const int i1 = i % 3, i2 = i / 3, j1 = j % 3, j2 = j / 3;
         double conv = 0.0;
-        for (int q = 0; q < NQ; ++q) conv += pq[q][i] * uq[a % NTC][q][j];
-        cm[a % NTC][i][j] = sa * conv;
-        if (cf.newton && i <= j) {
-          double nw[DIM][DIM];
-          for (int c = 0; c < DIM; ++c)
-            for (int e = 0; e < DIM; ++e) nw[c][e] = 0.0;
-          for (int q = 0; q < NQ; ++q) {
-            const double pp = ppq[q][i * NL + j];
-            for (int c = 0; c < DIM; ++c)
-              for (int e = 0; e < DIM; ++e) nw[c][e] += pp * gw[a][q][c][e];
-          }
-          for (int c = 0; c < DIM; ++c)
-            for (int e = 0; e < DIM; ++e) {
-              nm[a % NTC][i][j][c][e] = sa * nw[c][e];
-              nm[a % NTC][j][i][c][e] = sa * nw[c][e];
-            }
-        }
+        for (int q = 0; q < 3; ++q)
+          conv += wld[0][q * S2][i1][j1] * sfp[a % NTC][0][q][pair3(i2, j2)] +
+                  wld[1][q * S2][i2][j2] * sfq[a % NTC][q * S2][pair3(i1, j1)];
+        cm[a % NTC][i][j] = cf.tau * td.w[a] * conv;
       }
+      if (cf.newton)
+        for (int t = threadIdx.x; t < nt * 36 * DIM * DIM; t += blockDim.x) {
+          const int a = t / (36 * DIM * DIM), p1 = (t / (6 * DIM * DIM)) % 6, p2 = (t / (DIM * DIM)) % 6;
+          const int ce = t % (DIM * DIM);
+          double sum = 0.0;
+          for (int q1 = 0; q1 < 3; ++q1) sum += wll[0][q1 * S2][p1] * sfp[a % NTC][(1 + ce) * S2][q1][p2];
+          nmp[a % NTC][p1 * S2][p2][ce] = cf.tau * td.w[a] * sum;
+        }
       __syncthreads();
     }
 
@@ -355,7 +383,7 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
       for (int t = threadIdx.x; t < nd; t += blockDim.x) {
         const int e = t % DIM, c = (t / DIM) % DIM, a = (t / (DIM * DIM)) % nt;
         const int j = (t / (DIM * DIM * nt)) % NL, i = t / (DIM * DIM * nt * NL);
-        double val = cf.newton ? nm[a % NTC][i][j][c][e] : 0.0;
+        double val = cf.newton ? nmp[a % NTC][pair3(i % 3, j % 3) * S2][pair3(i / 3, j / 3)][c * DIM + e] : 0.0;
         if (c == e) val += cm[a % NTC][i][j];
         const int r = a * DIM + c, sc = a * DIM + e;
         vv[(long long)slots[i * NL + j] * NV * NV + (long long)r * NV + sc] += val;
