@@ -229,7 +229,7 @@ def gpu_arm(args) -> None:
     per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
     results = {}
     main = None
-    for name in ("f32", "f64", "bf16"):
+    for name in args.forms:
         solver = Solver(spec, k, cfg["nu"], cfg["tau"], w, **opts, **forms[name])
         b = solver.apply_jacobian(torch.from_numpy(xs_np).cuda())
         x = torch.zeros_like(b)
@@ -346,14 +346,15 @@ def gpu_arm(args) -> None:
         "fgmres_iters": r32["iters"], "rel_res": r32["rel_res"], "setup_ms": r32["setup_ms"],
         "autotune": r32["autotune"],
         "time_to_tol_ms": r32["time_to_tol_ms"],
-        "f64_form": {k_: results["f64"][k_] for k_ in ("value", "ms_per_step", "iters", "setup_ms", "time_to_tol_ms",
-                                                        "rel_res", "autotune")},
-        "bf16_factor_form": {k_: results["bf16"][k_] for k_ in ("value", "ms_per_step", "iters", "setup_ms",
-                                                                 "time_to_tol_ms", "rel_res", "autotune")},
-        "speedup_time_to_tol_f32_vs_f64": results["f64"]["time_to_tol_ms"] / r32["time_to_tol_ms"],
-        "speedup_step_f32_vs_f64": results["f64"]["ms_per_step"] / r32["ms_per_step"],
         "roofline": roofline, "e2e": r32["e2e"], "gpu_launches": r32["gpu_launches"], "clocks": r32["clocks"],
     }
+    keys = ("value", "ms_per_step", "iters", "setup_ms", "time_to_tol_ms", "rel_res", "autotune")
+    if "f64" in results:
+        out["f64_form"] = {k_: results["f64"][k_] for k_ in keys}
+        out["speedup_time_to_tol_f32_vs_f64"] = results["f64"]["time_to_tol_ms"] / r32["time_to_tol_ms"]
+        out["speedup_step_f32_vs_f64"] = results["f64"]["ms_per_step"] / r32["ms_per_step"]
+    if "bf16" in results:
+        out["bf16_factor_form"] = {k_: results["bf16"][k_] for k_ in keys}
     if main:
         main.close()
     if world == 1 and not args.no_cpu_baseline:
@@ -496,6 +497,8 @@ def main():
                     help="skip the autotuner and set the colour-kernel variants of levels 1.. per form, "
                          "e.g. '11,11,11;4,4,4;11,11,11' (the 'variants' a plain run reports), for "
                          "profiler runs")
+    ap.add_argument("--forms", default="f32,f64,bf16",
+                    help="precision forms to time (f32, the headline, always runs; e.g. 'f32' for profiler runs)")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the finest mesh by this factor (small cases for profiler captures)")
     ap.add_argument("--levels", type=int, default=0,
@@ -506,6 +509,7 @@ def main():
         parts = args.colour_variants.split(";")
         args.colour_variants = {"f32": parts[0], "f64": parts[min(1, len(parts) - 1)],
                                 "bf16": parts[min(2, len(parts) - 1)]}
+    args.forms = ["f32"] + [f for f in args.forms.split(",") if f in ("f64", "bf16")]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

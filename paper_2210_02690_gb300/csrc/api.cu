@@ -299,18 +299,21 @@ void linearise_internal(stg_ctx* c) {
   STG_CUDA_OK(cudaEventRecord(c->fork, c->st));
   STG_CUDA_OK(cudaStreamWaitEvent(c->side, c->fork, 0));
   STG_CUDA_OK(cudaStreamWaitEvent(c->aux, c->fork, 0));
+  // FP32 copies of a level's operator for the FP32 V-cycle (Kronecker split where there is one)
+  auto to_f32 = [&](LevelBufs& L, cudaStream_t s) {
+    if (vc64(c)) return;
+    if (L.vv32) convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, s);
+    const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
+    convert(nvp, L.vp, L.vp32, s);
+    convert(nvp, L.pv, L.pv32, s);
+    if (L.mk32) kron_split(L.g, L.nnzb, L.vv, c->td, L.mk32, L.ak32, s);
+  };
   for (int i = 0; i < nl; ++i) {
     const int l = i == 0 ? nl - 1 : i - 1;
     LevelBufs& L = c->lv[l];
     cudaStream_t s = l == 0 ? c->side : (l == nl - 1 ? c->st : c->aux);
     assemble_level_w(L.g, c->td, cf, L.w, L.rowptr, L.asm_tab, L.vconst, L.vv, L.nnzb, s);
-    if (!vc64(c)) {
-      if (L.vv32) convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, s);
-      const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
-      convert(nvp, L.vp, L.vp32, s);
-      convert(nvp, L.pv, L.pv32, s);
-      if (L.mk32) kron_split(L.g, L.nnzb, L.vv, c->td, L.mk32, L.ak32, s);
-    }
+    to_f32(L, s);
     if (l == 0) {
       if (coarse64(c))
         c->coarse64.factor(L.rowptr, L.colidx, L.vv, L.vp, L.pv, s);
