@@ -82,19 +82,17 @@ struct TimeF {
 // FP64 dense blocks: M_ij = J[(as,0),(bs,0)] / T_{as,bs} for the largest off-diagonal |T_{as,bs}|.
 __global__ void kron_split_kernel(Geom g, long long nnzb, const double* __restrict__ vv, TimeData td, int as,
                                   int bs, float* __restrict__ Mk, float* __restrict__ Ak) {
-  // one thread per (slot, block row r = a d + c): consecutive threads read consecutive rows and
-  // write consecutive d-float pieces of Ahat
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int NV = g.NV, D = g.dim;
-  if (t >= nnzb * NV) return;
-  const long long slot = t / NV;
-  const int r = (int)(t - slot * NV), a = r / D, c = r % D;
+  const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nnzb) return;
+  const int NV = g.NV, D = g.dim, NT = g.nt;
   const double* blk = vv + slot * NV * NV;
   const double M = blk[(as * D) * NV + bs * D] / td.T[as][bs];
-  if (r == 0) Mk[slot] = (float)M;
-  const double* row = blk + (long long)r * NV + a * D;
-  float* A = Ak + slot * NV * D + (long long)r * D;  // [a][c][e] = (a D + c) D + e
-  for (int e = 0; e < D; ++e) A[e] = (float)(row[e] - (c == e ? td.T[a][a] * M : 0.0));
+  Mk[slot] = (float)M;
+  float* A = Ak + slot * NT * D * D;
+  for (int a = 0; a < NT; ++a)
+    for (int c = 0; c < D; ++c)
+      for (int e = 0; e < D; ++e)
+        A[(a * D + c) * D + e] = (float)(blk[(a * D + c) * NV + a * D + e] - (c == e ? td.T[a][a] * M : 0.0));
 }
 
 // b - J x (or J x) on the velocity rows of the FP32 level operators from the Kronecker split,
@@ -902,7 +900,7 @@ void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData&
         as = a;
         bs = b;
       }
-  kron_split_kernel<<<grid_for(nnzb * g.NV, 256), 256, 0, st>>>(g, nnzb, vv, td, as, bs, Mk, Ak);
+  kron_split_kernel<<<grid_for(nnzb, 256), 256, 0, st>>>(g, nnzb, vv, td, as, bs, Mk, Ak);
   STG_LAUNCH_OK();
 }
 
