@@ -8,6 +8,11 @@
 
 namespace stg {
 
+// In-place inverses of `batch` FP32 m x m row-major matrices (m <= 256) by the on-chip
+// Gauss-Jordan kernel; status gets 1 + the first singular matrix.  Returns false (nothing
+// launched) for larger m.
+bool rgj_invert(int m, float* const* A, int batch, int* status, cudaStream_t st);
+
 template <typename T>
 struct CoarseView {
   Geom g;
