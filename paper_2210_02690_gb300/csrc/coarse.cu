@@ -328,12 +328,6 @@ __global__ void __launch_bounds__(256) bgemv2_kernel(int M, int N0, int N1, T al
   }
 }
 
-template <typename T>
-__global__ void copy_kernel(long long n, const T* __restrict__ a, T* __restrict__ b) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = a[t];
-}
-
 // ---------------------------------------------------------------- DoF classification
 struct Cls {
   int type;  // 0 = vertex plane, 1 = interior slab
