@@ -172,9 +172,16 @@ def max_over_ranks(world, value: float) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    # NCCL reduces device tensors; a gloo group (the CPU tests of this path) host tensors
+    t = torch.tensor([value], dtype=torch.float64, device="cpu" if dist.get_backend() == "gloo" else "cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_rank_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every rank processed in `steps` steps, divided by the
+    slowest rank's time (ms)."""
+    return units_per_rank_step * steps * world / (ms_max * 1e-3)
 
 
 # DRAM bytes per patch (dram__bytes_read.sum + dram__bytes_write.sum, ncu) of the colour-kernel
@@ -271,7 +278,7 @@ def gpu_arm(args) -> None:
                "autotune": {"finest_variant": tuned[0], "finest_sweep_ms": tuned[1],
                             "variants": ",".join(str(v) for v in solver.colour_variants())},
                "time_to_tol_ms": e[1].elapsed_time(e[2]), "rel_res": rel_s, "clocks": clocks,
-               "value": per_cycle * its * steps * world / (ms_max * 1e-3)}
+               "value": aggregate_rate(per_cycle * its, steps, world, ms_max)}
         if name == "f32":
             pms, plaunch, ppatch = solver.profile_read()
             res["gpu_launches"] = launches1 - launches0
@@ -297,7 +304,7 @@ def gpu_arm(args) -> None:
             e1.record()
             torch.cuda.synchronize()
             e2e_ms = max_over_ranks(world, e0.elapsed_time(e1))
-            res["e2e"] = {"value": per_cycle * its * steps * world / (e2e_ms * 1e-3), "unit": UNIT,
+            res["e2e"] = {"value": aggregate_rate(per_cycle * its, steps, world, e2e_ms), "unit": UNIT,
                           "h2d_bytes_per_step": int(w_h.numel() * 8 + b_h.numel() * 8),
                           "d2h_bytes_per_step": int(x_h.numel() * 8),
                           "ms_per_step": e2e_ms / steps, "wall_s": time.perf_counter() - t0}
