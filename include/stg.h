@@ -23,8 +23,11 @@
  *     numbered lexicographically with x fastest, d+1 P1disc coefficients
  *     {1, xi_1, .., xi_d} per cell in the cell's reference coordinates).
  *     Internally the library permutes to its own layout.
- *   - All work is enqueued on the stream given to stg_setup; entry points that
- *     return scalars to the host synchronise that stream.
+ *   - All work is ordered on the stream given to stg_setup; entry points that
+ *     return scalars to the host synchronise that stream.  stg_setup and
+ *     stg_update_linearisation fork part of their work (the coarse factorisation,
+ *     the intermediate levels) onto two higher-priority streams the context owns
+ *     and join them back into the given stream before they return.
  *   - Errors are returned as a status; no call aborts.  stg_last_error gives a
  *     text.  The context stays usable after STG_ENOCONV and STG_ESINGULAR.
  *   - The context owns all device memory it allocates (freed by stg_destroy).
