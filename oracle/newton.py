@@ -86,8 +86,10 @@ def residual(lev, X: np.ndarray, b: np.ndarray, nu: float, tau: float) -> np.nda
 
 
 def newton_slab(spec, k, nu, tau, X0, b, rtol=1e-8, atol=0.0, maxit=20, gmres_rtol=1e-8, nu1=2, nu2=2,
-                lam_min=1.0 / 16.0):
-    """Damped Newton for F_n(X) = 0; returns (X, Newton steps, total GMRES iterations, ||F|| history)."""
+                lam_min=1.0 / 16.0, lambdas=None):
+    """Damped Newton for F_n(X) = 0; returns (X, Newton steps, total GMRES iterations, ||F|| history).
+
+    `lambdas`, if a list, receives the damping factor accepted at each step."""
     lev = mesh.Level(spec, spec.n_levels - 1, k)
     X = np.array(X0, dtype=float, copy=True)
     F = residual(lev, X, b, nu, tau)
@@ -108,5 +110,7 @@ def newton_slab(spec, k, nu, tau, X0, b, rtol=1e-8, atol=0.0, maxit=20, gmres_rt
             lam *= 0.5
         X, F = Xt, Ft
         hist.append(np.linalg.norm(F))
+        if lambdas is not None:
+            lambdas.append(lam)
         steps += 1
     return X, steps, its_total, hist
