@@ -21,6 +21,7 @@ the Navier-Stokes equations"):
 * ``multigrid``  -- the V-cycle with a direct coarse solve on T_0.
 * ``fgmres``     -- right-preconditioned flexible GMRES.
 * ``newton``     -- nonlinear slab residual F_n, damped Newton (Sec. 3).
+* ``functionals`` -- drag and lift on an obstacle (Sec. 4).
 * ``cnn``        -- the warm-start network (3x3 convolutions, tanh, MSE loss,
                     Adam) and the next-slab features, targets and guess; the
                     paper has no learned part, its pins are closed forms.
@@ -28,5 +29,5 @@ the Navier-Stokes equations"):
 Every part is pinned by the ``-m "not gpu"`` tests against closed forms,
 invariants and brute-force dense linear algebra.
 """
-from . import timebasis, element, mesh, assemble, vanka, transfer, multigrid, fgmres, newton, cnn  # noqa: F401
+from . import timebasis, element, mesh, assemble, vanka, transfer, multigrid, fgmres, newton, cnn, functionals  # noqa: F401
 from .multigrid import Hierarchy  # noqa: F401

@@ -69,9 +69,9 @@ class CellOperators:
         # Nitsche face terms per cell: velocity-velocity (ncells, i, c, j, e), pressure (ncells, i, c, m)
         vv = np.zeros((nc, nloc, d, nloc, d))
         vp = np.zeros((nc, nloc, d, d + 1))
-        for e, side, cells in lev.boundary_faces():
-            if not lev.is_dirichlet(e, side):
-                continue  # do-nothing face: natural condition of A_h, no boundary term
+        # Dirichlet faces: the domain's (a do-nothing face is the natural condition of A_h and
+        # carries no boundary term) and those of an obstacle
+        for e, side, cells in lev.dirichlet_faces():
             fp, fw = element.face_rule(d, e, side)
             fdet = np.prod(np.delete(h, e) / 2.0)
             fqw = fw * fdet
@@ -128,7 +128,23 @@ def element_matrices(lev, w: np.ndarray, nu: float, tau: float, newton: bool,
         # pressure rows, velocity columns: (div psi_j, xi_m) - <psi_j . n, xi_m>
         pv = ops.div[None] - np.transpose(ops.face_vp, (0, 3, 1, 2))        # (nc, m, j, e)
         out[:, pa, ra] += s * pv.reshape(nc, lev.Shat, lev.Rhat)
+    out[lev.masked] = 0.0            # cells removed by an obstacle carry no element matrices
     return out
+
+
+def dead_dofs(lev) -> np.ndarray:
+    """Unknowns without an equation in the obstacle domain: the velocity at Q2 nodes of removed
+    cells only and the pressure of removed cells, every Radau node (C-ABI numbers)."""
+    if not lev.masked.any():
+        return np.zeros(0, dtype=np.int64)
+    out = []
+    cells = np.nonzero(lev.masked)[0]
+    for a in range(lev.k + 1):
+        for c in range(lev.dim):
+            out.append(lev.vel_index(a, lev.dead_nodes, c))
+        for m in range(lev.dim + 1):
+            out.append(lev.pres_index(a, cells, m))
+    return np.sort(np.concatenate(out))
 
 
 def jacobian(lev, w: np.ndarray, nu: float, tau: float, newton: bool,
@@ -138,6 +154,9 @@ def jacobian(lev, w: np.ndarray, nu: float, tau: float, newton: bool,
     rows = np.broadcast_to(lev.dof[:, :, None], emat.shape).ravel()
     cols = np.broadcast_to(lev.dof[:, None, :], emat.shape).ravel()
     jac = sp.coo_matrix((emat.ravel(), (rows, cols)), shape=(lev.N, lev.N)).tocsr()
+    dead = dead_dofs(lev)
+    if len(dead):
+        jac = jac + sp.csr_matrix((np.ones(len(dead)), (dead, dead)), shape=(lev.N, lev.N))
     jac.sum_duplicates()
     jac.eliminate_zeros()
     return jac
@@ -150,12 +169,13 @@ def mass_matrix(lev) -> sp.csr_matrix:
     vals, _ = element.q2_basis(pts)
     me = np.einsum("q,qi,qj->ij", wts * np.prod(np.asarray(lev.h) / 2.0), vals, vals)
     rows, cols, data = [], [], []
+    cn = lev.cell_nodes[~lev.masked]                 # cells removed by an obstacle add nothing
     for c in range(d):
-        ri = lev.cell_nodes[:, :, None] * d + c
-        ci = lev.cell_nodes[:, None, :] * d + c
-        rows.append(np.broadcast_to(ri, (lev.n_cells,) + me.shape).ravel())
-        cols.append(np.broadcast_to(ci, (lev.n_cells,) + me.shape).ravel())
-        data.append(np.broadcast_to(me, (lev.n_cells,) + me.shape).ravel())
+        ri = cn[:, :, None] * d + c
+        ci = cn[:, None, :] * d + c
+        rows.append(np.broadcast_to(ri, (len(cn),) + me.shape).ravel())
+        cols.append(np.broadcast_to(ci, (len(cn),) + me.shape).ravel())
+        data.append(np.broadcast_to(me, (len(cn),) + me.shape).ravel())
     return sp.coo_matrix((np.concatenate(data), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(lev.R, lev.R)).tocsr()
 
@@ -184,11 +204,12 @@ def rhs_linear(lev, f, g, v_prev, nu: float, tau: float, t0: float = 0.0,
         xq = centres[:, None, :] + pts[None, :, :] * (h / 2.0)      # (nc, nq, d)
         fq = f(xq.reshape(-1, d), ta).reshape(lev.n_cells, -1, d)
         loc = np.einsum("q,qi,kqc->kic", qw * det, vals, fq)       # (nc, nloc, d)
+        loc[lev.masked] = 0.0
         vel = np.zeros((lev.n_nodes, d))
         np.add.at(vel, lev.cell_nodes, loc)
         pres = np.zeros((lev.n_cells, d + 1))
-        for e, side, cells in lev.boundary_faces():
-            if not lev.is_dirichlet(e, side) or g is None:
+        for e, side, cells in lev.dirichlet_faces():
+            if g is None:
                 continue
             fp, fw = element.face_rule(d, e, side)
             fqw = fw * np.prod(np.delete(h, e) / 2.0)

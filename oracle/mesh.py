@@ -44,6 +44,17 @@ class Level:
         self.dof = self._dof_map()
         # colour(K) = sum_i (c_i & 1) 2^i: cells of one colour share no Q2 node
         self.colour = np.sum((self.cell_idx & 1) << np.arange(self.dim), axis=1)
+        # cells removed by an obstacle (2D): they carry no element matrices; the Q2 nodes that
+        # belong to no remaining cell and the P1disc coefficients of removed cells are unknowns
+        # without an equation, fixed by identity rows
+        self.masked = np.zeros(self.n_cells, dtype=bool)
+        box = spec.obstacle_cells(level) if getattr(spec, "obstacle", ()) else ()
+        if box:
+            cx, cy = self.cell_idx[:, 0], self.cell_idx[:, 1]
+            self.masked = (cx >= box[0]) & (cx < box[1]) & (cy >= box[2]) & (cy < box[3])
+        fluid_count = np.zeros(self.n_nodes, dtype=np.int64)
+        np.add.at(fluid_count, self.cell_nodes[~self.masked].ravel(), 1)
+        self.dead_nodes = np.nonzero(fluid_count == 0)[0]
 
     def node_number(self, g: np.ndarray) -> np.ndarray:
         """Global number of Q2 node multi-indices g (..., dim), x fastest."""
@@ -82,6 +93,27 @@ class Level:
                 target = 0 if side == 0 else self.cells[e] - 1
                 faces.append((e, side, np.nonzero(self.cell_idx[:, e] == target)[0]))
         return faces
+
+    def dirichlet_faces(self):
+        """(direction, side, cell numbers) of every Dirichlet face of the fluid domain: the
+        domain's Dirichlet faces (cells not removed) and the faces of remaining cells whose
+        neighbour across that face is removed by the obstacle."""
+        out = []
+        for e, side, cells in self.boundary_faces():
+            if self.is_dirichlet(e, side):
+                out.append((e, side, cells[~self.masked[cells]]))
+        if self.masked.any():
+            stride = [1, self.cells[0], self.cells[0] * (self.cells[1] if self.dim > 1 else 1)]
+            for e in range(self.dim):
+                for side in (0, 1):
+                    step = 1 if side == 1 else -1
+                    nb = self.cell_idx[:, e] + step
+                    inside = (nb >= 0) & (nb < self.cells[e])
+                    nbcell = np.arange(self.n_cells) + step * stride[e]
+                    hit = inside & ~self.masked
+                    hit[hit] = self.masked[nbcell[hit]]
+                    out.append((e, side, np.nonzero(hit)[0]))
+        return [f for f in out if len(f[2])]
 
     def is_dirichlet(self, direction: int, side: int) -> bool:
         return bool(self.spec.dirichlet >> (2 * direction + side) & 1)

@@ -55,9 +55,7 @@ def rhs_nodal(lev, f_nodal, g_nodal, v_prev, nu: float, tau: float,
             gn = g_nodal[a].reshape(lev.n_nodes, d)
             vloc = np.zeros((lev.n_nodes, d))
             ploc = np.zeros((lev.n_cells, d + 1))
-            for e, side, cells in lev.boundary_faces():
-                if not lev.is_dirichlet(e, side):
-                    continue
+            for e, side, cells in lev.dirichlet_faces():
                 fp, fw = element.face_rule(d, e, side)
                 fqw = fw * np.prod(np.delete(h, e) / 2.0)
                 fv, fg = element.q2_basis(fp)

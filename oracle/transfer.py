@@ -6,7 +6,9 @@ Reading: the canonical ones of nested conforming spaces.  The prolongation P
 maps the coefficients of a coarse finite element function to the coefficients
 of the same function on the fine mesh (Q2: its values at the fine nodes;
 P1disc: its P1 expansion on each child cell); the restriction is P^T.  Time
-nodes are not coarsened: P acts identically on every Radau node block.
+nodes are not coarsened: P acts identically on every Radau node block.  With an
+obstacle the spaces are those of the fluid domain: P is zero on the fine unknowns
+outside it.
 """
 from __future__ import annotations
 
@@ -71,7 +73,18 @@ def prolongation(coarse, fine) -> sp.csr_matrix:
                        shape=(fine.S, coarse.S)).tocsr()
     pp.eliminate_zeros()
     blk = sp.block_diag([pv, pp], format="csr")
-    return sp.block_diag([blk] * (k + 1), format="csr")
+    out = sp.block_diag([blk] * (k + 1), format="csr")
+    if fine.masked.any():
+        # obstacle domain: the fine unknowns without an equation (outside the domain) are not
+        # part of the nested space; P sets them to zero, so R = P^T never carries their residual
+        # into the coarse unknowns of the obstacle's boundary
+        from .assemble import dead_dofs
+        keep = np.ones(fine.N)
+        keep[dead_dofs(fine)] = 0.0
+        out = sp.diags(keep) @ out
+        out = sp.csr_matrix(out)
+        out.eliminate_zeros()
+    return out
 
 
 def _coarse_cell_and_ref_fixed(coarse, xyz, cell):

@@ -21,6 +21,21 @@ from __future__ import annotations
 import numpy as np
 
 
+def patch_active(lev) -> np.ndarray:
+    """(ncells, n_patch) bool: the local unknowns each patch smooths.  A cell of the fluid domain
+    smooths all of its unknowns.  With an obstacle (cells removed from the mesh), a removed cell's
+    patch holds only its unknowns without an equation (velocity at Q2 nodes of removed cells only,
+    its pressure), whose rows are the identity: the paper's patches are the cells of the mesh, and
+    the unknowns outside the domain are solved exactly in patches of their own."""
+    act = np.ones((lev.n_cells, lev.n_patch), dtype=bool)
+    if lev.masked.any():
+        dead = np.zeros(lev.N, dtype=bool)
+        from .assemble import dead_dofs
+        dead[dead_dofs(lev)] = True
+        act[lev.masked] = dead[lev.dof[lev.masked]]
+    return act
+
+
 def local_matrices(jac, lev) -> np.ndarray:
     """J_K = J[dof(K,.), dof(K,.)] for every cell: (ncells, n_patch, n_patch)."""
     out = np.zeros((lev.n_cells, lev.n_patch, lev.n_patch))
@@ -32,21 +47,31 @@ def local_matrices(jac, lev) -> np.ndarray:
 
 
 def local_inverses(jac, lev) -> np.ndarray:
-    """J_K^{-1} for every cell via LAPACK (numpy.linalg.inv)."""
-    return np.linalg.inv(local_matrices(jac, lev))
+    """J_K^{-1} for every cell via LAPACK (numpy.linalg.inv).  A removed cell's patch (see
+    patch_active) acts on its identity rows only: its inverse is the projector onto them."""
+    if not lev.masked.any():
+        return np.linalg.inv(local_matrices(jac, lev))
+    act = patch_active(lev)
+    out = np.zeros((lev.n_cells, lev.n_patch, lev.n_patch))
+    fluid = ~lev.masked
+    out[fluid] = np.linalg.inv(local_matrices(jac, lev)[fluid])
+    for cell in np.nonzero(lev.masked)[0]:
+        out[cell] = np.diag(act[cell].astype(float))
+    return out
 
 
 def sweep_averaged(jac, lev, jinv, b, d, omega: float = 0.7, sweeps: int = 1) -> np.ndarray:
     """J_max = `sweeps` iterations of (S0)-(S3) starting from d^0 = d."""
     dof = lev.dof
+    act = patch_active(lev).astype(float)
     d = np.array(d, dtype=float, copy=True)
     for _ in range(sweeps):
         p = np.zeros(lev.N)                                      # (S0)
         z = np.zeros(lev.N)
         r = b - jac @ d                                          # b - J d^{j-1}, shared by all K
         y = d[dof] + omega * np.einsum("kij,kj->ki", jinv, r[dof])   # (S1): S_K(d^{j-1})
-        np.add.at(z, dof, y)                                     # (S2)
-        np.add.at(p, dof, 1.0)
+        np.add.at(z, dof, y * act)                               # (S2), over each patch's unknowns
+        np.add.at(p, dof, act)
         d = z / p                                                # (S3)
     return d
 

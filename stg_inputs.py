@@ -32,6 +32,9 @@ class MeshSpec:
     hi: tuple           # domain upper corner
     n_levels: int       # levels 0 (coarsest) .. n_levels-1 (finest)
     dirichlet: int      # bit mask of Dirichlet faces; the other faces are do-nothing
+    # 2D only: cells removed from the domain, the box [x0, x1) x [y0, y1) of coarsest-level cell
+    # indices (empty: none); its faces carry Dirichlet data (no-slip for the obstacle channel)
+    obstacle: tuple = ()
 
     def cells(self, level: int) -> tuple:
         f = 2 ** (self.n_levels - 1 - level)
@@ -42,6 +45,13 @@ class MeshSpec:
 
     def pure_dirichlet(self) -> bool:
         return self.dirichlet == (1 << (2 * self.dim)) - 1
+
+    def obstacle_cells(self, level: int) -> tuple:
+        """The obstacle box in the cell indices of `level`, (x0, x1, y0, y1), or ()."""
+        if not self.obstacle:
+            return ()
+        f = 2 ** level
+        return tuple(int(v) * f for v in self.obstacle)
 
 
 def n_nodes(cells: tuple) -> int:
@@ -178,6 +188,9 @@ WORKLOADS = {
     # 3D unit cube 48^3 -> 6^3, dG(1)
     "cube48_k1": dict(spec=MeshSpec(3, (48, 48, 48), (0.0,) * 3, (1.0,) * 3, 4, ALL3), k=1, nu=1e-3,
                       tau=0.01, newton=False, w="fourier", nu1=2, nu2=2),
+    # 3D unit cube 32^3 -> 4^3 for the robustness study in k = 0, 1, 2 (Sec. 4, Table 3.2)
+    "cube32": dict(spec=MeshSpec(3, (32, 32, 32), (0.0,) * 3, (1.0,) * 3, 4, ALL3), k=1, nu=1e-3,
+                   tau=0.01, newton=False, w="fourier", nu1=2, nu2=2),
 }
 
 
