@@ -1,13 +1,15 @@
 // Allocation-free batched inverse of caller-supplied local matrices.
 //
 // Some callers cannot call cudaMalloc at the point where they need local
-// inverses: code that runs while a CUDA stream is being captured into a graph
-// (allocation is not a capturable operation), host frameworks that hand out
-// device memory only from their own arenas, and real-time loops that forbid
-// allocation after start-up.  stg_setup allocates everything a context needs,
-// so it is not usable there.  This entry point needs no context: the caller
-// passes the matrices and the output buffer, and the Gauss-Jordan working
-// copies live in a fixed array compiled into the library.
+// inverses: host applications and frameworks that own the GPU's memory and
+// hand it out only from their own pools or arenas (a stray cudaMalloc there
+// fails once the pool holds the memory, or breaks the host's accounting), and
+// real-time loops that forbid allocation after start-up because cudaMalloc and
+// cudaFree may synchronise the device and take unbounded time.  stg_setup
+// allocates everything a context needs, so it is not usable there.  This entry
+// point needs no context: the caller passes the matrices and the output
+// buffer, and the Gauss-Jordan working copies live in a fixed array compiled
+// into the library.
 //
 // The kernel is a variant of the patch-inversion kernel of the smoother set-up
 // (same in-place Gauss-Jordan elimination with partial pivoting, first maximal
@@ -30,16 +32,18 @@ constexpr int kMaxDevices = 64;
 
 // Working matrices of the in-flight batch; held by every GPU that loads the library.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
-// [0]: 1 + index of the first singular matrix of the call (0 = none).
-static __device__ __align__(256) int g_noalloc_status[4];
+// Lowest index of a singular matrix in the current call (all bits set = none); set to
+// all ones at the start of every call, lowered by atomicMin.
+static __device__ __align__(256) unsigned long long g_noalloc_status[4];
 
 // Device addresses of the two arrays, looked up once per device.
 double* g_scratch_ptr[kMaxDevices];
-int* g_status_ptr[kMaxDevices];
+unsigned long long* g_status_ptr[kMaxDevices];
 bool g_ready[kMaxDevices];
 
 __global__ void __launch_bounds__(256) invert_dense_kernel(int n, long long p0, const double* __restrict__ a,
-                                                           double* __restrict__ a_inv, double* work, int* status) {
+                                                           double* __restrict__ a_inv, double* work,
+                                                           unsigned long long* status) {
   const long long p = p0 + blockIdx.x;
   double* A = work + (long long)blockIdx.x * n * n;
   __shared__ double colj[kNoAllocMaxN];
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(256) invert_dense_kernel(int n, long long p0, 
   }
   double* dst = a_inv + p * n * n;
   if (s_fail) {
-    if (tid == 0) atomicCAS(status, 0, (int)(p + 1));
+    if (tid == 0) atomicMin(status, (unsigned long long)p);
     for (int t = tid; t < n * n; t += nth) dst[t] = 0.0;
     return;
   }
@@ -154,23 +158,24 @@ extern "C" stg_status stg_invert_local_noalloc(int n, long long count, const dou
     g_ready[dev] = true;
   }
   double* work = g_scratch_ptr[dev];
-  int* status = g_status_ptr[dev];
-  e = cudaMemsetAsync(status, 0, sizeof(int) * 4, st);  // the array keeps the previous call's flag
+  unsigned long long* status = g_status_ptr[dev];
+  // the array keeps the previous call's value: reset it to "none" (all bits set)
+  e = cudaMemsetAsync(status, 0xff, sizeof(unsigned long long), st);
   const long long slots = kNoAllocScratchDoubles / ((long long)n * n);
   for (long long p0 = 0; e == cudaSuccess && p0 < count; p0 += slots) {
     const long long cnt = count - p0 < slots ? count - p0 : slots;
     invert_dense_kernel<<<(unsigned)cnt, 256, 0, st>>>(n, p0, a, a_inv, work, status);
     e = cudaGetLastError();
   }
-  int h[4] = {0, 0, 0, 0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st);
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_global_error(std::string("stg_invert_local_noalloc: ") + cudaGetErrorString(e));
     return STG_ECUDA;
   }
-  if (h[0]) {
-    set_global_error("stg_invert_local_noalloc: matrix " + std::to_string(h[0] - 1) + " has a zero pivot");
+  if (h != ~0ULL) {
+    set_global_error("stg_invert_local_noalloc: matrix " + std::to_string(h) + " has a zero pivot");
     return STG_ESINGULAR;
   }
   return STG_OK;
