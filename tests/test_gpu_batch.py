@@ -55,3 +55,32 @@ def test_autotune_keeps_results_bit_identical():
         assert 0 <= variant < 13 and ms > 0
         assert torch.equal(s.vcycle(b), v0)
         s.close()
+
+
+def test_batch_members_match_oracle():
+    """Three members of the batch (a channel at k = 1, a square at k = 2, a square at k = 0) against
+    the oracle: the same FGMRES iteration count within one and the 1e-8 true residual of the
+    oracle's operator."""
+    import oracle
+    from oracle import fgmres
+    from paper_2210_02690_gb300 import Batch
+    solvers = [_solver(spec, k, 10 + i) for i, (spec, k) in enumerate(PROBLEMS)]
+    refs, rhs = {}, []
+    for i, (s, (spec, k)) in enumerate(zip(solvers, PROBLEMS)):
+        w = si.channel_w(spec, k, seed=10 + i) if spec.dirichlet == OUT2 else si.fourier_w(spec, k, seed=10 + i)
+        ref = oracle.Hierarchy(spec, k, 1e-3, 0.01, w, newton=True, nu1=2, nu2=2)
+        refs[i] = ref
+        rhs.append(torch.from_numpy(ref.apply(si.reference_solution(spec, k, seed=20 + i))).cuda())
+    batch = Batch(solvers)
+    xs, its, rel, ok = batch.gmres_solve(rhs)
+    assert ok
+    for i in (0, 1, 3):
+        ref = refs[i]
+        b = rhs[i].cpu().numpy()
+        x = xs[i].cpu().numpy()
+        _, its_ref, _, ok_ref = fgmres.fgmres(ref.apply, ref.vcycle, b, rtol=1e-8)
+        assert ok_ref and abs(its[i] - its_ref) <= 1, (i, its[i], its_ref)
+        assert np.linalg.norm(b - ref.apply(x)) / np.linalg.norm(b) <= 1.01e-8
+    batch.close()
+    for s in solvers:
+        s.close()

@@ -72,3 +72,25 @@ def test_time_march_three_slabs():
         Xg = solver.slab_initial_guess(Xg)
         assert np.array_equal(Xg.cpu().numpy(), expect)
     solver.close()
+
+
+def test_damped_newton_branch_matches_oracle():
+    """The oracle's damping case (third full step raises ||F||, the half step is taken): the GPU
+    takes the same number of steps to the same solution, so it damped the same step."""
+    from test_oracle_newton import DAMP_K, DAMP_NU, DAMP_SPEC, DAMP_TAU, damping_case
+    from paper_2210_02690_gb300 import Solver
+
+    lev, b, X0, v0, g = damping_case()
+    lams = []
+    X_ref, steps_ref, _, hist = newton.newton_slab(DAMP_SPEC, DAMP_K, DAMP_NU, DAMP_TAU, X0, b, rtol=1e-10,
+                                                   gmres_rtol=1e-12, lambdas=lams)
+    assert min(lams) < 1.0
+    w0 = torch.from_numpy(np.concatenate([X0[a * (lev.R + lev.S):a * (lev.R + lev.S) + lev.R]
+                                          for a in range(DAMP_K + 1)])).cuda()
+    solver = Solver(DAMP_SPEC, DAMP_K, DAMP_NU, DAMP_TAU, w0, nu1=2, nu2=2, gmres_rtol=1e-12)
+    X, steps, its, res, ok = solver.newton_slab(torch.from_numpy(X0).cuda(), v_prev=torch.from_numpy(v0).cuda(),
+                                                g=torch.from_numpy(g.ravel()).cuda(), rtol=1e-10)
+    assert ok and steps == steps_ref
+    X = X.cpu().numpy()
+    assert np.linalg.norm(X - X_ref) / np.linalg.norm(X_ref) < 1e-9
+    solver.close()

@@ -1,12 +1,14 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on small meshes.
 
-Tolerances (FP64 form): operator applications are held to the forward-error
-bound of a product whose entries carry a few tens of ulps (each entry is a sum
-of ~30 quadrature terms): 64 eps || |J| |x| || / || J x ||; transfers (exact
-weights) to 1e-14 relative; results that pass through the local inverses
-J_K^{-1} carry their rounding amplified by cond(J_K) (up to ~1e4 on these
-meshes), so local inverses, sweeps and V-cycles are held to 1e-11 relative;
-FGMRES solutions at rtol 1e-12 agree to 1e-8 relative.
+Tolerances (FP64 form):
+* operator applications: the forward-error bound of a product whose entries carry a few tens of
+  ulps (each entry is a sum of ~30 quadrature terms), 64 eps || |J| |x| || / || J x ||;
+* transfers (exact weights): 1e-14 relative;
+* local inverses, smoother sweeps and V-cycles: 1e-12 relative per application, measured block by
+  block: for every Radau node, the velocity block and the pressure block of a vector (every
+  (row block, column block) pair of a local inverse) is held to max|x - x_ref| <= 1e-12 max|x_ref|
+  of that block, so no block can hide behind a larger one;
+* FGMRES solutions at rtol 1e-12 agree to 1e-8 relative.
 """
 import numpy as np
 import pytest
@@ -31,6 +33,8 @@ CASES = {
     "tall_k1_coarse_global": (si.MeshSpec(2, (8, 32), (0.0, 0.0), (0.5, 2.0), 2, OUT2), 1, True),
     "cube_k0": (si.MeshSpec(3, (4, 4, 2), (0.0,) * 3, (1.0, 1.0, 0.5), 2, si.ALL3), 0, True),
     "cube_k1_outflow": (si.MeshSpec(3, (2, 4, 2), (0.0,) * 3, (0.5, 1.0, 0.5), 2, si.ALL3 & ~si.FACE_XHI), 1, True),
+    # 3D dG(2): 255 x 255 local matrices (FP64 inversion through global scratch)
+    "cube_k2": (si.MeshSpec(3, (4, 2, 2), (0.0,) * 3, (1.0, 0.5, 0.5), 2, si.ALL3 & ~si.FACE_XHI), 2, True),
 }
 NU, TAU = 1e-3, 0.01
 
@@ -72,6 +76,45 @@ def cpu(t):
     return t.detach().cpu().numpy()
 
 
+FP64_BAR = 1e-12
+
+
+def vector_blocks(lev):
+    """Index arrays of the velocity and the pressure block of every Radau node (C-ABI order)."""
+    out = []
+    for a in range(lev.k + 1):
+        base = a * (lev.R + lev.S)
+        out.append(np.arange(base, base + lev.R))
+        out.append(np.arange(base + lev.R, base + lev.R + lev.S))
+    return out
+
+
+def brel(x, x_ref, lev):
+    """Largest block-wise max-abs relative error over the blocks of vector_blocks."""
+    x, x_ref = np.asarray(x), np.asarray(x_ref)
+    return max(np.max(np.abs(x[i] - x_ref[i])) / max(np.max(np.abs(x_ref[i])), 1e-300) for i in vector_blocks(lev))
+
+
+def patch_blocks(lev):
+    """Index arrays of the velocity and pressure rows of every Radau node in a local patch."""
+    out = []
+    for a in range(lev.k + 1):
+        base = a * (lev.Rhat + lev.Shat)
+        out.append(np.arange(base, base + lev.Rhat))
+        out.append(np.arange(base + lev.Rhat, base + lev.Rhat + lev.Shat))
+    return out
+
+
+def brel_matrix(m, m_ref, lev):
+    """Largest max-abs relative error over all (row block, column block) pairs of a local inverse."""
+    worst = 0.0
+    for ri in patch_blocks(lev):
+        for ci in patch_blocks(lev):
+            ref = m_ref[np.ix_(ri, ci)]
+            worst = max(worst, np.max(np.abs(m[np.ix_(ri, ci)] - ref)) / max(np.max(np.abs(ref)), 1e-300))
+    return worst
+
+
 def consistent_rhs(ref, seed=7):
     xs = si.reference_solution(ref.spec, ref.k, seed=seed)
     return ref.apply(xs)
@@ -91,14 +134,33 @@ def test_jacobian_every_level(name):
         assert rel(y, y_ref) < bound, (lvl, rel(y, y_ref), bound)
 
 
+def refined_inverse(A, X):
+    """X improved by two Newton-Schulz steps X <- X + X (I - A X) in extended precision."""
+    Al, Xl = A.astype(np.longdouble), X.astype(np.longdouble)
+    eye = np.eye(len(A), dtype=np.longdouble)
+    for _ in range(2):
+        Xl = Xl + Xl @ (eye - Al @ Xl)
+    return Xl.astype(float)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_local_inverses(name):
+    """J_K^{-1} against the oracle's J_K: LAPACK's inverse refined in extended precision is the
+    reference.  The GPU is held to the FP64 bar, or, where cond(J_K) keeps LAPACK's own inverse
+    further than that from the reference (k = 3, 4: cond ~1e5, n = 84, 105), to twice LAPACK's
+    own block-wise error: at least as accurate as the oracle's inverse."""
+    from oracle import vanka as ov
     gpu, ref = pair(name)
     for lvl in range(1, len(ref.levels)):
-        n_cells = ref.levels[lvl].n_cells
+        lev = ref.levels[lvl]
+        n_cells = lev.n_cells
+        local = ov.local_matrices(ref.J[lvl], lev)
         for cell in sorted({0, n_cells // 3, n_cells - 1}):
             g = gpu.local_inverse(lvl, cell)
-            assert rel(g, ref.jinv[lvl][cell]) < 1e-11, (lvl, cell)
+            exact = refined_inverse(local[cell], ref.jinv[lvl][cell])
+            lapack = brel_matrix(ref.jinv[lvl][cell], exact, lev)
+            err = brel_matrix(g, exact, lev)
+            assert err < max(FP64_BAR, 2 * lapack), (lvl, cell, err, lapack)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -120,17 +182,21 @@ def test_coarse_solve(name):
     xs = si.reference_solution(ref.spec, ref.k, seed=5, level=0)
     b = ref.J[0] @ xs
     x = cpu(gpu.coarse_solve(torch.from_numpy(b).cuda()))
-    assert rel(ref.J[0] @ x, b) < 1e-11
+    assert rel(ref.J[0] @ x, b) < 1e-13
+    x_ref = ref.coarse_solve(b)
     if ref.singular:
-        x = multigrid.normalise_pressure(lev0, x)
-    assert rel(x, ref.coarse_solve(b) if not ref.singular else multigrid.normalise_pressure(lev0, ref.coarse_solve(b))) < 1e-9
+        x, x_ref = multigrid.normalise_pressure(lev0, x), multigrid.normalise_pressure(lev0, x_ref)
+    # two backward-stable solves differ by about cond(J_0) eps in the forward error
+    cond = np.linalg.cond(ref.J[0].toarray()) if lev0.N <= 4000 else 1e6
+    assert rel(x, x_ref) < max(1e-12, 10 * cond * EPS), (rel(x, x_ref), cond)
 
 
 def test_coarse_solve_large_slab_blocks():
     """Coarse mesh 2x64 at k = 2: slab blocks of 1347 and 777 unknowns, inverted by the
     multi-launch Gauss-Jordan.  Explicit inverses of such blocks carry rounding that grows like
-    n_b eps cond(block): the backward error is held to 1e-9 (observed 6e-11) and the forward
-    error to cond(J_0) times that (cond(J_0) = 9.4e4)."""
+    n_b eps cond(block) (relative residual 6e-11 unrefined); after the FP64 form's refinement
+    step the residual is held to 1e-13 and the forward error to 10 cond(J_0) eps
+    (cond(J_0) = 9.4e4)."""
     from paper_2210_02690_gb300 import Solver
     import oracle
     spec = si.MeshSpec(2, (4, 128), (0.0, 0.0), (0.25, 8.0), 2, OUT2)
@@ -140,9 +206,9 @@ def test_coarse_solve_large_slab_blocks():
     xs = si.reference_solution(spec, 2, seed=5, level=0)
     b = ref.J[0] @ xs
     x = cpu(gpu.coarse_solve(torch.from_numpy(b).cuda()))
-    assert rel(ref.J[0] @ x, b) < 1e-9
+    assert rel(ref.J[0] @ x, b) < 1e-13
     cond = np.linalg.cond(ref.J[0].toarray())
-    assert rel(x, ref.coarse_solve(b)) < cond * 1e-9
+    assert rel(x, ref.coarse_solve(b)) < 10 * cond * EPS
     # the whole solver still converges to the FP64 oracle's solution of the fine system
     bf = consistent_rhs(ref)
     xf, its, relres, ok = gpu.gmres_solve(torch.from_numpy(bf).cuda())
@@ -159,7 +225,8 @@ def test_smoother_sweeps(name):
     d0 = si.random_vector(lev.N, 22)
     d = cpu(gpu.smooth(lvl, 3, torch.from_numpy(b).cuda(), torch.from_numpy(d0).cuda()))
     d_ref = vanka.sweep_averaged(ref.J[lvl], lev, ref.jinv[lvl], b, d0, 0.7, 3)
-    assert rel(d, d_ref) < 1e-11
+    err = brel(d, d_ref, lev)
+    assert err < FP64_BAR, err
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -170,13 +237,48 @@ def test_vcycle(name):
     x_ref = ref.vcycle(b)
     if ref.singular:
         x, x_ref = multigrid.normalise_pressure(ref.fine, x), multigrid.normalise_pressure(ref.fine, x_ref)
-    assert rel(x, x_ref) < 1e-11
+    err = brel(x, x_ref, ref.fine)
+    assert err < FP64_BAR, err
 
 
 def test_vcycle_coloured_smoother():
     gpu, ref = pair("channel_k1_newton", smoother=1)
     b = consistent_rhs(ref)
-    assert rel(cpu(gpu.vcycle(torch.from_numpy(b).cuda())), ref.vcycle(b)) < 1e-11
+    err = brel(cpu(gpu.vcycle(torch.from_numpy(b).cuda())), ref.vcycle(b), ref.fine)
+    assert err < FP64_BAR, err
+
+
+N_VARIANTS = 13
+
+
+@pytest.mark.parametrize("variant", range(N_VARIANTS))
+def test_every_colour_variant_matches_oracle(variant):
+    """Every colour-kernel variant the autotuner can pick (one warp per patch: 9 shapes; factors
+    staged by bulk copies: 4 pipeline shapes), set on all levels: FP64 sweeps and V-cycles at the
+    FP64 bar, the FP32 form's V-cycle at the FP32 bar."""
+    gpu, ref = pair("channel_k1_newton")
+    saved = gpu.colour_variants()
+    gpu.set_colour_variants([variant] * len(saved))
+    try:
+        lvl = len(ref.levels) - 1
+        lev = ref.levels[lvl]
+        b = si.random_vector(lev.N, 21)
+        d0 = si.random_vector(lev.N, 22)
+        d = cpu(gpu.smooth(lvl, 2, torch.from_numpy(b).cuda(), torch.from_numpy(d0).cuda()))
+        d_ref = vanka.sweep_averaged(ref.J[lvl], lev, ref.jinv[lvl], b, d0, 0.7, 2)
+        assert brel(d, d_ref, lev) < FP64_BAR
+        bc = consistent_rhs(ref)
+        assert brel(cpu(gpu.vcycle(torch.from_numpy(bc).cuda())), ref.vcycle(bc), ref.fine) < FP64_BAR
+    finally:
+        gpu.set_colour_variants(saved)
+    g32, _ = pair("channel_k1_newton", vcycle_prec="f32", factor_prec="f32")
+    saved = g32.colour_variants()
+    g32.set_colour_variants([variant] * len(saved))
+    try:
+        bc = consistent_rhs(ref)
+        assert rel(cpu(g32.vcycle(torch.from_numpy(bc).cuda())), ref.vcycle(bc)) < 1e-4
+    finally:
+        g32.set_colour_variants(saved)
 
 
 @pytest.mark.parametrize("name", ["channel_k1_newton", "square_k0_dirichlet", "cube_k1_outflow"])
@@ -204,8 +306,8 @@ def test_reduced_precision_forms_converge(prec):
     x, its, relres, ok = gpu.gmres_solve(torch.from_numpy(b).cuda())
     assert ok64 and ok and relres <= 1e-8
     assert rel(ref.apply(cpu(x)), b) <= 1.01e-8
+    assert its <= its64 + 1          # reduced-precision factors are kept only if the counts hold
     if fprec == "f32":
-        assert its <= its64 + 1
         v = cpu(gpu.vcycle(torch.from_numpy(b).cuda()))
         assert rel(v, ref.vcycle(b)) < 1e-4
 
