@@ -77,16 +77,52 @@ def oracle_step_cli(factor: int, repeats: int) -> None:
                       "n_dofs": si.n_dofs(2, spec.n, cfg["k"])}))
 
 
-def run_oracle(factor: int, repeats: int, timeout: float = 900.0) -> dict:
+def _oracle_env() -> dict:
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
+    return env
+
+
+def run_oracle(factor: int, repeats: int, timeout: float = 900.0) -> dict:
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-step", str(factor), str(repeats)],
-                         capture_output=True, text=True, env=env, timeout=timeout, cwd=ROOT)
+                         capture_output=True, text=True, env=_oracle_env(), timeout=timeout, cwd=ROOT)
     if out.returncode:
         raise RuntimeError("oracle run failed: " + out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def available_memory_bytes() -> int:
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_oracle_all_cores(factor: int, gb_per_process: float, timeout: float = 900.0) -> dict:
+    """The unmodified oracle step on every host core at once: one single-threaded process per core
+    (as many as the free memory holds), each solving the same sample; the rate is the smoothed DoFs
+    of all processes over the wall time from the first start to the last finish."""
+    cores = os.cpu_count() or 1
+    procs = max(1, min(cores, int(available_memory_bytes() / (gb_per_process * 1e9)) or 1))
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-step", str(factor), "1"],
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=_oracle_env(), cwd=ROOT)
+          for _ in range(procs)]
+    outs = []
+    for p in ps:
+        so, se = p.communicate(timeout=timeout)
+        if p.returncode:
+            raise RuntimeError("oracle run failed: " + se[-2000:])
+        outs.append(json.loads(so.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    dofs = sum(o["smoothed_per_cycle"] * sum(o["iters"]) for o in outs)
+    return {"value": dofs / wall, "processes": procs, "host_cores": cores, "wall_s": wall, "cells": outs[0]["cells"],
+            "n_dofs": outs[0]["n_dofs"]}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -198,6 +234,88 @@ def colour_kernel_name(variant: int) -> str:
             f"({128 << (variant % 3)} threads, finest level)")
 
 
+def q2_block_couplings(cells: tuple) -> int:
+    """Number of (node, node) blocks of the Q2 velocity operator: two Q2 nodes couple when they
+    share a cell, which factorises over the directions (a vertex line couples with the nodes
+    within two steps, a cell-interior line with those within one)."""
+    total = 1
+    for c in cells:
+        m = 2 * c + 1
+        total *= sum(min(i + (2 if i % 2 == 0 else 1), m - 1) - max(i - (2 if i % 2 == 0 else 1), 0) + 1
+                     for i in range(m))
+    return total
+
+
+def sweep_bytes(dim: int, cells: tuple, k: int, form: str) -> dict:
+    """Algorithmic bytes of one averaged Vanka sweep on a level (each array read or written once):
+    the residual r = b - J x (operator + x, b read, r written), the colour kernels (every J_K^{-1}
+    read, r gathered, z read and written per patch) and the update (d, z read and written)."""
+    nt = k + 1
+    ncell = int(np.prod(cells))
+    n = nt * (3 ** dim * dim + dim + 1)
+    N = si.n_dofs(dim, cells, k)
+    nnzb = q2_block_couplings(cells)
+    vs = 8 if form == "f64" else 4
+    fs = {"f64": 8, "f32": 4, "bf16": 2}[form]
+    vp = ncell * 3 ** dim * nt * dim * (dim + 1)           # velocity-pressure (and pressure-velocity) entries
+    if form == "f64" or dim == 3 or k == 0:
+        op = nnzb * (nt * dim) ** 2 * vs + 2 * vp * vs       # dense node blocks
+    else:
+        op = nnzb * 4 + nnzb * nt * dim * dim * 4 + 2 * vp * 4   # Kronecker split: M_ij + per-node blocks
+    residual = op + 3 * N * vs
+    colour = ncell * (n * n * fs + 3 * n * vs)
+    update = 4 * N * vs
+    return {"residual": residual, "colour": colour, "update": update, "total": residual + colour + update}
+
+
+def time_ms(torch, stream, fn, reps: int = 1) -> float:
+    """Device time of fn() (reps times) on `stream`, CUDA events, synchronised on both sides."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, peak: float) -> dict:
+    """HBM fraction of the finest level's colour kernels (2D): algorithmic bytes (every J_K^{-1}
+    in the form's factor precision, r gathered, z read and written) over their CUDA-event time."""
+    n = 21 * (k + 1)
+    fs = {"f64": 8, "f32": 4, "bf16": 2}[form]
+    vs = 8 if form == "f64" else 4
+    per_launch = n * (n * fs + 3 * vs) * patches / max(launches, 1)
+    avg = ms / max(launches, 1)
+    gbs = per_launch / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+    return {"bytes_per_launch": per_launch, "avg_launch_ms": avg, "gbs": gbs, "frac": gbs / peak,
+            "launches": launches}
+
+
+def smoother_report(solver, spec, k, cfg, form: str, peak: float, torch, sweeps: int = 20) -> dict:
+    """Sweep- and cycle-level smoothed DoF/s (SURVEY's metric 1) and the finest sweep's HBM fraction.
+    One sweep (residual + colour kernels + update) is timed as the difference of stg_smooth with
+    2 + sweeps and 2 sweeps on the finest level (the C-ABI conversions cancel); a V-cycle as the
+    mean of `sweeps` stg_vcycle calls."""
+    top = spec.n_levels - 1
+    N = si.n_dofs(spec.dim, spec.n, k)
+    b = torch.from_numpy(si.random_vector(N, 31)).cuda()
+    x0 = torch.zeros_like(b)
+    solver.smooth(top, 2, b, x0)
+    t_lo = min(time_ms(torch, solver.stream, lambda: solver.smooth(top, 2, b, x0)) for _ in range(3))
+    t_hi = min(time_ms(torch, solver.stream, lambda: solver.smooth(top, 2 + sweeps, b, x0)) for _ in range(3))
+    t_sweep = (t_hi - t_lo) / sweeps
+    by = sweep_bytes(spec.dim, spec.n, k, form)
+    out = solver.vcycle(b)
+    t_cycle = time_ms(torch, solver.stream, lambda: solver.vcycle(b, out=out), reps=sweeps) / sweeps
+    per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
+    achieved = by["total"] / (t_sweep * 1e-3) / 1e9
+    return {"sweep_ms": t_sweep, "sweep_dofs_per_s": N / (t_sweep * 1e-3),
+            "vcycle_ms": t_cycle, "cycle_dofs_per_s": per_cycle / (t_cycle * 1e-3),
+            "sweep_bytes": by, "sweep_gbs": achieved, "sweep_hbm_frac": achieved / peak}
+
+
 def timed_steps(solver, w, b, x, steps: int, torch) -> tuple:
     """Runs `steps` steps on the solver's stream; returns (ms, iterations of the last step)."""
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -234,6 +352,11 @@ def gpu_arm(args) -> None:
              "bf16": dict(vcycle_prec="f32", factor_prec="bf16")}
     n_dofs = si.n_dofs(2, spec.n, k)
     per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs", 6800.0)
     results = {}
     main = None
     for name in args.forms:
@@ -249,8 +372,8 @@ def gpu_arm(args) -> None:
             tuned = solver.autotune()
         timed_steps(solver, w, b, x, args.warmup, torch)
         steps = args.steps if name == "f32" else max(3, args.steps // 2)
+        solver.profile(True)
         if name == "f32":
-            solver.profile(True)
             launches0 = solver.kernel_launches()
         barrier(world)
         with ClockSampler(local) as clk:
@@ -279,11 +402,14 @@ def gpu_arm(args) -> None:
                             "variants": ",".join(str(v) for v in solver.colour_variants())},
                "time_to_tol_ms": e[1].elapsed_time(e[2]), "rel_res": rel_s, "clocks": clocks,
                "value": aggregate_rate(per_cycle * its, steps, world, ms_max)}
+        pms, plaunch, ppatch = solver.profile_read()
+        res["colour_kernel"] = (pms, plaunch, ppatch)
+        solver.profile(False)
+        res["colour_kernel_frac"] = colour_fraction(k, name, pms, plaunch, ppatch, peak)
+        if world == 1:
+            res["smoother"] = smoother_report(solver, spec, k, cfg, name, peak, torch)
         if name == "f32":
-            pms, plaunch, ppatch = solver.profile_read()
             res["gpu_launches"] = launches1 - launches0
-            res["colour_kernel"] = (pms, plaunch, ppatch)
-            solver.profile(False)
             # end to end through the public API: pinned host inputs, copies inside the timed region
             w_h = torch.from_numpy(w_np.ravel()).pin_memory()
             b_h = b.cpu().pin_memory()
@@ -321,11 +447,6 @@ def gpu_arm(args) -> None:
     bytes_per_patch = npatch * npatch * 4 + 3 * npatch * 4
     avg_ms = pms / max(plaunch, 1)
     per_launch_bytes = bytes_per_patch * ppatch / max(plaunch, 1)
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    peak = peaks.get("hbm_gbs", 6800.0)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     variant = r32["autotune"]["finest_variant"]
     per_patch = MEASURED_TRAFFIC_PER_PATCH.get(variant)
@@ -355,13 +476,17 @@ def gpu_arm(args) -> None:
         "time_to_tol_ms": r32["time_to_tol_ms"],
         "roofline": roofline, "e2e": r32["e2e"], "gpu_launches": r32["gpu_launches"], "clocks": r32["clocks"],
     }
-    keys = ("value", "ms_per_step", "iters", "setup_ms", "time_to_tol_ms", "rel_res", "autotune")
+    if "smoother" in r32:
+        out["smoother"] = r32["smoother"]
+    out["colour_kernel_frac"] = r32["colour_kernel_frac"]
+    keys = ("value", "ms_per_step", "iters", "setup_ms", "time_to_tol_ms", "rel_res", "autotune",
+            "colour_kernel_frac", "smoother")
     if "f64" in results:
-        out["f64_form"] = {k_: results["f64"][k_] for k_ in keys}
+        out["f64_form"] = {k_: results["f64"][k_] for k_ in keys if k_ in results["f64"]}
         out["speedup_time_to_tol_f32_vs_f64"] = results["f64"]["time_to_tol_ms"] / r32["time_to_tol_ms"]
         out["speedup_step_f32_vs_f64"] = results["f64"]["ms_per_step"] / r32["ms_per_step"]
     if "bf16" in results:
-        out["bf16_factor_form"] = {k_: results["bf16"][k_] for k_ in keys}
+        out["bf16_factor_form"] = {k_: results["bf16"][k_] for k_ in keys if k_ in results["bf16"]}
     if main:
         main.close()
     if world == 1 and not args.no_cpu_baseline:
@@ -372,11 +497,85 @@ def gpu_arm(args) -> None:
                                "sample": f"oracle full step (assembly, LAPACK local inverses, coarse LU, FGMRES to "
                                          f"1e-8) on the same channel at {o['cells'][0]}x{o['cells'][1]} quads "
                                          f"({o['n_dofs']} DoFs, 4 levels), 1 thread, {t:.1f} s"}
+        a = run_oracle_all_cores(CPU_SAMPLE_FACTOR, 2.5)
+        out["cpu_baseline"]["all_cores"] = {
+            "value": a["value"], "unit": UNIT, "cores": a["processes"], "host_cores": a["host_cores"],
+            "kind": "oracle",
+            "sample": f"{a['processes']} single-threaded oracle processes at once, each the full step on the "
+                      f"{a['cells'][0]}x{a['cells'][1]} channel; {a['wall_s']:.1f} s wall"}
+    if world == 1 and not args.no_workloads:
+        import torch
+        out["square256"] = square256_report(peak, torch)
+        out["cube48"] = cube48_report(peak, torch)
+    if world == 1 and not args.no_workloads:
+        out["obstacle_march"] = obstacle_march_report()
     if world == 1 and not args.no_warm_start:
         out["warm_start"] = warm_start_report()
     if world == 1 and not args.no_batch:
         out["batched"] = batch_report()
     print(json.dumps(out), flush=True)
+
+
+FORMS = {"f32": dict(vcycle_prec="f32", factor_prec="f32"), "f64": dict(vcycle_prec="f64", factor_prec="f64"),
+         "bf16": dict(vcycle_prec="f32", factor_prec="bf16")}
+
+
+def workload_line(name: str, k: int, form: str, peak: float, torch, reps: int = 3) -> dict:
+    """Set-up, FGMRES time-to-1e-8 and the smoother figures of one (workload, k, form)."""
+    from paper_2210_02690_gb300 import Solver
+
+    cfg = si.WORKLOADS[name]
+    spec = cfg["spec"]
+    w = torch.from_numpy(si.fourier_w(spec, k).ravel()).cuda()
+    s = Solver(spec, k, cfg["nu"], cfg["tau"], w, nu1=cfg["nu1"], nu2=cfg["nu2"],
+               linearisation="newton" if cfg["newton"] else "oseen", **FORMS[form])
+    b = s.apply_jacobian(torch.from_numpy(si.reference_solution(spec, k)).cuda())
+    x = torch.zeros_like(b)
+    variant, _ = s.autotune()
+    s.update_linearisation(w)
+    s.gmres_solve(b, out=x)
+    t_setup = min(time_ms(torch, s.stream, lambda: s.update_linearisation(w)) for _ in range(reps))
+    its = [0]
+
+    def solve():
+        _, its[0], rel, ok = s.gmres_solve(b, out=x)
+        if not ok:
+            raise RuntimeError(f"{name} k={k} {form}: FGMRES did not converge ({rel:.2e})")
+    t_solve = min(time_ms(torch, s.stream, solve) for _ in range(reps))
+    per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
+    out = {"n_dofs": si.n_dofs(spec.dim, spec.n, k), "setup_ms": t_setup, "time_to_tol_ms": t_solve,
+           "iters": its[0], "finest_variant": variant,
+           "value": per_cycle * its[0] / ((t_setup + t_solve) * 1e-3),
+           "smoother": smoother_report(s, spec, k, cfg, form, peak, torch)}
+    s.close()
+    return out
+
+
+def square256_report(peak: float, torch) -> dict:
+    """Unit square 256x256 (5 levels, 16x16 coarse), Oseen, k = 1..4 (patches of 42..105
+    unknowns), local inverses in FP64, FP32 and BF16, outer FGMRES in FP64."""
+    cfg = si.WORKLOADS["square256"]
+    out = {"workload": "unit square 256x256 quads, 5 levels (coarse 16x16), Q2/P1disc, dG(k), Oseen at seeded "
+                       f"Fourier w, nu={cfg['nu']}, tau={cfg['tau']}, Dirichlet on all faces, V(2,2), FGMRES to 1e-8"}
+    for k in (1, 2, 3, 4):
+        for form in ("f64", "f32", "bf16"):
+            out[f"k{k}_{form}"] = workload_line("square256", k, form, peak, torch)
+    return out
+
+
+def cube48_report(peak: float, torch) -> dict:
+    """Unit cube 48^3 (levels 6^3 .. 48^3), Oseen, dG(1) (170 x 170 local matrices), FP32 local
+    inverses and V-cycle, FP64 outer FGMRES."""
+    cfg = si.WORKLOADS["cube48_k1"]
+    out = {"workload": "unit cube 48^3 hexes, 4 levels (coarse 6^3), Q2/P1disc, dG(1), Oseen at seeded "
+                       f"divergence-free w, nu={cfg['nu']}, tau={cfg['tau']}, Dirichlet on all faces, V(2,2), "
+                       "FGMRES to 1e-8"}
+    out["k1_f32"] = workload_line("cube48_k1", 1, "f32", peak, torch)
+    # robustness in the time degree (Sec. 4 runs dG(0..2) in 3D): the 32^3 cube keeps the k = 2
+    # operators (9 x 9 FP64 node blocks) within memory
+    for k in (0, 1, 2):
+        out[f"cube32_k{k}_f32"] = workload_line("cube32", k, "f32", peak, torch)
+    return out
 
 
 def batch_report() -> dict:
@@ -431,6 +630,45 @@ def batch_report() -> dict:
             "iters_f64": its64, "all_converged": bool(ok_b)}
 
 
+def obstacle_march_report(slabs: int | None = None) -> dict:
+    """Newton time march on the channel with an obstacle (the structured stand-in for the flow
+    around an obstacle of Sec. 4): from rest with the Poiseuille inflow switched on at t = 0,
+    dG(k) for k = 0..4, FP32 form, the paper's absolute tolerances (Newton 1e-8, GMRES 1e-9).
+    Reports the mean Newton steps per slab and GMRES iterations per Newton step (the statistics
+    of Tables 3.1 and 3.2) and the drag and lift coefficients at the end of the march."""
+    import torch
+    from paper_2210_02690_gb300.march import March, summary
+
+    cfg = si.OBSTACLE
+    spec = cfg["spec"]
+    n_slabs = cfg["slabs"] if slabs is None else slabs
+    box = spec.obstacle_cells(0)
+    h0 = ((spec.hi[0] - spec.lo[0]) / spec.cells(0)[0], (spec.hi[1] - spec.lo[1]) / spec.cells(0)[1])
+    diameter = (box[3] - box[2]) * h0[1]
+    u_mean = 2.0 * cfg["u_max"] / 3.0
+    out = {"workload": f"channel [0,2.2]x[0,0.41], {spec.n[0]}x{spec.n[1]} quads, {spec.n_levels} levels, "
+                       f"obstacle of {box[1] - box[0]}x{box[3] - box[2]} coarse cells around (0.2, 0.2) "
+                       f"(D = {diameter:.4f}), nu = {cfg['nu']}, Poiseuille inflow U_max = {cfg['u_max']} "
+                       f"(Re = U_mean D / nu = {u_mean * diameter / cfg['nu']:.0f}), tau = {cfg['tau']}, "
+                       f"{n_slabs} slabs from rest; FP32 form; Newton 1e-8, GMRES 1e-9 absolute"}
+    for k in range(5):
+        m = March(spec, k, cfg["nu"], cfg["tau"], np.zeros(2 * np.prod([2 * c + 1 for c in spec.n])),
+                  si.obstacle_inflow(spec, k, cfg["u_max"]), vcycle_prec="f32", factor_prec="f32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.run(n_slabs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sm = summary(m.stats)
+        F = m.solver.obstacle_forces(m.X[-1])
+        c = 2.0 * F[-1] / (u_mean ** 2 * diameter)
+        out[f"k{k}"] = {"dofs_per_slab": int(m.N), "mean_newton": sm["mean_newton"],
+                        "mean_gmres_per_newton": sm["mean_gmres_per_newton"], "seconds": wall,
+                        "c_drag_end": float(c[0]), "c_lift_end": float(c[1])}
+        m.close()
+    return out
+
+
 def warm_start_report() -> dict:
     """Time march with the learned warm start (2D channel 128x32, dG(1), 400 slabs; network
     trained on slabs 1-200, every slab 201-400 solved from three guesses to the absolute
@@ -459,6 +697,22 @@ def warm_start_report() -> dict:
                                               "max_final_over_tol", "all_converged")}
     out["gmres_iters_saved_vs_fallback"] = 1.0 - out["network"]["gmres_iters"] / out["fallback"]["gmres_iters"]
     out["time_to_tol_speedup_vs_fallback"] = out["fallback"]["seconds"] / out["network"]["seconds"]
+    keys = ("newton_steps", "gmres_iters", "mean_r0", "seconds", "max_final_over_tol", "all_converged")
+    eval_slabs = list(range(cfg["train_slabs"], cfg["slabs"]))
+    # the plain FP64 form (FP64 local inverses and V-cycle) from the fallback guess: the method
+    # without reduced precision and without the learned part, on the same slabs and tolerances
+    f64 = m.companion_solver(vcycle_prec="f64", factor_prec="f64")
+    ev64 = m.evaluate(eval_slabs, net, sv, solver=f64, names=("fallback",))
+    f64.close()
+    out["plain_f64_fallback"] = {key: summary(ev64["fallback"])[key] for key in keys}
+    out["time_to_tol_speedup_warm_f32_vs_plain_f64"] = out["plain_f64_fallback"]["seconds"] / out["network"]["seconds"]
+    # a tighter regime in which the guesses differ in cost: Newton to 1e-10, GMRES to 1e-11 absolute
+    tight = m.companion_solver(vcycle_prec="f32", factor_prec="f32", gmres_atol=1e-11)
+    evt = m.evaluate(eval_slabs, net, sv, solver=tight, atol=1e-10)
+    tight.close()
+    out["tight"] = {"tolerances": "Newton absolute 1e-10, GMRES absolute 1e-11, FP32 form"}
+    for name, rows in evt.items():
+        out["tight"][name] = {key: summary(rows)[key] for key in keys}
     net.close()
     m.close()
     return out
@@ -500,6 +754,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start report")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve report")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the lines of the 256x256 square (k = 1..4) and the 48^3 cube")
     ap.add_argument("--colour-variants", default=None, metavar="F32;F64;BF16",
                     help="skip the autotuner and set the colour-kernel variants of levels 1.. per form, "
                          "e.g. '11,11,11;4,4,4;11,11,11' (the 'variants' a plain run reports), for "

@@ -61,13 +61,22 @@ enum { STG_F64 = 0, STG_F32 = 1, STG_BF16 = 2 };        /* storage/arithmetic pr
  * n/2^(n_levels-1-l) cells per direction, so every n must be divisible by
  * 2^(n_levels-1).  Bit 2*dir+side of dirichlet_faces marks a Dirichlet face
  * (side 0 = low, 1 = high); the other faces carry the do-nothing condition
- * (Sec. 1). */
+ * (Sec. 1).
+ * obstacle (2D only): the cells [obstacle[0], obstacle[1]) x [obstacle[2],
+ * obstacle[3]) of the COARSEST level (and their children on every finer level)
+ * are removed from the domain, a structured stand-in for the obstacle of the
+ * benchmark of Sec. 4; the faces of the remaining cells that border it carry
+ * Dirichlet data (Nitsche's method, Eq. (2.1)).  The unknowns left without an
+ * equation (velocity at Q2 nodes of removed cells only, pressure of removed
+ * cells) keep their place in the vectors with identity rows; solutions are zero
+ * there for zero right-hand sides.  All four zero: no obstacle. */
 typedef struct {
   int dim;                 /* 2 or 3 */
   int nx, ny, nz;          /* finest-level cells (nz ignored for dim = 2) */
   int n_levels;            /* >= 1; level 0 is solved directly */
   double x0, x1, y0, y1, z0, z1;
   unsigned dirichlet_faces;
+  int obstacle[4];         /* x_lo, x_hi, y_lo, y_hi in coarsest-level cells (2D)  */
 } stg_mesh;
 
 typedef struct {
@@ -84,9 +93,10 @@ typedef struct {
   double gmres_atol;       /* (defaults 1e-8 and 0; the paper's absolute 1e-9: set    */
                            /*  rtol = 0, atol = 1e-9)                                  */
   int use_graph;           /* capture the V-cycle in a CUDA graph (default 1)         */
-  int coarse_refine;       /* FP32 V-cycle with FP32 coarse factors: each coarse      */
-                           /* solve adds this many steps of iterative refinement      */
-                           /* with FP64 residuals (default 1)                         */
+  int coarse_refine;       /* steps of iterative refinement with FP64 residuals      */
+                           /* after each coarse solve (default 1): with FP32 coarse   */
+                           /* factors, and in the FP64 V-cycle (whose explicit block  */
+                           /* inverses it brings to the accuracy of an LU solve)      */
   int coarse_prec;         /* FP32 V-cycle only: precision of the coarse factors,     */
                            /* STG_F32 (default; refined as above) or STG_F64 (one    */
                            /* FP64 solve per cycle, no refinement, but an FP64       */
@@ -116,6 +126,17 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
 /* Re-assembles and re-factors every level for a new linearisation velocity w
  * (same layout as in stg_setup); allocates nothing. */
 stg_status stg_update_linearisation(stg_ctx* ctx, const double* w);
+
+/* Changes the slab length tau = t_n - t_{n-1} of the context (Sec. 4 marches with
+ * tau_n = 0.1, 0.05, 0.01; Eq. (2.2) integrates every spatial term of slab I_n with
+ * the weights tau w_a).  Re-assembles the w-independent part of every level and
+ * re-linearises every level at the current linearisation velocity (the last one
+ * given to stg_setup / stg_update_linearisation, or the last Newton iterate after
+ * stg_newton_slab); allocates nothing.  tau must be finite and >= 0 (STG_EINVAL
+ * otherwise).  tau = 0 leaves every local J_K without its pressure coupling and
+ * returns STG_ESINGULAR with the cell id in stg_last_error; the context stays
+ * usable and a later call with tau > 0 restores it. */
+stg_status stg_set_slab_length(stg_ctx* ctx, double tau);
 
 /* y = J x on the finest level (Eq. (3.3)); x, y DEVICE doubles of length N. */
 stg_status stg_apply_jacobian(stg_ctx* ctx, const double* x, double* y);
@@ -169,6 +190,16 @@ stg_status stg_newton_slab(stg_ctx* ctx, const double* v_prev, const double* f, 
                            double rtol, double atol, int maxit, int* newton_steps, int* gmres_iters,
                            double* residual);
 
+/* Drag and lift (Sec. 4 reports drag and lift coefficients of the flow around the
+ * obstacle, from surface integrals of the stress): the force of the fluid on the
+ * obstacle of the mesh at every Radau node a of slab vector X (DEVICE, C-ABI order),
+ *   F_a = - int_S (nu grad v_h - p_h I) n dS,
+ * S the obstacle's faces, n the unit normal of the fluid domain (pointing into the
+ * obstacle), v_h and p_h from the fluid cells next to S, 3-point Gauss rule per face.
+ * forces: HOST doubles [k+1][2] = (F_x, F_y) per Radau node (drag, lift; the
+ * coefficients are 2 F / (U_mean^2 D)).  STG_EINVAL without an obstacle. */
+stg_status stg_obstacle_forces(stg_ctx* ctx, const double* X, double* forces);
+
 /* X0 = the previous slab's end value (the last Radau-node block of X_prev, velocity
  * and pressure) repeated at every Radau node: the initial guess of the next slab.
  * DEVICE vectors of length N in the C-ABI order. */
@@ -203,9 +234,10 @@ long long stg_kernel_launches(void);
 
 /* Allocation-free batched inverse of caller-supplied dense matrices.  (The
  * paper has no counterpart: it is a service for callers that cannot allocate
- * device memory when they need local inverses -- code running while a CUDA
- * stream is captured into a graph, hosts that hand out device memory only
- * from their own arenas, loops that forbid allocation after start-up.)
+ * device memory when they need local inverses -- host applications that own
+ * the GPU's memory and hand it out only from their own pools or arenas, and
+ * real-time loops that forbid cudaMalloc/cudaFree after start-up because those
+ * calls may synchronise the device and take unbounded time.)
  *   n       matrix order, 1 <= n <= 256 (else STG_EINVAL with a message)
  *   count   number of matrices (0 is a no-op)
  *   a       DEVICE doubles [count][n][n], row-major, caller-owned, read only
@@ -213,12 +245,14 @@ long long stg_kernel_launches(void);
  *           (Gauss-Jordan with partial pivoting), zeros for a singular matrix
  *   stream  cudaStream_t for the work; the call synchronises it
  * Needs no context and allocates nothing: the working copies live in one
- * 8 MiB array compiled into the library, which every GPU that loads the
- * library holds until the process exits.  The first call on a device looks up
- * that array's device address; make it before any stream capture.  All calls
- * share the array, so calls that overlap on the GPU (other streams or host
- * threads) race.  Returns STG_ESINGULAR (index of the first singular matrix in
- * stg_last_error(NULL)) or STG_ECUDA on failure. */
+ * 8 MiB array compiled into the library (2^20 doubles, so one launch takes
+ * at most 2^20 / n^2 matrices and larger counts run in several launches),
+ * which every GPU that loads the library holds until the process exits.  The
+ * first call on a device looks up that array's device address.  All calls
+ * share the array and keep the last call's contents, so calls that overlap on
+ * the GPU (other streams or host threads) race.  Returns STG_ESINGULAR (the
+ * lowest index of a matrix with a zero pivot in stg_last_error(NULL)) or
+ * STG_ECUDA on failure. */
 stg_status stg_invert_local_noalloc(int n, long long count, const double* a, double* a_inv, void* stream);
 
 /* Autotuner: times every variant of the smoother's colour kernel (one warp per

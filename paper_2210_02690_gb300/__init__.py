@@ -25,11 +25,12 @@ STG_VANKA_AVERAGED, STG_VANKA_COLOURED = 0, 1
 STG_F64, STG_F32, STG_BF16 = 0, 1, 2
 PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16}
 
-EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg_apply_jacobian",
+EXPORTED = ("stg_options_default", "stg_setup", "stg_update_linearisation", "stg_set_slab_length",
+            "stg_apply_jacobian",
             "stg_apply_level_jacobian", "stg_vcycle", "stg_smooth", "stg_prolongate", "stg_restrict",
             "stg_coarse_solve", "stg_gmres_solve", "stg_get_sizes", "stg_get_local_inverse", "stg_profile",
             "stg_profile_read", "stg_kernel_launches", "stg_invert_local_noalloc", "stg_newton_slab",
-            "stg_slab_initial_guess", "stg_autotune", "stg_set_wait_limit", "stg_get_colour_variant",
+            "stg_slab_initial_guess", "stg_obstacle_forces", "stg_autotune", "stg_set_wait_limit", "stg_get_colour_variant",
             "stg_set_colour_variant",
             "stg_batch_create", "stg_batch_gmres_solve",
             "stg_batch_destroy", "stg_cnn_create", "stg_cnn_n_params", "stg_cnn_set_params",
@@ -48,7 +49,7 @@ class stg_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("z0", ctypes.c_double),
-                ("z1", ctypes.c_double), ("dirichlet_faces", ctypes.c_uint)]
+                ("z1", ctypes.c_double), ("dirichlet_faces", ctypes.c_uint), ("obstacle", ctypes.c_int * 4)]
 
 
 class stg_options(ctypes.Structure):
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_setup": (I, [ctypes.POINTER(stg_mesh), I, D, D, P, ctypes.POINTER(stg_options), P,
                           ctypes.POINTER(P)]),
         "stg_update_linearisation": (I, [P, P]),
+        "stg_set_slab_length": (I, [P, D]),
         "stg_apply_jacobian": (I, [P, P, P]),
         "stg_apply_level_jacobian": (I, [P, I, P, P]),
         "stg_vcycle": (I, [P, P, P]),
@@ -98,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "stg_invert_local_noalloc": (I, [I, LL, P, P, P]),
         "stg_newton_slab": (I, [P, P, P, P, P, D, D, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
         "stg_slab_initial_guess": (I, [P, P, P]),
+        "stg_obstacle_forces": (I, [P, P, P]),
         "stg_autotune": (I, [P, ctypes.POINTER(I), ctypes.POINTER(D)]),
         "stg_set_wait_limit": (I, [LL]),
         "stg_get_colour_variant": (I, [P, I, ctypes.POINTER(I)]),
@@ -136,8 +139,9 @@ def make_mesh(spec) -> stg_mesh:
     n = list(spec.n) + [1] * (3 - len(spec.n))
     lo = list(spec.lo) + [0.0] * (3 - len(spec.lo))
     hi = list(spec.hi) + [1.0] * (3 - len(spec.hi))
+    ob = tuple(getattr(spec, "obstacle", ()) or (0, 0, 0, 0))
     return stg_mesh(spec.dim, n[0], n[1], n[2], spec.n_levels, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2],
-                    spec.dirichlet)
+                    spec.dirichlet, (ctypes.c_int * 4)(*ob))
 
 
 def make_options(**kw) -> stg_options:
@@ -238,6 +242,11 @@ class Solver:
         w = self._dev(w)
         self._call(self.lib.stg_update_linearisation, self._p(w))
 
+    def set_slab_length(self, tau: float):
+        """New slab length tau; every level is re-assembled at the current linearisation velocity."""
+        self._call(self.lib.stg_set_slab_length, float(tau))
+        self.tau = tau
+
     def apply_jacobian(self, x, level: int = -1):
         level = self.spec.n_levels - 1 if level < 0 else level
         x = self._dev(x)
@@ -306,6 +315,13 @@ class Solver:
         X0 = self.torch.empty_like(Xp)
         self._call(self.lib.stg_slab_initial_guess, self._p(Xp), self._p(X0))
         return X0
+
+    def obstacle_forces(self, X) -> np.ndarray:
+        """(k+1, 2) force of the fluid on the obstacle (drag, lift) at every Radau node of X."""
+        Xd = self._dev(X)
+        out = np.zeros((self.k + 1, 2))
+        self._call(self.lib.stg_obstacle_forces, self._p(Xd), out.ctypes.data_as(ctypes.c_void_p))
+        return out
 
     # -- learned warm start of the next slab (2D)
     def node_grid(self):

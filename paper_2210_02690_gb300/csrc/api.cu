@@ -41,6 +41,9 @@ Geom make_geom(const stg_mesh& m, int level, int k) {
     }
   }
   g.dirichlet = m.dirichlet_faces;
+  const int fo = 1 << level;  // the obstacle box is given in coarsest-level cells
+  for (int i = 0; i < 4; ++i) g.ob[i] = m.obstacle[i] * fo;
+  if (g.ob[1] <= g.ob[0] || g.ob[3] <= g.ob[2]) g.ob[0] = g.ob[1] = g.ob[2] = g.ob[3] = 0;
   g.NV = g.nt * g.dim;
   g.NP = g.nt * (g.dim + 1);
   g.nloc = g.dim == 2 ? 9 : 27;
@@ -445,15 +448,26 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
   }
 }
 
-// x = J_0^{-1} b on FP64 vectors.  FP64 form: the FP64 factors.  FP32 form: the
-// FP32 factors followed by coarse_refine steps of iterative refinement with the
-// residual b - J_0 x computed in FP64.
+// x = J_0^{-1} b on FP64 vectors: the factors (FP64, or FP32 in the FP32 form) followed by
+// coarse_refine steps of iterative refinement with the residual b - J_0 x computed in FP64
+// (FP64 factors are refined only in the FP64 V-cycle).
 void coarse_solve64(stg_ctx* c, const double* b, double* x) {
+  const LevelBufs& L = c->lv[0];
   if (coarse64(c)) {
     c->coarse64.solve(b, x, c->st);
+    // The FP64 V-cycle refines its FP64 solve as well: the block cyclic reduction applies
+    // explicit block inverses, whose forward error grows with cond(block) (observed relative
+    // residuals around 5e-14 against about 1e-16 for an LU solve); each step with the FP64
+    // residual brings the solve back to LU accuracy.  FP64 factors under the FP32 V-cycle
+    // are used as they are.
+    if (vc64(c))
+      for (int it = 0; it < c->opt.coarse_refine; ++it) {
+        apply64(c, L, x, b, c->cr64);
+        c->coarse64.solve(c->cr64, c->cd64, c->st);
+        axpby(L.g.N, 1.0, c->cd64, 1.0, x, c->st);
+      }
     return;
   }
-  const LevelBufs& L = c->lv[0];
   c->coarse32.solve(b, x, c->st);
   for (int it = 0; it < c->opt.coarse_refine; ++it) {
     apply64(c, L, x, b, c->cr64);
@@ -817,6 +831,15 @@ stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
   const double lo[3] = {m->x0, m->y0, m->z0}, hi[3] = {m->x1, m->y1, m->z1};
   for (int e = 0; e < m->dim; ++e)
     if (!(hi[e] > lo[e])) throw Error{STG_EINVAL, "empty domain"};
+  const int* ob = m->obstacle;
+  if (ob[0] || ob[1] || ob[2] || ob[3]) {
+    const int nc0[2] = {m->nx / f, m->ny / f};
+    if (m->dim != 2) throw Error{STG_EINVAL, "an obstacle is supported in 2D only"};
+    if (!(0 <= ob[0] && ob[0] < ob[1] && ob[1] <= nc0[0] && 0 <= ob[2] && ob[2] < ob[3] && ob[3] <= nc0[1]))
+      throw Error{STG_EINVAL, "obstacle box outside the coarsest level's cells or empty"};
+    if (ob[1] - ob[0] == nc0[0] || ob[3] - ob[2] == nc0[1])
+      throw Error{STG_EINVAL, "an obstacle may not cut the domain in two"};
+  }
   if (o->vcycle_prec == STG_F64 && o->factor_prec != STG_F64)
     throw Error{STG_EINVAL, "an FP64 V-cycle needs FP64 local inverses"};
   if (o->vcycle_prec == STG_F32 && o->factor_prec == STG_F64)
@@ -997,6 +1020,46 @@ stg_status stg_update_linearisation(stg_ctx* c, const double* w) {
   if (!c || !w) return STG_EINVAL;
   try {
     linearise(c, w);
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_obstacle_forces(stg_ctx* c, const double* X, double* forces) {
+  if (!c || !X || !forces) return STG_EINVAL;
+  try {
+    const Geom& g = c->lv.back().g;
+    if (!has_obstacle(g)) throw Error{STG_EINVAL, "the mesh has no obstacle"};
+    cabi_to_internal<double>(g, X, c->tmp_a, c->st);
+    obstacle_forces(g, c->nu, c->tmp_a, c->hd, c->st);
+    STG_CUDA_OK(cudaMemcpyAsync(c->hh, c->hd, sizeof(double) * 2 * g.nt, cudaMemcpyDeviceToHost, c->st));
+    STG_CUDA_OK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < 2 * g.nt; ++i) forces[i] = c->hh[i];
+    return STG_OK;
+  } catch (const Error& e) {
+    return fail(c, e);
+  }
+}
+
+stg_status stg_set_slab_length(stg_ctx* c, double tau) {
+  if (!c) return STG_EINVAL;
+  if (!(tau >= 0.0) || !std::isfinite(tau)) {
+    c->err = "slab length must be finite and >= 0";
+    return STG_EINVAL;
+  }
+  try {
+    // tau scales every spatial term of D_ab and the velocity-pressure blocks: the
+    // w-independent part of every level is assembled again, then the levels are
+    // re-linearised at the current w (the last one set or left by the Newton iteration)
+    c->tau = tau;
+    const AsmCoef cf0{c->nu, tau, c->opt.gamma1, c->opt.gamma2, 0};
+    for (LevelBufs& L : c->lv) {
+      assemble_level(L.g, c->td, cf0, nullptr, L.rowptr, L.asm_tab, L.vv, L.nnzb, L.vp, L.pv, c->st);
+      STG_CUDA_OK(cudaMemcpyAsync(L.vconst, L.vv, sizeof(double) * L.nnzb * L.g.NV * L.g.NV,
+                                  cudaMemcpyDeviceToDevice, c->st));
+    }
+    linearise_internal(c);
     return STG_OK;
   } catch (const Error& e) {
     return fail(c, e);

@@ -63,12 +63,18 @@ __device__ __forceinline__ void basis_at(const Geom& g, const int* p, int i, dou
 // Face class of a cell: bit 2e set when the cell lies on a Dirichlet face
 // x_e = low, bit 2e+1 for x_e = high.  On a uniform box every w-independent
 // element matrix depends only on this class.
+// With an obstacle (2D) the faces of a remaining cell that border a removed cell are Dirichlet
+// faces as well.
 template <int DIM>
 __device__ __forceinline__ unsigned face_class(const Geom& g, const int* cc) {
   unsigned faces = 0;
   for (int e = 0; e < DIM; ++e) {
     if (cc[e] == 0 && (g.dirichlet >> (2 * e) & 1u)) faces |= 1u << (2 * e);
     if (cc[e] == g.n[e] - 1 && (g.dirichlet >> (2 * e + 1) & 1u)) faces |= 1u << (2 * e + 1);
+    if (DIM == 2) {
+      if (face_on_obstacle(g, cc[0], cc[1], e, 0)) faces |= 1u << (2 * e);
+      if (face_on_obstacle(g, cc[0], cc[1], e, 1)) faces |= 1u << (2 * e + 1);
+    }
   }
   return faces;
 }
@@ -284,6 +290,17 @@ __global__ void __launch_bounds__(256) assemble_cells(Geom g, int colour, TimeDa
   patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
   const int cc[3] = {cx, cy, cz};
   const long long cell = cell_id(g, cx, cy, cz);
+  if (DIM == 2 && cell_masked(g, cx, cy)) {
+    // a removed cell carries no element matrices (uniform over the block: safe early return)
+    if (!WONLY) {
+      const int nvp0 = NL * nt * DIM * (DIM + 1);
+      for (int t = threadIdx.x; t < nvp0; t += blockDim.x) {
+        vp[cell * nvp0 + t] = 0.0;
+        pv[cell * nvp0 + t] = 0.0;
+      }
+    }
+    return;
+  }
   const unsigned cls = face_class<DIM>(g, cc);
   const double* mass = tab;
   const double* cvv = tab + NL * NL + (long long)cls * tab_class_size(DIM, NL);
@@ -524,6 +541,7 @@ __global__ void __launch_bounds__(256) assemble_rhs(Geom g, int colour, TimeData
   patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
   const int cc[3] = {cx, cy, cz};
   const long long cell = cell_id(g, cx, cy, cz);
+  if (DIM == 2 && cell_masked(g, cx, cy)) return;  // removed cell: no data terms (b is zeroed)
   const unsigned cls = face_class<DIM>(g, cc);
   const double* nb = rt + (long long)cls * (ND * ND + (DIM + 1) * ND);
   const double* pb = nb + ND * ND;
@@ -554,6 +572,18 @@ __global__ void __launch_bounds__(256) assemble_rhs(Geom g, int colour, TimeData
     for (int J = 0; J < ND; ++J) s += pb[m * ND + J] * gl[(J / DIM) * NV + a * DIM + J % DIM];
     b[g.nvel + cell * g.NP + t] = cf.tau * td.w[a] * s;
   }
+}
+
+// Identity rows of the unknowns without an equation (obstacle): I added to the diagonal block
+// of every Q2 node of removed cells only (the pressure of removed cells is handled by the
+// residual and the patch inversion, as the velocity-pressure blocks carry no diagonal).
+__global__ void dead_node_identity(Geom g, const int* __restrict__ rowptr, double* __restrict__ vv) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n_nodes) return;
+  const int ix = (int)(node % g.nn[0]), iy = (int)(node / g.nn[0]);
+  if (!node_dead(g, ix, iy)) return;
+  const long long slot = bcsr_slot(g, rowptr, ix, iy, 0, ix, iy, 0);
+  for (int r = 0; r < g.NV; ++r) vv[(slot * g.NV + r) * g.NV + r] += 1.0;
 }
 
 }  // namespace
@@ -591,6 +621,10 @@ void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const 
       assemble_cells<3, false><<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, tab, K, vv, vp, pv);
     STG_LAUNCH_OK();
   }
+  if (has_obstacle(g)) {
+    dead_node_identity<<<grid_for(g.n_nodes, 256), 256, 0, st>>>(g, rowptr, vv);
+    STG_LAUNCH_OK();
+  }
 }
 
 void assemble_level_w(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
@@ -613,6 +647,78 @@ void assemble_level_w(const Geom& g, const TimeData& td, const AsmCoef& cf, cons
 }  // namespace stg
 
 namespace stg {
+
+namespace {
+
+// Force of the fluid on the obstacle (2D) at every Radau node,
+//   F_a = - sum over the faces of remaining cells that border the obstacle of
+//         int_F (nu grad v_h - p_h I) n dS        (n: the fluid cell's outward normal),
+// with the 3-point Gauss rule per face.  One CTA; each thread takes (face, Radau node) tasks
+// and the partial sums are reduced in shared memory in a fixed order.
+__global__ void __launch_bounds__(256) obstacle_forces_kernel(Geom g, double nu, const double* __restrict__ x,
+                                                            double* __restrict__ out) {
+  constexpr int NL = 9;
+  __shared__ double part[256][2 * 5];
+  const int tid = threadIdx.x, nt = g.nt, NV = g.NV;
+  double acc[2 * 5];
+  for (int i = 0; i < 2 * 5; ++i) acc[i] = 0.0;
+  // faces: (e, side, fixed cell index along e, range along the other direction)
+  const int nf0 = g.ob[3] - g.ob[2], nf1 = g.ob[1] - g.ob[0];
+  const int nfaces = 2 * nf0 + 2 * nf1;
+  for (int task = tid; task < nfaces * nt; task += blockDim.x) {
+    const int f = task / nt, a = task % nt;
+    int cx, cy, e, side;
+    if (f < nf0) {  // left of the obstacle: the cell's high-x face
+      e = 0; side = 1; cx = g.ob[0] - 1; cy = g.ob[2] + f;
+    } else if (f < 2 * nf0) {  // right of it: the low-x face
+      e = 0; side = 0; cx = g.ob[1]; cy = g.ob[2] + f - nf0;
+    } else if (f < 2 * nf0 + nf1) {  // below: the high-y face
+      e = 1; side = 1; cx = g.ob[0] + f - 2 * nf0; cy = g.ob[2] - 1;
+    } else {  // above: the low-y face
+      e = 1; side = 0; cx = g.ob[0] + f - 2 * nf0 - nf1; cy = g.ob[3];
+    }
+    if (cx < 0 || cx >= g.n[0] || cy < 0 || cy >= g.n[1]) continue;  // obstacle on the domain boundary
+    const double nrm = side ? 1.0 : -1.0;
+    const long long cell = cell_id(g, cx, cy, 0);
+    const double* pc = x + g.nvel + cell * g.NP + a * 3;
+    for (int fq = 0; fq < 3; ++fq) {
+      int pidx[3] = {0, 0, 0};
+      const double wt = face_point<2>(g, e, side, fq, pidx);
+      double gv[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+      for (int i = 0; i < NL; ++i) {
+        double v, gr[3];
+        basis_at<2>(g, pidx, i, v, gr);
+        const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + i / 3, 0);
+        for (int c = 0; c < 2; ++c) {
+          const double vi = x[nd * NV + a * 2 + c];
+          gv[c][0] += gr[0] * vi;
+          gv[c][1] += gr[1] * vi;
+        }
+      }
+      // P1disc {1, xi, eta} at the face point
+      const double xi = c_X[pidx[0]], eta = c_X[pidx[1]];
+      const double p = pc[0] + pc[1] * xi + pc[2] * eta;
+      for (int c = 0; c < 2; ++c) {
+        const double trac = nu * gv[c][e] * nrm - (c == e ? p * nrm : 0.0);
+        acc[2 * a + c] -= wt * trac;
+      }
+    }
+  }
+  for (int i = 0; i < 2 * 5; ++i) part[tid][i] = acc[i];
+  __syncthreads();
+  if (tid < 2 * nt) {
+    double sum = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) sum += part[t][tid];
+    out[tid] = sum;
+  }
+}
+
+}  // namespace
+
+void obstacle_forces(const Geom& g, double nu, const double* x_int, double* out, cudaStream_t st) {
+  obstacle_forces_kernel<<<1, 256, 0, st>>>(g, nu, x_int, out);
+  STG_LAUNCH_OK();
+}
 
 long long rhs_table_doubles(int dim) {
   const long long nd = (long long)(dim == 2 ? 9 : 27) * dim;

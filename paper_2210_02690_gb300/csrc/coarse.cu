@@ -15,6 +15,11 @@
 // constant-pressure null vector per Radau node; the pressure coefficient 0 of
 // cell 0 is then fixed to zero at every Radau node (its row and column become
 // identity rows), which yields the solution with that value for consistent b.
+// An obstacle (2D) splits the cell columns it crosses into a piece below and a
+// piece above it; each piece's interior block has its own constant-pressure null
+// vector, so the cell-constant coefficient of the first cell above the obstacle
+// joins V_s as well (a second group of nt slots in every vertex plane, identity
+// rows where unused); removed cells' pressures are identity rows.
 #include <algorithm>
 #include <vector>
 
@@ -335,6 +340,11 @@ struct Cls {
   int loc;
 };
 
+// First cell above the obstacle in a cell column the obstacle crosses (2D).
+__host__ __device__ __forceinline__ bool piece_start(const Geom& g, int col, long long row) {
+  return has_obstacle(g) && col >= g.ob[0] && col < g.ob[1] && row == g.ob[3] && g.ob[3] < g.n[1];
+}
+
 __device__ __forceinline__ Cls classify(const Geom& g, int mV, long long t) {
   Cls c;
   const long long pn = (long long)g.nn[1] * g.nn[2];
@@ -360,6 +370,9 @@ __device__ __forceinline__ Cls classify(const Geom& g, int mV, long long t) {
     if (cr == 0 && m == 0) {
       c.type = 0;
       c.loc = (int)(pn * g.NV + a);
+    } else if (m == 0 && piece_start(g, c.slab, cr)) {
+      c.type = 0;
+      c.loc = (int)(pn * g.NV + g.nt + a);
     } else if (cr == 0) {
       c.type = 1;
       c.loc = (int)(pn * g.NV + a * g.dim + m - 1);
@@ -471,6 +484,34 @@ __global__ void pin_diag(CoarseView<T> v) {
   if (v.pin) v.D[loc * mV + loc] = (T)1;
 }
 
+// Obstacle: identity rows for the pressures of removed cells, for the second pressure group of
+// vertex planes whose cell column has no piece above the obstacle, and for the interior slot left
+// by each moved coefficient.  One thread per (plane or cell, Radau node).
+template <typename T>
+__global__ void obstacle_diag(CoarseView<T> v) {
+  const Geom& g = v.g;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long pn = (long long)g.nn[1] * g.nn[2];
+  const long long mV = v.mV, mI = v.mI;
+  if (t < (long long)v.nsv * g.nt) {
+    const int s = (int)(t / g.nt), a = (int)(t % g.nt);
+    const bool used = s < v.nsi && piece_start(g, s, g.ob[3]);
+    const long long loc = pn * g.NV + g.nt + a;
+    if (!used) v.D[((long long)s * mV + loc) * mV + loc] = (T)1;
+    if (used) {
+      // the moved coefficient's own slot in I_s (cell row ob[3] >= 1, coefficient 0)
+      const long long il = pn * g.NV + (long long)g.nt * g.dim + (g.ob[3] - 1) * g.NP + a * (g.dim + 1);
+      v.AII[((long long)s * mI + il) * mI + il] = (T)1;
+    }
+  }
+  const long long u = t;
+  if (u < g.n_cells * g.NP) {
+    const long long cell = u / g.NP;
+    const int cx = (int)(cell % g.n[0]), cy = (int)(cell / g.n[0]);
+    if (cell_masked(g, cx, cy)) put(v, g.nvel + u, g.nvel + u, 1.0);
+  }
+}
+
 // D[t] -= C[t-1](lower right) + C[t](upper left); U[t] -= C[t](upper right); L[t+1] -= C[t](lower left)
 template <typename T>
 __global__ void schur_combine(CoarseView<T> v, const T* __restrict__ C) {
@@ -545,7 +586,7 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   v.nsi = geom.n[0];
   v.nsv = geom.n[0] + 1;
   const long long pn = (long long)geom.nn[1] * geom.nn[2];
-  v.mV = (int)(pn * geom.NV + geom.nt);
+  v.mV = (int)(pn * geom.NV + (has_obstacle(geom) ? 2 : 1) * geom.nt);
   v.mI = (int)(pn * geom.NV + (long long)geom.n[1] * geom.n[2] * geom.NP - geom.nt);
   const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
   auto alloc = [&](T** p, long long n) {
@@ -810,6 +851,11 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
   STG_LAUNCH_OK();
   pin_diag<T><<<1, 32, 0, st>>>(v);
   STG_LAUNCH_OK();
+  if (has_obstacle(g)) {
+    const long long n_ob = std::max<long long>((long long)nsv * g.nt, g.n_cells * g.NP);
+    obstacle_diag<T><<<grid_for(n_ob, 256), 256, 0, st>>>(v);
+    STG_LAUNCH_OK();
+  }
   // interiors: A_II^{-1}, W = A_II^{-1} A_IV, C = A_VI W, S = A_VV - C (scattered)
   gj<T>((int)mI, d_AII, (int)nsi, v.status, gj_scr, gj_perm, gj_fail, st);
   const T one = 1, zero = 0, mone = -1;

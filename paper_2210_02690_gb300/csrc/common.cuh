@@ -38,6 +38,9 @@ struct Geom {
   // cells of each colour: count per direction and offset of the colour's first patch
   int ccount[8][3];
   long long coff[9];
+  // removed cells (2D obstacle) in this level's cell indices: [ob[0], ob[1]) x [ob[2], ob[3]);
+  // empty (ob[1] <= ob[0]) without an obstacle
+  int ob[4];
 };
 
 Geom make_geom(const stg_mesh& m, int level, int k);
@@ -107,8 +110,58 @@ __host__ __device__ __forceinline__ long long patch_dof(const Geom& g, int cx, i
   }
   return g.nvel + cell_id(g, cx, cy, cz) * g.NP + (mu - vel);
 }
-// Number of cells sharing Q2 node (ix,iy,iz): the static multiplicity p of (S2).
+// ------------------------------------------------------------------ obstacle (2D)
+__host__ __device__ __forceinline__ bool has_obstacle(const Geom& g) { return g.ob[1] > g.ob[0]; }
+__host__ __device__ __forceinline__ bool cell_masked(const Geom& g, int cx, int cy) {
+  return cx >= g.ob[0] && cx < g.ob[1] && cy >= g.ob[2] && cy < g.ob[3];
+}
+// Range of cell indices that contain Q2 node index i along one direction.
+__host__ __device__ __forceinline__ void node_cells(int i, int n, int& lo, int& hi) {
+  if (i & 1) {
+    lo = hi = (i - 1) / 2;
+  } else {
+    lo = i / 2 - 1 < 0 ? 0 : i / 2 - 1;
+    hi = i / 2 > n - 1 ? n - 1 : i / 2;
+  }
+}
+// Cells containing node (ix, iy): (fluid, removed) counts.
+__host__ __device__ __forceinline__ void node_cell_counts(const Geom& g, int ix, int iy, int& fluid, int& removed) {
+  int xl, xh, yl, yh;
+  node_cells(ix, g.n[0], xl, xh);
+  node_cells(iy, g.n[1], yl, yh);
+  fluid = removed = 0;
+  for (int cy = yl; cy <= yh; ++cy)
+    for (int cx = xl; cx <= xh; ++cx) {
+      if (cell_masked(g, cx, cy))
+        ++removed;
+      else
+        ++fluid;
+    }
+}
+// A Q2 node of removed cells only: its velocity has no equation (identity rows).
+__host__ __device__ __forceinline__ bool node_dead(const Geom& g, int ix, int iy) {
+  if (!has_obstacle(g)) return false;
+  int f, r;
+  node_cell_counts(g, ix, iy, f, r);
+  return f == 0;
+}
+// Face (e, side) of a remaining cell borders the obstacle.
+__host__ __device__ __forceinline__ bool face_on_obstacle(const Geom& g, int cx, int cy, int e, int side) {
+  if (!has_obstacle(g)) return false;
+  const int nx = cx + (e == 0 ? (side ? 1 : -1) : 0), ny = cy + (e == 1 ? (side ? 1 : -1) : 0);
+  if (nx < 0 || nx >= g.n[0] || ny < 0 || ny >= g.n[1]) return false;
+  return cell_masked(g, nx, ny);
+}
+
+// Number of cells sharing Q2 node (ix,iy,iz): the static multiplicity p of (S2).  With an
+// obstacle, the patches of the remaining cells smooth the nodes of the fluid domain, and a
+// node of removed cells only is smoothed by the patches of those cells.
 __host__ __device__ __forceinline__ int node_multiplicity(const Geom& g, int ix, int iy, int iz) {
+  if (has_obstacle(g)) {
+    int f, r;
+    node_cell_counts(g, ix, iy, f, r);
+    return f > 0 ? f : r;
+  }
   int m = 1;
   if (!(ix & 1) && ix > 0 && ix < g.nn[0] - 1) m *= 2;
   if (g.dim > 1 && !(iy & 1) && iy > 0 && iy < g.nn[1] - 1) m *= 2;

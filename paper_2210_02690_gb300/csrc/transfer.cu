@@ -7,7 +7,9 @@
 // -1/2 (+1/2) takes the coarse cell's nodal values with weights (3/8, 3/4,
 // -1/8) ((-1/8, 3/4, 3/8)); nodes on coarse nodes take weight 1.  A child
 // cell with offset s in {-1/2, +1/2}^d gets c0 + sum_e s_e c_e and c_e / 2.
-// Time nodes are not coarsened.
+// Time nodes are not coarsened.  With an obstacle (2D) the spaces are those of the fluid
+// domain: P is zero on the fine unknowns outside it (Q2 nodes of removed cells only, the
+// pressure of removed cells), and P^T leaves their residual out of the coarse problem.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -72,6 +74,7 @@ __global__ void prolong_vel(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __r
   const int v = (int)(t - node * NV);
   const int f[3] = {(int)(node % gf.nn[0]), (int)((node / gf.nn[0]) % gf.nn[1]),
                     (int)(node / ((long long)gf.nn[0] * gf.nn[1]))};
+  if (gf.dim == 2 && node_dead(gf, f[0], f[1])) return;
   int ix[3][3], n[3];
   VT w[3][3];
   for (int e = 0; e < 3; ++e) n[e] = prolong_1d<VT>(f[e], ix[e], w[e]);
@@ -92,6 +95,7 @@ __global__ void prolong_pres(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __
   const int q = (int)(t - K * gf.NP);
   const int a = q / (d + 1), m = q % (d + 1);
   const int f[3] = {(int)(K % gf.n[0]), (int)((K / gf.n[0]) % gf.n[1]), (int)(K / ((long long)gf.n[0] * gf.n[1]))};
+  if (d == 2 && cell_masked(gf, f[0], f[1])) return;
   const long long Kc = cell_id(gc, f[0] >> 1, f[1] >> 1, f[2] >> 1);
   const VT* c = xc + gc.nvel + Kc * gc.NP + a * (d + 1);
   VT val;
@@ -117,10 +121,13 @@ __global__ void restrict_vel(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __
   VT w[3][5];
   for (int e = 0; e < 3; ++e) n[e] = restrict_1d<VT>(c[e], gf.nn[e], ix[e], w[e]);
   VT acc = 0;
+  const bool obst = gf.dim == 2 && has_obstacle(gf);
   for (int z = 0; z < n[2]; ++z)
     for (int y = 0; y < n[1]; ++y)
-      for (int x = 0; x < n[0]; ++x)
+      for (int x = 0; x < n[0]; ++x) {
+        if (obst && node_dead(gf, ix[0][x], ix[1][y])) continue;
         acc += w[0][x] * w[1][y] * w[2][z] * rf[node_id(gf, ix[0][x], ix[1][y], ix[2][z]) * NV + v];
+      }
   bc[t] = acc;
 }
 
@@ -138,6 +145,7 @@ __global__ void restrict_pres(Geom gc, Geom gf, const VT* __restrict__ rf, VT* _
   for (int o = 0; o < nch; ++o) {
     const int fx = 2 * c[0] + (o & 1), fy = d > 1 ? 2 * c[1] + ((o >> 1) & 1) : 0;
     const int fz = d > 2 ? 2 * c[2] + ((o >> 2) & 1) : 0;
+    if (d == 2 && cell_masked(gf, fx, fy)) continue;  // removed child: P is zero there
     const VT* f = rf + gf.nvel + cell_id(gf, fx, fy, fz) * gf.NP + a * (d + 1);
     if (m == 0) {
       acc += f[0];

@@ -16,6 +16,25 @@
 namespace stg {
 namespace {
 
+// Factor of a removed cell's patch (obstacle, 2D): the projector onto the patch's unknowns without
+// an equation (velocity at Q2 nodes of removed cells only, the cell's pressure), whose rows are
+// the identity; the patch smooths only those.  1 at local entry mu when it is such an unknown.
+__device__ __forceinline__ bool patch_entry_dead(const Geom& g, int cx, int cy, int mu) {
+  const int vel = g.nloc * g.NV;
+  if (mu >= vel) return true;
+  const int i = mu / g.NV;
+  return node_dead(g, 2 * cx + i % 3, 2 * cy + i / 3);
+}
+template <typename FT>
+__device__ void write_patch_projector(const Geom& g, int cx, int cy, FT* out, int tid, int nth) {
+  const int n = g.npatch;
+  for (int t = tid; t < n * n; t += nth) {
+    const int col = t / n, row = t - col * n;
+    out[t] = cvt<FT>((row == col && patch_entry_dead(g, cx, cy, row)) ? 1.f : 0.f);
+  }
+}
+
+
 template <typename T>
 struct AccT { using type = T; };
 template <>
@@ -235,6 +254,10 @@ __global__ void __launch_bounds__(256) op_pres_rows(Geom g, const MT* __restrict
   const int cz = (int)(K / ((long long)g.n[0] * g.n[1]));
   const MT* row = pv + ((K * g.nt + a) * (DIM + 1) + m) * (long long)g.nloc * DIM;
   VT acc = 0;
+  if (DIM == 2 && cell_masked(g, cx, cy)) {  // removed cell: identity row
+    out[g.nvel + t] = b ? b[g.nvel + t] - x[g.nvel + t] : x[g.nvel + t];
+    return;
+  }
   for (int i = 0; i < g.nloc; ++i) {
     const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
     const VT* xv = x + nd * g.NV + a * DIM;
@@ -259,6 +282,10 @@ __global__ void __launch_bounds__(256) invert_kernel(Geom g, long long p0, const
   int cx, cy, cz;
   patch_cell(g, p, cx, cy, cz);
   const long long cell = cell_id(g, cx, cy, cz);
+  if (g.dim == 2 && cell_masked(g, cx, cy)) {  // removed cell: block-uniform early return
+    write_patch_projector(g, cx, cy, jinv + p * stride, threadIdx.x, blockDim.x);
+    return;
+  }
   extern __shared__ unsigned char smem_raw[];
   CT* A;
   CT* tail;
@@ -417,6 +444,10 @@ __global__ void __launch_bounds__(256) invert_warp_kernel(Geom g, const int* __r
     int cx, cy, cz;
     patch_cell(g, p, cx, cy, cz);
     const long long cell = cell_id(g, cx, cy, cz);
+    if (dim == 2 && cell_masked(g, cx, cy)) {  // removed cell: warp-uniform
+      write_patch_projector(g, cx, cy, jinv + p * stride, lane, 32);
+      continue;
+    }
     for (int t = lane; t < n * n; t += 32) A[t] = 0;
     __syncwarp();
     const int nvv = nloc * nloc * NV * NV;
@@ -545,11 +576,12 @@ __global__ void __launch_bounds__(N * PPB, N == 42 ? 6 : 1) invert_rows_kernel(G
   const int pl = threadIdx.x / N, row = threadIdx.x % N;
   for (long long p0 = (long long)blockIdx.x * PPB; p0 < g.n_cells; p0 += (long long)gridDim.x * PPB) {
     const long long p = p0 + pl;
-    const bool live = p < g.n_cells;
+    int cx = 0, cy = 0, cz = 0;
+    if (p < g.n_cells) patch_cell(g, p, cx, cy, cz);
+    const bool removed = p < g.n_cells && cell_masked(g, cx, cy);
+    const bool live = p < g.n_cells && !removed;
     float a[N];
     if (live) {
-      int cx, cy, cz;
-      patch_cell(g, p, cx, cy, cz);
       const long long cell = cell_id(g, cx, cy, cz);
       if (row < VOFF) {
         const int i = row / NV, v = row % NV, ta = v / DIM, c = v % DIM;
@@ -648,6 +680,222 @@ __global__ void __launch_bounds__(N * PPB, N == 42 ? 6 : 1) invert_rows_kernel(G
 #pragma unroll
         for (int col = 0; col < N; ++col) out[col * N + row] = cvt<FT>(a[col] * csr * s_rs[pl][col]);
       }
+    } else if (removed) {
+      FT* out = jinv + p * stride;
+      const float one = patch_entry_dead(g, cx, cy, row) ? 1.f : 0.f;
+      for (int col = 0; col < N; ++col) out[col * N + row] = cvt<FT>(col == row ? one : 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+// Row r of the 2D local matrix J_K (local order: time node, 9 Q2 nodes x 2 components,
+// then the 3 P1disc coefficients per time node), gathered from the block-CSR velocity
+// blocks and the per-cell velocity-pressure blocks and rounded to FP32.
+template <int N, typename MT>
+__device__ __forceinline__ void gather_patch_row(const Geom& g, const int* __restrict__ rowptr,
+                                                 const MT* __restrict__ vv, const MT* __restrict__ vp,
+                                                 const MT* __restrict__ pv, int cx, int cy, long long cell,
+                                                 int row, float (&a)[N]) {
+  constexpr int DIM = 2, NL = 9, NT = N / 21, NV = NT * DIM, NP = NT * (DIM + 1), VOFF = NL * NV;
+  if (row < VOFF) {
+    const int i = row / NV, v = row % NV, ta = v / DIM, c = v % DIM;
+    const int ix = 2 * cx + i % 3, iy = 2 * cy + i / 3;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const long long slot = bcsr_slot(g, rowptr, ix, iy, 0, 2 * cx + j % 3, 2 * cy + j / 3, 0);
+      const MT* b = vv + slot * NV * NV + v * NV;
+#pragma unroll
+      for (int s2 = 0; s2 < NV; ++s2) a[j * NV + s2] = (float)b[s2];
+    }
+    const MT* q = vp + (((cell * NL + i) * NT + ta) * DIM + c) * (DIM + 1);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) a[VOFF + m] = (m / (DIM + 1) == ta) ? (float)q[m % (DIM + 1)] : 0.f;
+  } else if (row < N) {
+    const int qq = row - VOFF, ta = qq / (DIM + 1), m = qq % (DIM + 1);
+    const MT* q = pv + ((cell * NT + ta) * (DIM + 1) + m) * (long long)NL * DIM;
+#pragma unroll
+    for (int col = 0; col < VOFF; ++col) {
+      const int j = col / NV, s2 = col % NV;
+      a[col] = (s2 / DIM == ta) ? (float)q[j * DIM + s2 % DIM] : 0.f;
+    }
+#pragma unroll
+    for (int m2 = 0; m2 < NP; ++m2) a[VOFF + m2] = 0.f;
+  } else {
+#pragma unroll
+    for (int l = 0; l < N; ++l) a[l] = 0.f;  // padding row of an odd N
+  }
+}
+
+// Entries 4 l4 .. 4 l4 + 3 of a register row as a float4 (zeros past the end).
+template <int N>
+__device__ __forceinline__ float4 pack4(const float (&x)[N], int l4) {
+  float v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * l4 + u;
+    v[u] = i < N ? x[i < N ? i : N - 1] : 0.f;
+  }
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// One step of the rotated Gauss-Jordan elimination of invert_pairs_kernel for the two rows
+// (x, y) of a thread.  The pivot row is read unscaled from shared memory as float4 (raw[0] the
+// pivot); every row, the pivot row included, takes x[c - 1] = x[c] - (fx / pivot) raw[c]: with
+// fx = pivot - 1 the pivot row becomes x / pivot (up to about eps max(1, |pivot|)), so no row
+// needs a select per entry and the pivot row needs no scaling pass before the barrier.  ex = 1 on
+// the pivot row supplies the new last column, 1 / pivot.
+template <int N>
+__device__ __forceinline__ void pairs_update(float (&x)[N], float (&y)[N], const float* raw, float fx, float fy,
+                                             float ex, float ey) {
+  constexpr int NR = (N + 3) / 4 * 4;
+  const float inv = 1.f / raw[0];
+  const float gx = fx * inv, gy = fy * inv;
+#pragma unroll
+  for (int l4 = 0; l4 < NR / 4; ++l4) {
+    const float4 q = reinterpret_cast<const float4*>(raw)[l4];
+    const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = 4 * l4 + u;
+      if (c >= 1 && c < N) {
+        x[c - 1] = fmaf(-gx, qv[u], x[c]);
+        y[c - 1] = fmaf(-gy, qv[u], y[c]);
+      }
+    }
+  }
+  x[N - 1] = fmaf(-fx, inv, ex);
+  y[N - 1] = fmaf(-fy, inv, ey);
+}
+
+// Register-resident variant for 2D patches with two rows per thread (rows 2t and 2t + 1;
+// (N + 1) / 2 threads per patch, PPB patches per CTA): each pivot-row value read from shared
+// memory feeds two FMAs, and the pivot row needs no per-entry select, so a step costs about
+// half the instructions of invert_rows_kernel per row.  Same method: Gauss-Jordan without row
+// interchanges on the equilibrated J_K, columns rotated so that the pivot column is always
+// register 0, a pivot below 1e-3 flags the patch for the pivoting kernel.
+template <int N, int PPB, typename MT, typename FT>
+__global__ void __launch_bounds__(((N + 1) / 2) * PPB, 6)
+    invert_pairs_kernel(Geom g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
+                        const MT* __restrict__ vp, const MT* __restrict__ pv, FT* __restrict__ jinv,
+                        long long stride, int* __restrict__ flags) {
+  constexpr int TP = (N + 1) / 2;
+  constexpr int NR = (N + 3) / 4 * 4;
+  static_assert(N % 2 == 0, "two rows per thread: even patch size");
+  __shared__ float s_abs[PPB][N][N + 1];
+  __shared__ __align__(16) float s_row[2][PPB][NR];
+  __shared__ float s_cs[PPB][N];
+  __shared__ float s_rs[PPB][N];
+  __shared__ int s_bad[PPB];
+  const int pl = threadIdx.x / TP, t = threadIdx.x % TP;
+  const int r0 = 2 * t, r1 = 2 * t + 1;
+  for (long long p0 = (long long)blockIdx.x * PPB; p0 < g.n_cells; p0 += (long long)gridDim.x * PPB) {
+    const long long p = p0 + pl;
+    int cx = 0, cy = 0, cz = 0;
+    if (p < g.n_cells) patch_cell(g, p, cx, cy, cz);
+    const bool removed = p < g.n_cells && cell_masked(g, cx, cy);
+    const bool live = p < g.n_cells && !removed;
+    float a[N], b[N];
+    if (live) {
+      const long long cell = cell_id(g, cx, cy, cz);
+      gather_patch_row<N, MT>(g, rowptr, vv, vp, pv, cx, cy, cell, r0, a);
+      gather_patch_row<N, MT>(g, rowptr, vv, vp, pv, cx, cy, cell, r1, b);
+    } else {
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        a[l] = r0 == l ? 1.f : 0.f;  // identity keeps idle threads harmless
+        b[l] = r1 == l ? 1.f : 0.f;
+      }
+    }
+    // equilibration: row scales, then column scales through a transposed copy
+    float ma = 0.f, mb = 0.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      ma = fmaxf(ma, fabsf(a[l]));
+      mb = fmaxf(mb, fabsf(b[l]));
+    }
+    const float rsa = ma > 0.f ? 1.f / ma : 1.f, rsb = mb > 0.f ? 1.f / mb : 1.f;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      a[l] *= rsa;
+      b[l] *= rsb;
+      s_abs[pl][l][r0] = fabsf(a[l]);
+      s_abs[pl][l][r1] = fabsf(b[l]);
+    }
+    s_rs[pl][r0] = rsa;
+    s_rs[pl][r1] = rsb;
+    if (t == 0) s_bad[pl] = 0;
+    __syncthreads();
+    {
+      float c0 = 0.f, c1 = 0.f;
+#pragma unroll 6
+      for (int r = 0; r < N; ++r) {
+        c0 = fmaxf(c0, s_abs[pl][r0][r]);
+        c1 = fmaxf(c1, s_abs[pl][r1][r]);
+      }
+      s_cs[pl][r0] = c0 > 0.f ? 1.f / c0 : 1.f;
+      s_cs[pl][r1] = c1 > 0.f ? 1.f / c1 : 1.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      a[l] *= s_cs[pl][l];
+      b[l] *= s_cs[pl][l];
+    }
+    // two elimination steps per iteration: step j takes its pivot from row a (j even) or
+    // b (j odd) of thread j / 2, so the pivot row is a compile-time register array.  The
+    // pivot row of step j goes to buffer j & 1 unscaled (one barrier per step, as in
+    // invert_rows_kernel); each thread scales by the pivot itself.  The loop stays rolled:
+    // the rotation x[c - 1] = f(x[c]) keeps every array element in its own register.
+    for (int j = 0; j < N; j += 2) {
+      const bool own = t == (j >> 1);
+      {
+        float* sr = s_row[0][pl];
+        if (own) {
+          if (!(fabsf(a[0]) > 1e-3f) || isinf(a[0])) s_bad[pl] = 1;
+#pragma unroll
+          for (int l4 = 0; l4 < NR / 4; ++l4)
+            reinterpret_cast<float4*>(sr)[l4] = pack4<N>(a, l4);
+        }
+        __syncthreads();
+        const float fa = own ? a[0] - 1.f : a[0];
+        pairs_update<N>(a, b, sr, fa, b[0], own ? 1.f : 0.f, 0.f);
+      }
+      {
+        float* sr = s_row[1][pl];
+        if (own) {
+          if (!(fabsf(b[0]) > 1e-3f) || isinf(b[0])) s_bad[pl] = 1;
+#pragma unroll
+          for (int l4 = 0; l4 < NR / 4; ++l4)
+            reinterpret_cast<float4*>(sr)[l4] = pack4<N>(b, l4);
+        }
+        __syncthreads();
+        const float fb = own ? b[0] - 1.f : b[0];
+        pairs_update<N>(a, b, sr, a[0], fb, 0.f, own ? 1.f : 0.f);
+      }
+    }
+    __syncthreads();
+    if (live) {
+      if (s_bad[pl]) {
+        if (t == 0) flags[p] = 1;
+      } else {
+        // J_K^{-1} = Dc A'^{-1} Dr, column-major: element (row, col) at col * N + row
+        FT* out = jinv + p * stride;
+        const float ca = s_cs[pl][r0], cb = s_cs[pl][r1];
+#pragma unroll
+        for (int col = 0; col < N; ++col) {
+          const float rc = s_rs[pl][col];
+          out[col * N + r0] = cvt<FT>(a[col] * ca * rc);
+          out[col * N + r1] = cvt<FT>(b[col] * cb * rc);
+        }
+      }
+    } else if (removed) {
+      FT* out = jinv + p * stride;
+      const float o0 = patch_entry_dead(g, cx, cy, r0) ? 1.f : 0.f, o1 = patch_entry_dead(g, cx, cy, r1) ? 1.f : 0.f;
+      for (int col = 0; col < N; ++col) {
+        out[col * N + r0] = cvt<FT>(col == r0 ? o0 : 0.f);
+        out[col * N + r1] = cvt<FT>(col == r1 ? o1 : 0.f);
+      }
     }
     __syncthreads();
   }
@@ -728,12 +976,22 @@ __global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, c
 // iteration limit; a CTA that reaches it raises g_colour_timeout, waits (again with a
 // limit) for its own copies still in flight, and returns.
 
+// 1: a wait for a factor copy reached its limit; 2: in addition, a copy already in flight
+// had not landed when its drain wait gave up (the CTA then returned with it pending).
 __device__ int g_colour_timeout;
 
 constexpr long long kBarrierSpins = 1LL << 22;
-// limit of the waits for a patch's factor (read at run time, so graph replays see changes);
-// the waits for copies still in flight after giving up always use kBarrierSpins
+// limit of the waits for a patch's factor (read at run time, so graph replays see changes;
+// 0 makes every such wait give up at once)
 __device__ long long g_colour_wait_spins = kBarrierSpins;
+// Limit of the drain waits after giving up.  A bulk copy that has been issued always lands
+// unless the context has already faulted, and a CTA that returned before its copies landed
+// would leave them writing into shared memory that the next CTA on the SM may own.  So the
+// drain wait does not depend on the fault-injection limit above: it backs off with
+// __nanosleep and gives up only after about 2^24 sleeps of up to 1 us (tens of seconds),
+// a bound no healthy copy comes near; it stays finite so that no wait in this kernel is
+// unbounded.
+constexpr long long kDrainSleeps = 1LL << 24;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -750,6 +1008,24 @@ __device__ __forceinline__ bool barrier_wait(unsigned bar, unsigned phase, long 
         : "r"(bar), "r"(phase)
         : "memory");
     if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool drain_wait(unsigned bar, unsigned phase) {
+  unsigned ns = 32;
+  for (long long i = 0; i < kDrainSleeps; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
   }
   return false;
 }
@@ -822,7 +1098,7 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
         atomicExch(&g_colour_timeout, 1);
         for (int j = it; j < it + S - 1; ++j) {
           if (first + (long long)j * step >= cnt) break;
-          barrier_wait(smem_u32(bar + (j % S)), (unsigned)((j / S) & 1), kBarrierSpins);
+          if (!drain_wait(smem_u32(bar + (j % S)), (unsigned)((j / S) & 1))) atomicExch(&g_colour_timeout, 2);
         }
       }
       __syncthreads();
@@ -955,11 +1231,11 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     };
     if (vv32) {
       if (n == 21) run(invert_rows_kernel<21, 8, float, FT>, 8, 21 * 8, vv32, vp32, pv32);
-      else if (n == 42) run(invert_rows_kernel<42, 2, float, FT>, 2, 42 * 2, vv32, vp32, pv32);
+      else if (n == 42) run(invert_pairs_kernel<42, 3, float, FT>, 3, 21 * 3, vv32, vp32, pv32);
       else run(invert_rows_kernel<63, 2, float, FT>, 2, 63 * 2, vv32, vp32, pv32);
     } else {
       if (n == 21) run(invert_rows_kernel<21, 8, double, FT>, 8, 21 * 8, vv, vp, pv);
-      else if (n == 42) run(invert_rows_kernel<42, 2, double, FT>, 2, 42 * 2, vv, vp, pv);
+      else if (n == 42) run(invert_pairs_kernel<42, 3, double, FT>, 3, 21 * 3, vv, vp, pv);
       else run(invert_rows_kernel<63, 2, double, FT>, 2, 63 * 2, vv, vp, pv);
     }
     only = flags;
@@ -1028,12 +1304,11 @@ bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, 
   const size_t smem = 128 + bulk_rl_bytes<VT>(2 * n) + (size_t)S * stage_bytes;
   const int threads = (n + 31) / 32 * 32;
   if (smem > 200 * 1024 || threads > 1024) return false;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    STG_CUDA_OK(cudaGetDevice(&dev));
-    STG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+  // queried per launch (a host-side attribute read): contexts on different devices may share
+  // this process
+  int sms = 0, dev = 0;
+  STG_CUDA_OK(cudaGetDevice(&dev));
+  STG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (smem > 48 * 1024)
     STG_CUDA_OK(cudaFuncSetAttribute(vanka_colour_bulk_kernel<VT, FT, S>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

@@ -33,7 +33,7 @@ class March:
 
         options = dict(dict(gmres_rtol=0.0, gmres_atol=GMRES_ATOL), **options)
         self.torch = torch
-        self.spec, self.k = spec, k
+        self.spec, self.k, self.nu, self.tau, self.v0 = spec, k, nu, tau, np.asarray(v0, dtype=np.float64)
         R = spec.dim * np.prod([2 * c + 1 for c in spec.n])
         self.R = int(R)
         w = np.tile(np.asarray(v0, dtype=np.float64), (k + 1, 1))
@@ -48,6 +48,14 @@ class March:
         self.X = [torch.from_numpy(X0.ravel()).cuda()]
         self.stats = []
 
+    def companion_solver(self, **options):
+        """Another context of the same slab problem (e.g. the plain FP64 form, or a tighter GMRES
+        tolerance) for evaluate(); it is re-linearised by every Newton step it takes."""
+        options = dict(dict(gmres_rtol=0.0, gmres_atol=GMRES_ATOL), **options)
+        w = np.tile(self.v0, (self.k + 1, 1))
+        return Solver(self.spec, self.k, self.nu, self.tau, self.torch.from_numpy(w.ravel()).cuda(),
+                      linearisation="newton", **options)
+
     def end_velocity(self, X):
         """View of the nodal velocities at the last Radau node (t_n) of a slab vector."""
         off = self.k * (self.R + self.S)
@@ -58,12 +66,13 @@ class March:
         _, _, _, res, _ = self.solver.newton_slab(X0, v_prev=self.end_velocity(self.X[n]), g=self.g, maxit=0)
         return res
 
-    def solve_slab(self, n, X0, rtol=0.0, atol=NEWTON_ATOL, maxit=20):
+    def solve_slab(self, n, X0, rtol=0.0, atol=NEWTON_ATOL, maxit=20, solver=None):
         """Slab n+1 from slab n and initial guess X0: (X, steps, GMRES its, ||F||, ok, seconds)."""
+        solver = self.solver if solver is None else solver
         self.torch.cuda.synchronize()
         t0 = time.perf_counter()
-        X, steps, its, res, ok = self.solver.newton_slab(X0, v_prev=self.end_velocity(self.X[n]), g=self.g,
-                                                         rtol=rtol, atol=atol, maxit=maxit)
+        X, steps, its, res, ok = solver.newton_slab(X0, v_prev=self.end_velocity(self.X[n]), g=self.g,
+                                                    rtol=rtol, atol=atol, maxit=maxit)
         self.torch.cuda.synchronize()
         return X, steps, its, res, ok, time.perf_counter() - t0
 
@@ -120,20 +129,23 @@ class March:
         self.torch.cuda.synchronize()
         return net, sv, losses, time.perf_counter() - t0
 
-    def evaluate(self, slabs, net, sv, maxit=20, atol=NEWTON_ATOL):
+    def evaluate(self, slabs, net, sv, maxit=20, atol=NEWTON_ATOL, solver=None,
+                 names=("fallback", "linear", "network")):
         """Solves slab n+1 for n in `slabs` from the fallback guess, the linear extrapolation and
-        the network's guess, all to the same absolute tolerance."""
-        out = {"fallback": [], "linear": [], "network": []}
+        the network's guess (those of `names`), all to the same absolute Newton tolerance.  The
+        solves run on `solver` (default: the march's own), e.g. a context of the same problem in
+        another precision form or with a tighter GMRES tolerance; the guesses are the same."""
+        out = {name: [] for name in names}
         for n in slabs:
             sd = self.scale_d(n)
-            guesses = {"fallback": self.solver.slab_initial_guess(self.X[n]),
-                       "linear": self.solver.warm_start(None, self.X[n], self.X[n - 1], sv, sd),
-                       "network": self.solver.warm_start(net, self.X[n], self.X[n - 1], sv, sd)}
-            tol = atol
-            for name, X0 in guesses.items():
+            make = {"fallback": lambda: self.solver.slab_initial_guess(self.X[n]),
+                    "linear": lambda: self.solver.warm_start(None, self.X[n], self.X[n - 1], sv, sd),
+                    "network": lambda: self.solver.warm_start(net, self.X[n], self.X[n - 1], sv, sd)}
+            for name in names:
+                X0 = make[name]()
                 r0 = self.initial_residual(n, X0)
-                X, steps, its, res, ok, sec = self.solve_slab(n, X0, rtol=0.0, atol=tol, maxit=maxit)
-                out[name].append(dict(slab=n + 1, r0=r0, tol=tol, steps=steps, its=its, res=res, ok=ok, sec=sec))
+                X, steps, its, res, ok, sec = self.solve_slab(n, X0, rtol=0.0, atol=atol, maxit=maxit, solver=solver)
+                out[name].append(dict(slab=n + 1, r0=r0, tol=atol, steps=steps, its=its, res=res, ok=ok, sec=sec))
         return out
 
     # -- checkpoint / resume

@@ -222,6 +222,39 @@ MARCH = dict(spec=MeshSpec(2, (128, 32), (0.0, 0.0), (2.2, 0.41), 4, FACE_XLO | 
              nu=1e-3, tau=0.005, slabs=400, train_slabs=200, pert=0.5, channels=(4, 16, 16, 4))
 
 
+# ---------------------------------------------------------------- channel with an obstacle
+# A structured stand-in for the benchmark of Sec. 4 (flow around an obstacle in a channel): the
+# channel [0, 2.2] x [0, 0.41] with a square of cells removed around (0.2, 0.2), no-slip on its
+# faces and on the walls, the Poiseuille profile at the inflow, do-nothing outflow.
+OBSTACLE = dict(spec=MeshSpec(2, (176, 32), (0.0, 0.0), (2.2, 0.41), 3, FACE_XLO | FACE_YLO | FACE_YHI,
+                              (3, 5, 3, 5)),
+                k=1, nu=1e-3, tau=0.01, u_max=1.5, slabs=40)
+
+
+def obstacle_node_mask(spec: MeshSpec, level: int | None = None) -> np.ndarray:
+    """(n_nodes,) bool: Q2 nodes of the level that belong to a removed cell (on the obstacle's
+    faces or inside it)."""
+    level = spec.n_levels - 1 if level is None else level
+    cells = spec.cells(level)
+    nn = [2 * c + 1 for c in cells]
+    out = np.zeros(nn[0] * nn[1], dtype=bool)
+    box = spec.obstacle_cells(level)
+    if not box:
+        return out
+    ix = np.arange(nn[0])
+    iy = np.arange(nn[1])
+    inx = (ix >= 2 * box[0]) & (ix <= 2 * box[1])
+    iny = (iy >= 2 * box[2]) & (iy <= 2 * box[3])
+    return (iny[:, None] & inx[None, :]).ravel()
+
+
+def obstacle_inflow(spec: MeshSpec, k: int, u_max: float = 1.5) -> np.ndarray:
+    """Dirichlet data (k+1, R): the Poiseuille profile, zero on the obstacle (no-slip)."""
+    g = channel_w(spec, k, u_max=u_max, pert=0.0)
+    g.reshape(k + 1, -1, spec.dim)[:, obstacle_node_mask(spec)] = 0.0
+    return g
+
+
 def march_initial_velocity(spec: MeshSpec, seed: int = BASE_SEED, pert: float = 0.5) -> np.ndarray:
     """v(0) at the finest Q2 nodes, (R,) in the C-ABI order."""
     return channel_w(spec, 0, seed=seed, pert=pert)[0].copy()

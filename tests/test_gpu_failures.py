@@ -61,3 +61,47 @@ def test_negative_wait_limit_is_rejected():
     from paper_2210_02690_gb300 import StgError, set_wait_limit
     with pytest.raises(StgError):
         set_wait_limit(-1)
+
+
+def test_singular_local_matrix_reports_cell_and_context_recovers():
+    """tau = 0 removes the pressure coupling of every local J_K (the velocity-pressure blocks carry
+    the factor tau w_a): stg_setup and stg_set_slab_length return STG_ESINGULAR with a cell id; the
+    live context is restored by a positive slab length and then matches the oracle again."""
+    from paper_2210_02690_gb300 import Solver, StgError
+    import oracle
+    w = si.channel_w(SPEC, 1)
+    for prec in (dict(), dict(vcycle_prec="f32", factor_prec="f32")):
+        with pytest.raises(StgError) as e:
+            Solver(SPEC, 1, 1e-3, 0.0, torch.from_numpy(w.ravel()).cuda(), nu1=2, nu2=2, **prec)
+        assert e.value.status == 4 and "cell" in str(e.value)
+    gpu, ref = _pair()
+    with pytest.raises(StgError) as e:
+        gpu.set_slab_length(0.0)
+    assert e.value.status == 4 and "cell" in str(e.value)
+    with pytest.raises(StgError) as e:
+        gpu.set_slab_length(float("nan"))
+    assert e.value.status == 1
+    gpu.set_slab_length(0.01)
+    b = ref.apply(si.reference_solution(SPEC, 1, seed=3))
+    x = gpu.vcycle(torch.from_numpy(b).cuda()).cpu().numpy()
+    x_ref = ref.vcycle(b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-12
+    gpu.close()
+    del oracle
+
+
+def test_fgmres_iteration_limit_reports_noconv_with_results_written():
+    """gmres_maxit = 1 at rtol 1e-14: STG_ENOCONV, with x (one preconditioned step) and the relative
+    residual written; the context keeps working."""
+    gpu, ref = _pair(gmres_maxit=1, gmres_rtol=1e-14)
+    b = ref.apply(si.reference_solution(SPEC, 1, seed=4))
+    bt = torch.from_numpy(b).cuda()
+    x, its, relres, ok = gpu.gmres_solve(bt)
+    assert not ok and its == 1
+    x = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - ref.apply(x)) / np.linalg.norm(b)
+    assert 1e-14 < relres < 1.0 and abs(relres - true_rel) <= 1e-6 * true_rel
+    assert "gmres_maxit" in gpu.lib.stg_last_error(gpu.ctx).decode()
+    x2, its2, rel2, ok2 = gpu.gmres_solve(bt, x0=torch.from_numpy(x).cuda())
+    assert not ok2 and rel2 < relres            # a restart from the returned x keeps improving
+    gpu.close()

@@ -51,3 +51,29 @@ def test_network_warm_start_beats_the_fallback(march):
     assert nw["mean_r0"] < 0.8 * lin["mean_r0"]
     assert nw["gmres_iters"] <= lin["gmres_iters"]
     net.close()
+
+
+def test_guesses_at_tight_tolerances_and_plain_f64(march):
+    """At Newton 1e-10 / GMRES 1e-11 absolute the initial guess decides how many GMRES iterations a
+    slab needs: the network's guess needs no more than the linear extrapolation and fewer than the
+    fallback; the warm-started FP32 form needs no more GMRES iterations than the plain FP64 form
+    solved from the fallback guess at the paper's tolerances."""
+    from paper_2210_02690_gb300.march import summary
+    cfg = si.MARCH
+    n_train = cfg["train_slabs"]
+    net, sv, _, _ = march.train(cfg["channels"], si.cnn_init(cfg["channels"]), list(range(2, n_train)))
+    slabs = list(range(n_train, n_train + 60))
+    tight = march.companion_solver(vcycle_prec="f32", factor_prec="f32", gmres_atol=1e-11)
+    ev = march.evaluate(slabs, net, sv, solver=tight, atol=1e-10)
+    tight.close()
+    s = {name: summary(rows) for name, rows in ev.items()}
+    for name, v in s.items():
+        assert v["all_converged"] and v["max_final_over_tol"] <= 1.0, name
+    assert s["network"]["gmres_iters"] <= s["linear"]["gmres_iters"]
+    assert s["network"]["gmres_iters"] < s["fallback"]["gmres_iters"]
+    f64 = march.companion_solver(vcycle_prec="f64", factor_prec="f64")
+    ev64 = march.evaluate(slabs, net, sv, solver=f64, names=("fallback",))
+    f64.close()
+    warm = march.evaluate(slabs, net, sv, names=("network",))
+    assert summary(warm["network"])["gmres_iters"] <= summary(ev64["fallback"])["gmres_iters"]
+    net.close()
