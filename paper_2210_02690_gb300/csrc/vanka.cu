@@ -276,9 +276,11 @@ __global__ void __launch_bounds__(256) invert_kernel(Geom g, long long p0, const
                                                      const double* __restrict__ vv,
                                                      const double* __restrict__ vp,
                                                      const double* __restrict__ pv, FT* __restrict__ jinv,
-                                                     long long stride, int* status, int equil, CT* scratch) {
+                                                     long long stride, int* status, int equil, CT* scratch,
+                                                     const int* __restrict__ only) {
   const int n = g.npatch, NV = g.NV, nloc = g.nloc, dim = g.dim, nt = g.nt;
   const long long p = p0 + blockIdx.x;
+  if (only && !only[p]) return;  // block-uniform: only the patches a pivot-free pass flagged
   int cx, cy, cz;
   patch_cell(g, p, cx, cy, cz);
   const long long cell = cell_id(g, cx, cy, cz);
@@ -901,6 +903,180 @@ __global__ void __launch_bounds__(((N + 1) / 2) * PPB, 6)
   }
 }
 
+// Entry (mu, nu) of J_K (internal local order: 3^d nodes x NV velocity values, node-major, then
+// the NP pressure values), gathered from the block-CSR velocity blocks and the per-cell
+// velocity-pressure blocks; 0 in the pressure-pressure block; the identity beyond n (padding).
+template <typename MT>
+__device__ __forceinline__ float patch_entry(const Geom& g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
+                                             const MT* __restrict__ vp, const MT* __restrict__ pv, int cx, int cy,
+                                             int cz, long long cell, int mu, int nu) {
+  const int n = g.npatch, NV = g.NV, dim = g.dim, nloc = g.nloc, vel = nloc * NV;
+  if (mu >= n || nu >= n) return mu == nu ? 1.f : 0.f;
+  if (mu < vel) {
+    const int i = mu / NV, v = mu - i * NV;
+    if (nu < vel) {
+      const int j = nu / NV, s2 = nu - j * NV;
+      const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9,
+                                       2 * cx + j % 3, 2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+      return (float)vv[(slot * NV + v) * NV + s2];
+    }
+    const int q = nu - vel, a = q / (dim + 1), m = q - a * (dim + 1);
+    const int ta = v / dim, c = v - ta * dim;
+    return ta == a ? (float)vp[(((cell * nloc + i) * g.nt + a) * dim + c) * (dim + 1) + m] : 0.f;
+  }
+  if (nu >= vel) return 0.f;
+  const int q = mu - vel, a = q / (dim + 1), m = q - a * (dim + 1);
+  const int j = nu / NV, s2 = nu - j * NV, tb = s2 / dim, e = s2 - tb * dim;
+  return tb == a ? (float)pv[((cell * g.nt + a) * (dim + 1) + m) * (long long)nloc * dim + j * dim + e] : 0.f;
+}
+
+// Register-tiled variant for the larger patches (2D k >= 2, 3D): one CTA per patch, the
+// (padded) NPAD x NPAD matrix spread over a T x T grid of threads (T = NPAD / B), each holding a
+// B x B tile in registers.  Gauss-Jordan without row interchanges on the equilibrated J_K (the
+// velocity unknowns come before the pressure unknowns, as in invert_rows_kernel); a pivot below
+// 1e-3 flags the patch for the pivoting kernel.  Step j = cb B + jj runs over column blocks cb
+// and, unrolled, their columns jj, so a thread's pivot-row and pivot-column registers are
+// compile-time indices: the threads of column block cb publish column j, those of row block cb
+// publish row j (unscaled), one barrier per step (double-buffered), then every thread applies
+//   a[r][c] -= (f_r / pivot) row[c]   (f_r = the row's entry in column j; pivot row: f = pivot - 1)
+// and the threads of column block cb write the new column j (-f_r / pivot; 1 / pivot on the pivot
+// row).  B x B FMAs per step read 2 B values from shared memory.
+template <int NPAD, int B, typename MT, typename FT>
+__global__ void __launch_bounds__((NPAD / B) * (NPAD / B), NPAD <= 64 ? 8 : (NPAD <= 88 ? 4 : (NPAD <= 112 ? 2 : 1)))
+    invert_tiles_kernel(Geom g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
+                        const MT* __restrict__ vp, const MT* __restrict__ pv, FT* __restrict__ jinv,
+                        long long stride, int* __restrict__ flags) {
+  constexpr int T = NPAD / B;
+  static_assert(NPAD % B == 0 && B % 4 == 0, "tile layout");
+  __shared__ __align__(16) float s_col[2][NPAD];
+  __shared__ __align__(16) float s_row[2][NPAD];
+  __shared__ float s_red[NPAD][T + 1];
+  __shared__ float s_rs[NPAD], s_cs[NPAD];
+  __shared__ int s_bad;
+  const int n = g.npatch;
+  const int tid = threadIdx.x, rg = tid % T, cg = tid / T;
+  const long long p = blockIdx.x;
+  int cx, cy, cz;
+  patch_cell(g, p, cx, cy, cz);
+  if (g.dim == 2 && cell_masked(g, cx, cy)) {  // removed cell: block-uniform early return
+    write_patch_projector(g, cx, cy, jinv + p * stride, tid, blockDim.x);
+    return;
+  }
+  const long long cell = cell_id(g, cx, cy, cz);
+  float a[B][B];
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) a[r][c] = patch_entry<MT>(g, rowptr, vv, vp, pv, cx, cy, cz, cell, rg * B + r, cg * B + c);
+  if (tid == 0) s_bad = 0;
+  // equilibration: row scales (max over the row, reduced over the thread columns), then column
+  // scales of the row-scaled matrix
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < B; ++c) mx = fmaxf(mx, fabsf(a[r][c]));
+    s_red[rg * B + r][cg] = mx;
+  }
+  __syncthreads();
+  for (int i = tid; i < NPAD; i += T * T) {
+    float mx = 0.f;
+    for (int t = 0; t < T; ++t) mx = fmaxf(mx, s_red[i][t]);
+    s_rs[i] = mx > 0.f ? 1.f / mx : 1.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const float rs = s_rs[rg * B + r];
+#pragma unroll
+    for (int c = 0; c < B; ++c) a[r][c] *= rs;
+  }
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < B; ++r) mx = fmaxf(mx, fabsf(a[r][c]));
+    s_red[cg * B + c][rg] = mx;
+  }
+  __syncthreads();
+  for (int i = tid; i < NPAD; i += T * T) {
+    float mx = 0.f;
+    for (int t = 0; t < T; ++t) mx = fmaxf(mx, s_red[i][t]);
+    s_cs[i] = mx > 0.f ? 1.f / mx : 1.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const float cs = s_cs[cg * B + c];
+#pragma unroll
+    for (int r = 0; r < B; ++r) a[r][c] *= cs;
+  }
+  for (int cb = 0; cb < T; ++cb) {
+    const bool colown = cg == cb, rowown = rg == cb;
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) {
+      const int j = cb * B + jj;
+      float* col = s_col[jj & 1];
+      float* row = s_row[jj & 1];
+      if (colown)
+#pragma unroll
+        for (int r4 = 0; r4 < B / 4; ++r4)
+          reinterpret_cast<float4*>(col + rg * B)[r4] =
+              make_float4(a[4 * r4][jj], a[4 * r4 + 1][jj], a[4 * r4 + 2][jj], a[4 * r4 + 3][jj]);
+      if (rowown)
+#pragma unroll
+        for (int c4 = 0; c4 < B / 4; ++c4)
+          reinterpret_cast<float4*>(row + cg * B)[c4] =
+              make_float4(a[jj][4 * c4], a[jj][4 * c4 + 1], a[jj][4 * c4 + 2], a[jj][4 * c4 + 3]);
+      __syncthreads();
+      const float piv = row[j];
+      if (tid == 0 && (!(fabsf(piv) > 1e-3f) || isinf(piv))) s_bad = 1;
+      const float inv = 1.f / piv;
+      float f[B], q[B];
+#pragma unroll
+      for (int r4 = 0; r4 < B / 4; ++r4) {
+        const float4 v = reinterpret_cast<const float4*>(col + rg * B)[r4];
+        f[4 * r4] = v.x;
+        f[4 * r4 + 1] = v.y;
+        f[4 * r4 + 2] = v.z;
+        f[4 * r4 + 3] = v.w;
+        const float4 w = reinterpret_cast<const float4*>(row + cg * B)[r4];
+        q[4 * r4] = w.x;
+        q[4 * r4 + 1] = w.y;
+        q[4 * r4 + 2] = w.z;
+        q[4 * r4 + 3] = w.w;
+      }
+#pragma unroll
+      for (int r = 0; r < B; ++r) {
+        const float gr = ((rowown && r == jj) ? f[r] - 1.f : f[r]) * inv;
+#pragma unroll
+        for (int c = 0; c < B; ++c) a[r][c] = fmaf(-gr, q[c], a[r][c]);
+      }
+      if (colown)
+#pragma unroll
+        for (int r = 0; r < B; ++r) a[r][jj] = (rowown && r == jj) ? inv : -f[r] * inv;
+    }
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) flags[p] = 1;
+    return;
+  }
+  // J_K^{-1} = Dc A'^{-1} Dr, column-major: element (row, col) at col * n + row
+  FT* out = jinv + p * stride;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const int colx = cg * B + c;
+    if (colx >= n) continue;
+    const float rc = s_rs[colx];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      const int rowx = rg * B + r;
+      if (rowx < n) out[(long long)colx * n + rowx] = cvt<FT>(a[r][c] * s_cs[rowx] * rc);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ smoother
 template <typename VT, typename FT, int RPL, int CB>
 __global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
@@ -1219,7 +1395,7 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
   STG_CUDA_OK(cudaGetDevice(&dev));
   STG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int* only = nullptr;
-  if (compute_f32 && g.dim == 2 && n <= 63 && flags) {
+  if (compute_f32 && g.dim == 2 && n <= 42 && flags) {
     // register-resident pivot-free pass, then the pivoting kernel for flagged patches only
     STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
     // one CTA per PPB patches (not a resident-capped grid): the set-up runs this beside other
@@ -1231,12 +1407,32 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     };
     if (vv32) {
       if (n == 21) run(invert_rows_kernel<21, 8, float, FT>, 8, 21 * 8, vv32, vp32, pv32);
-      else if (n == 42) run(invert_pairs_kernel<42, 3, float, FT>, 3, 21 * 3, vv32, vp32, pv32);
-      else run(invert_rows_kernel<63, 2, float, FT>, 2, 63 * 2, vv32, vp32, pv32);
+      else run(invert_pairs_kernel<42, 3, float, FT>, 3, 21 * 3, vv32, vp32, pv32);
     } else {
       if (n == 21) run(invert_rows_kernel<21, 8, double, FT>, 8, 21 * 8, vv, vp, pv);
-      else if (n == 42) run(invert_pairs_kernel<42, 3, double, FT>, 3, 21 * 3, vv, vp, pv);
-      else run(invert_rows_kernel<63, 2, double, FT>, 2, 63 * 2, vv, vp, pv);
+      else run(invert_pairs_kernel<42, 3, double, FT>, 3, 21 * 3, vv, vp, pv);
+    }
+    only = flags;
+  } else if (compute_f32 && flags && (n == 63 || n == 84 || n == 105 || n == 85 || n == 170)) {
+    // larger patches: register tiles, pivot-free, then the pivoting kernel for flagged patches
+    STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
+    auto tiles = [&](auto kern, int threads_t, auto* V, auto* VP, auto* PV) {
+      kern<<<(unsigned)g.n_cells, threads_t, 0, st>>>(g, rowptr, V, VP, PV, jinv, stride, flags);
+      STG_LAUNCH_OK();
+    };
+    const bool f32src = vv32 != nullptr;
+    if (n == 63) {
+      if (f32src) tiles(invert_tiles_kernel<64, 8, float, FT>, 64, vv32, vp32, pv32);
+      else tiles(invert_tiles_kernel<64, 8, double, FT>, 64, vv, vp, pv);
+    } else if (n == 84 || n == 85) {
+      if (f32src) tiles(invert_tiles_kernel<88, 8, float, FT>, 121, vv32, vp32, pv32);
+      else tiles(invert_tiles_kernel<88, 8, double, FT>, 121, vv, vp, pv);
+    } else if (n == 105) {
+      if (f32src) tiles(invert_tiles_kernel<112, 8, float, FT>, 196, vv32, vp32, pv32);
+      else tiles(invert_tiles_kernel<112, 8, double, FT>, 196, vv, vp, pv);
+    } else {
+      if (f32src) tiles(invert_tiles_kernel<176, 8, float, FT>, 484, vv32, vp32, pv32);
+      else tiles(invert_tiles_kernel<176, 8, double, FT>, 484, vv, vp, pv);
     }
     only = flags;
   }
@@ -1266,7 +1462,7 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
                                      (int)std::max<size_t>(full <= 200 * 1024 ? full : tail, 48 * 1024)));
     if (full <= 200 * 1024) {
       invert_kernel<CT, FT><<<(unsigned)g.n_cells, threads, full, st>>>(g, 0, rowptr, vv, vp, pv, jinv, stride,
-                                                                        status, compute_f32, (CT*)nullptr);
+                                                                        status, compute_f32, (CT*)nullptr, only);
       STG_LAUNCH_OK();
     } else {
       // matrix too large for shared memory: caller-provided global scratch, in chunks
@@ -1275,7 +1471,7 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
       for (long long p0 = 0; p0 < g.n_cells; p0 += chunk) {
         const long long cnt = g.n_cells - p0 < chunk ? g.n_cells - p0 : chunk;
         invert_kernel<CT, FT><<<(unsigned)cnt, threads, tail, st>>>(g, p0, rowptr, vv, vp, pv, jinv, stride,
-                                                                    status, compute_f32, (CT*)scratch);
+                                                                    status, compute_f32, (CT*)scratch, only);
         STG_LAUNCH_OK();
       }
     }
