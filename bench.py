@@ -718,6 +718,35 @@ def warm_start_report() -> dict:
     return out
 
 
+def setup_profile(args) -> None:
+    """One re-linearisation (assembly, local inverses, coarse factorisation) of a workload inside
+    the profiler range (`ncu --profile-from-start off`), after an untimed one."""
+    import torch
+
+    from paper_2210_02690_gb300 import Solver
+
+    cfg = si.WORKLOADS[args.setup_profile]
+    spec = cfg["spec"]
+    if args.scale > 1 or args.levels:
+        spec = si.scaled(spec, args.scale, args.levels or None)
+    k = cfg["k"]
+    w = torch.from_numpy(si.make_w(dict(cfg, spec=spec)).ravel()).cuda()
+    s = Solver(spec, k, cfg["nu"], cfg["tau"], w, nu1=cfg["nu1"], nu2=cfg["nu2"],
+               linearisation="newton" if cfg["newton"] else "oseen", **FORMS["f32"])
+    s.update_linearisation(w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record(s.stream)
+    s.update_linearisation(w)
+    e1.record(s.stream)
+    torch.cuda.profiler.stop()
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.setup_profile, "cells": list(spec.n), "levels": spec.n_levels,
+                      "setup_ms": e0.elapsed_time(e1)}), flush=True)
+    s.close()
+
+
 # ----------------------------------------------------------------------------- reference arm
 def reference_arm(args) -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -756,6 +785,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve report")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the lines of the 256x256 square (k = 1..4) and the 48^3 cube")
+    ap.add_argument("--setup-profile", default=None, metavar="WORKLOAD",
+                    help="profiler case: one untimed and one profiled re-linearisation (FP32 form) of a "
+                         "workload of stg_inputs.WORKLOADS (with --scale/--levels), then exit")
     ap.add_argument("--colour-variants", default=None, metavar="F32;F64;BF16",
                     help="skip the autotuner and set the colour-kernel variants of levels 1.. per form, "
                          "e.g. '11,11,11;4,4,4;11,11,11' (the 'variants' a plain run reports), for "
@@ -777,6 +809,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.setup_profile:
+        setup_profile(args)
     else:
         gpu_arm(args)
 

@@ -203,6 +203,139 @@ __global__ void __launch_bounds__(256) gj_update_kernel(int m, int j, T* const* 
   }
 }
 
+// Blocked Gauss-Jordan for the large blocks: the same pivots and operations as gj_pivot_kernel /
+// gj_update_kernel, arranged by panels of w columns [c0, c0 + w).  Within a panel every step
+// (first maximal pivot among the rows not yet used, row interchange, scaled pivot row, update)
+// runs on the m x w panel in shared memory; the other columns are updated once per panel:
+// with P the panel's pivot rows, Q the panel columns and C the others, w Gauss-Jordan steps turn
+// A_PC into A_PQ^{-1} A_PC and A_RC into A_RC - A_RQ A_PQ^{-1} A_PC, i.e.
+//   A[:, C] = [0 on rows P; A_RC] + panel_new A_PC_old,
+// one batched product (panel_new is the m x w panel after its steps: A_PQ^{-1} on rows P and
+// -A_RQ A_PQ^{-1} on the others).  3 launches per panel instead of 2 per column.
+template <typename T>
+__global__ void __launch_bounds__(1024) gjb_panel_kernel(int m, int c0, int w, T* const* As, T* const* Ps,
+                                                         int* __restrict__ perm, long long pstride,
+                                                         int* __restrict__ fail) {
+  const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  if (fail[b]) return;
+  T* A = As[b];
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  const int ld = w + 1;  // padded row stride: a panel column read across rows spreads over the banks
+  T* P = reinterpret_cast<T*>(sh_raw);
+  T* colj = P + (long long)m * ld;
+  __shared__ T s_best[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_pr, s_bad;
+  __shared__ T s_pv;
+  for (long long t = tid; t < (long long)m * w; t += nth) {
+    const int i = (int)(t / w), l = (int)(t - (long long)i * w);
+    P[i * ld + l] = A[(long long)i * m + c0 + l];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < w; ++jj) {
+    const int j = c0 + jj;
+    T best = -1;
+    int bi = m;
+    for (int i = j + tid; i < m; i += nth) {
+      const T v = fabs(P[i * ld + jj]);
+      if (v > best || (v == best && i < bi)) {
+        best = v;
+        bi = i;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const T ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if ((tid & 31) == 0) {
+      s_best[tid >> 5] = best;
+      s_idx[tid >> 5] = bi;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      best = tid < (nth >> 5) ? s_best[tid] : (T)-1;
+      bi = tid < (nth >> 5) ? s_idx[tid] : m;
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        const T pv = bi < m ? P[bi * ld + jj] : (T)0;
+        s_pr = bi;
+        s_pv = pv;
+        s_bad = (!(fabs(pv) > (T)0) || isinf(pv)) ? 1 : 0;
+        if (s_bad) fail[b] = 1;
+        perm[(long long)b * pstride + j] = bi;
+      }
+    }
+    __syncthreads();
+    if (s_bad) return;  // block-uniform; the matrix is reported by gj_unpermute_kernel
+    const int pr = s_pr;
+    if (pr != j)
+      for (int l = tid; l < w; l += nth) {
+        const T t = P[j * ld + l];
+        P[j * ld + l] = P[pr * ld + l];
+        P[pr * ld + l] = t;
+      }
+    __syncthreads();
+    const T inv = (T)1 / s_pv;
+    for (int i = tid; i < m; i += nth) colj[i] = P[i * ld + jj];
+    __syncthreads();
+    for (int l = tid; l < w; l += nth) P[j * ld + l] = (l == jj ? (T)1 : P[j * ld + l]) * inv;
+    __syncthreads();
+    for (long long t = tid; t < (long long)m * w; t += nth) {
+      const int i = (int)(t / w), l = (int)(t - (long long)i * w);
+      if (i == j) continue;
+      P[i * ld + l] = (l == jj ? (T)0 : P[i * ld + l]) - colj[i] * P[j * ld + l];
+    }
+    __syncthreads();
+  }
+  T* pn = Ps[b];
+  for (long long t = tid; t < (long long)m * w; t += nth) {
+    const int i = (int)(t / w), l = (int)(t - (long long)i * w);
+    const T v = P[i * ld + l];
+    A[(long long)i * m + c0 + l] = v;
+    pn[t] = v;
+  }
+}
+
+// The panel's row interchanges applied to the other columns (in order), then the pivot rows'
+// old values of the other columns saved (zero in the panel's own columns) and cleared in A.
+template <typename T>
+__global__ void __launch_bounds__(256) gjb_swap_save_kernel(int m, int c0, int w, T* const* As, T* const* Os,
+                                                            const int* __restrict__ perm, long long pstride,
+                                                            const int* __restrict__ fail) {
+  const int b = blockIdx.y;
+  if (fail[b]) return;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= m) return;
+  T* A = As[b];
+  T* O = Os[b];
+  const bool panel = l >= c0 && l < c0 + w;
+  if (!panel)
+    for (int t = 0; t < w; ++t) {
+      const int j = c0 + t, pr = perm[(long long)b * pstride + j];
+      if (pr != j) {
+        const T x = A[(long long)j * m + l];
+        A[(long long)j * m + l] = A[(long long)pr * m + l];
+        A[(long long)pr * m + l] = x;
+      }
+    }
+  for (int t = 0; t < w; ++t) {
+    T* a = A + (long long)(c0 + t) * m + l;
+    O[(long long)t * m + l] = panel ? (T)0 : *a;
+    if (!panel) *a = (T)0;
+  }
+}
+
 // columns swapped back (last interchange first); the status records the first failed matrix
 template <typename T>
 __global__ void __launch_bounds__(1024) gj_unpermute_kernel(int m, T* const* As, const int* __restrict__ perm,
@@ -611,6 +744,22 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
     owned.push_back(gj_perm);
     STG_CUDA_OK(cudaMalloc(&gj_fail, sizeof(int) * nb));
     owned.push_back(gj_fail);
+    if (mm >= 512) {
+      // blocked Gauss-Jordan scratch: panels of at most 32 columns (FP32) or 16 (FP64)
+      gjb.w = sizeof(T) == 4 ? 32 : 16;
+      gjb.m_max = mm;
+      gjb.batch_max = (int)nb;
+      T *pan = nullptr, *old = nullptr;
+      alloc(&pan, nb * mm * gjb.w);
+      alloc(&old, nb * mm * gjb.w);
+      std::vector<T*> hp(nb), ho(nb);
+      for (long long b = 0; b < nb; ++b) {
+        hp[b] = pan + b * mm * gjb.w;
+        ho[b] = old + b * mm * gjb.w;
+      }
+      gjb.panels = upload_ptrs(hp, owned);
+      gjb.olds = upload_ptrs(ho, owned);
+    }
   }
   alloc(&tV, nsv * mV);
   alloc(&xV, nsv * mV);
@@ -774,7 +923,12 @@ static bool rgj(int m, float* const* A, int batch, int* status, cudaStream_t st)
 static bool rgj(int, double* const*, int, int*, cudaStream_t) { return false; }
 
 template <typename T>
-static void gj(int m, T* const* A, int batch, int* status, T* scratch, int* perm, int* fail, cudaStream_t st) {
+static void gemm2(int M, int N, int K, T alpha, const T* const* A0, const T* const* B0, const T* const* A1,
+                  const T* const* B1, T beta, T* const* C, int batch, cudaStream_t st);
+
+template <typename T>
+static void gj(int m, T* const* A, int batch, int* status, T* scratch, int* perm, int* fail, const GjBlocked& blk,
+               cudaStream_t st) {
   if (batch <= 0 || m <= 0) return;
   if (rgj(m, A, batch, status, st)) return;
   const size_t tail = sizeof(T) * m + sizeof(int) * m;
@@ -794,12 +948,31 @@ static void gj(int m, T* const* A, int batch, int* status, T* scratch, int* perm
     return;
   }
   STG_CUDA_OK(cudaMemsetAsync(fail, 0, sizeof(int) * batch, st));
-  const dim3 ugrid((m + 31) / 32, (m + 31) / 32, batch);
-  for (int j = 0; j < m; ++j) {
-    gj_pivot_kernel<T><<<batch, 256, 0, st>>>(m, j, A, scratch, perm, fail);
-    STG_LAUNCH_OK();
-    gj_update_kernel<T><<<ugrid, 256, 0, st>>>(m, j, A, scratch, fail);
-    STG_LAUNCH_OK();
+  if (blk.panels && blk.m_max >= m && blk.batch_max >= batch) {
+    // blocked form: panels of w columns in shared memory, one batched product per panel
+    int w = blk.w;
+    while (w > 4 && ((size_t)m * (w + 1) + m) * sizeof(T) > 200 * 1024) w /= 2;
+    const size_t sm = ((size_t)m * (w + 1) + m) * sizeof(T);
+    STG_CUDA_OK(cudaFuncSetAttribute(gjb_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(sm, 48 * 1024)));
+    const dim3 sgrid((m + 255) / 256, batch);
+    for (int c0 = 0; c0 < m; c0 += w) {
+      const int wp = std::min(w, m - c0);
+      gjb_panel_kernel<T><<<batch, 1024, sm, st>>>(m, c0, wp, A, (T* const*)blk.panels, perm, m, fail);
+      STG_LAUNCH_OK();
+      gjb_swap_save_kernel<T><<<sgrid, 256, 0, st>>>(m, c0, wp, A, (T* const*)blk.olds, perm, m, fail);
+      STG_LAUNCH_OK();
+      gemm2<T>(m, m, wp, (T)1, (const T* const*)blk.panels, (const T* const*)blk.olds, nullptr, nullptr, (T)1, A,
+               batch, st);
+    }
+  } else {
+    const dim3 ugrid((m + 31) / 32, (m + 31) / 32, batch);
+    for (int j = 0; j < m; ++j) {
+      gj_pivot_kernel<T><<<batch, 256, 0, st>>>(m, j, A, scratch, perm, fail);
+      STG_LAUNCH_OK();
+      gj_update_kernel<T><<<ugrid, 256, 0, st>>>(m, j, A, scratch, fail);
+      STG_LAUNCH_OK();
+    }
   }
   gj_unpermute_kernel<T><<<batch, 1024, 0, st>>>(m, A, perm, fail, status);
   STG_LAUNCH_OK();
@@ -857,7 +1030,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
     STG_LAUNCH_OK();
   }
   // interiors: A_II^{-1}, W = A_II^{-1} A_IV, C = A_VI W, S = A_VV - C (scattered)
-  gj<T>((int)mI, d_AII, (int)nsi, v.status, gj_scr, gj_perm, gj_fail, st);
+  gj<T>((int)mI, d_AII, (int)nsi, v.status, gj_scr, gj_perm, gj_fail, gjb, st);
   const T one = 1, zero = 0, mone = -1;
   gemm2<T>((int)mI, (int)(2 * mV), (int)mI, one, d_AII, d_AIV, nullptr, nullptr, zero, d_W, (int)nsi, st);
   gemm2<T>((int)(2 * mV), (int)(2 * mV), (int)mI, one, d_AVI, d_W, nullptr, nullptr, zero, d_C, (int)nsi, st);
@@ -866,7 +1039,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
   // block cyclic reduction of the vertex-plane system
   const int m = (int)mV;
   for (const auto& lv : levels) {
-    gj<T>(m, lv.oD, lv.n_odd, v.status, gj_scr, gj_perm, gj_fail, st);
+    gj<T>(m, lv.oD, lv.n_odd, v.status, gj_scr, gj_perm, gj_fail, gjb, st);
     // [GL_i | GU_i] = D_i^{-1} [L_i | U_i]
     gemm2<T>(m, m, m, one, lv.gA, lv.gB, nullptr, nullptr, zero, lv.gC, 2 * lv.n_odd, st);
     // D_j -= L_j GU_{j-st} + U_j GL_{j+st}
@@ -874,7 +1047,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
     // L_j <- -L_j GL_{j-st}, U_j <- -U_j GU_{j+st}, into new blocks
     gemm2<T>(m, m, m, mone, lv.uA, lv.uB, nullptr, nullptr, zero, lv.uC, lv.n_left + lv.n_right, st);
   }
-  gj<T>(m, d_top, 1, v.status, gj_scr, gj_perm, gj_fail, st);
+  gj<T>(m, d_top, 1, v.status, gj_scr, gj_perm, gj_fail, gjb, st);
 }
 
 template <typename T>

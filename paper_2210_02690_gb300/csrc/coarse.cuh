@@ -38,6 +38,16 @@ struct CrLevel {
   T **gA, **gB, **gC, **dB0, **dB1, **dC, **uA, **uB, **uC;
 };
 
+// Scratch of the blocked Gauss-Jordan (blocks of 512+ rows): per matrix an m x w panel and a
+// w x m copy of the pivot rows, addressed through device pointer arrays.
+struct GjBlocked {
+  void* panels = nullptr;  // T** [batch_max]
+  void* olds = nullptr;    // T** [batch_max]
+  int w = 32;
+  long long m_max = 0;
+  int batch_max = 0;
+};
+
 template <typename T>
 struct CoarseSolver {
   CoarseView<T> v{};
@@ -48,6 +58,7 @@ struct CoarseSolver {
   T **d_top = nullptr, **d_topb = nullptr, **d_topx = nullptr;
   T* gj_scr = nullptr;  // Gauss-Jordan scratch for blocks too large for shared memory
   int *gj_perm = nullptr, *gj_fail = nullptr;
+  GjBlocked gjb;
   std::vector<CrLevel<T>> levels;
   std::vector<void*> owned;
 
