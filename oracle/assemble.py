@@ -39,11 +39,12 @@ class CellOperators:
         d = lev.dim
         self.lev = lev
         h = np.asarray(lev.h)
-        pts, wts = element.cell_rule(d)
+        r = lev.r
+        pts, wts = element.cell_rule_r(d, r)
         det = np.prod(h / 2.0)
-        vals, gref = element.q2_basis(pts)
+        vals, gref = element.q_basis(r, pts)
         gphys = gref * (2.0 / h)                     # (nq, nloc, d)
-        pb = element.p1disc_basis(pts)               # (nq, d+1)
+        pb = element.pdisc_basis(r, pts)             # (nq, dim P)
         qw = wts * det
         nloc = lev.n_loc_nodes
         self.mass = np.einsum("q,qi,qj->ij", qw, vals, vals)
@@ -68,20 +69,20 @@ class CellOperators:
 
         # Nitsche face terms per cell: velocity-velocity (ncells, i, c, j, e), pressure (ncells, i, c, m)
         vv = np.zeros((nc, nloc, d, nloc, d))
-        vp = np.zeros((nc, nloc, d, d + 1))
+        vp = np.zeros((nc, nloc, d, lev.Shat))
         # Dirichlet faces: the domain's (a do-nothing face is the natural condition of A_h and
         # carries no boundary term) and those of an obstacle
         for e, side, cells in lev.dirichlet_faces():
-            fp, fw = element.face_rule(d, e, side)
+            fp, fw = element.face_rule_r(d, e, side, r)
             fdet = np.prod(np.delete(h, e) / 2.0)
             fqw = fw * fdet
-            fv, fg = element.q2_basis(fp)
+            fv, fg = element.q_basis(r, fp)
             fgp = fg * (2.0 / h)
             nrm = np.zeros(d)
             nrm[e] = 1.0 if side == 1 else -1.0
             dn = fgp @ nrm                                    # normal derivative (nf, nloc)
             hf = h[e]
-            fpb = element.p1disc_basis(fp)
+            fpb = element.pdisc_basis(r, fp)
             consist = -nu * np.einsum("q,qj,qi->ij", fqw, dn, fv)     # -<nu d_n phi_j, phi_i>
             symm = -nu * np.einsum("q,qj,qi->ij", fqw, fv, dn)        # -<phi_j, nu d_n phi_i>
             pen1 = gamma1 * nu / hf * np.einsum("q,qj,qi->ij", fqw, fv, fv)
@@ -142,7 +143,7 @@ def dead_dofs(lev) -> np.ndarray:
     for a in range(lev.k + 1):
         for c in range(lev.dim):
             out.append(lev.vel_index(a, lev.dead_nodes, c))
-        for m in range(lev.dim + 1):
+        for m in range(lev.Shat):
             out.append(lev.pres_index(a, cells, m))
     return np.sort(np.concatenate(out))
 
@@ -165,8 +166,8 @@ def jacobian(lev, w: np.ndarray, nu: float, tau: float, newton: bool,
 def mass_matrix(lev) -> sp.csr_matrix:
     """Scalar-per-component velocity mass matrix on one time node block (R x R)."""
     d = lev.dim
-    pts, wts = element.cell_rule(d)
-    vals, _ = element.q2_basis(pts)
+    pts, wts = element.cell_rule_r(d, lev.r)
+    vals, _ = element.q_basis(lev.r, pts)
     me = np.einsum("q,qi,qj->ij", wts * np.prod(np.asarray(lev.h) / 2.0), vals, vals)
     rows, cols, data = [], [], []
     cn = lev.cell_nodes[~lev.masked]                 # cells removed by an obstacle add nothing
@@ -194,9 +195,9 @@ def rhs_linear(lev, f, g, v_prev, nu: float, tau: float, t0: float = 0.0,
     wts = timebasis.radau_weights(k)
     jump = timebasis.jump_vector(k)
     b = np.zeros(lev.N)
-    pts, qw = element.cell_rule(d)
+    pts, qw = element.cell_rule_r(d, lev.r)
     det = np.prod(h / 2.0)
-    vals, _ = element.q2_basis(pts)
+    vals, _ = element.q_basis(lev.r, pts)
     centres = lev.cell_centres()
     for a in range(k + 1):
         ta = t0 + tau * cn[a]
@@ -207,17 +208,17 @@ def rhs_linear(lev, f, g, v_prev, nu: float, tau: float, t0: float = 0.0,
         loc[lev.masked] = 0.0
         vel = np.zeros((lev.n_nodes, d))
         np.add.at(vel, lev.cell_nodes, loc)
-        pres = np.zeros((lev.n_cells, d + 1))
+        pres = np.zeros((lev.n_cells, lev.Shat))
         for e, side, cells in lev.dirichlet_faces():
             if g is None:
                 continue
-            fp, fw = element.face_rule(d, e, side)
+            fp, fw = element.face_rule_r(d, e, side, lev.r)
             fqw = fw * np.prod(np.delete(h, e) / 2.0)
-            fv, fg = element.q2_basis(fp)
+            fv, fg = element.q_basis(lev.r, fp)
             nrm = np.zeros(d)
             nrm[e] = 1.0 if side == 1 else -1.0
             dn = (fg * (2.0 / h)) @ nrm
-            fpb = element.p1disc_basis(fp)
+            fpb = element.pdisc_basis(lev.r, fp)
             xf = centres[cells][:, None, :] + fp[None] * (h / 2.0)
             gq = g(xf.reshape(-1, d), ta).reshape(len(cells), -1, d)
             gn = gq @ nrm

@@ -34,17 +34,17 @@ def obstacle_forces(lev, X: np.ndarray, nu: float) -> np.ndarray:
         cells = cells[inside]
         if not len(cells):
             continue
-        fp, fw = element.face_rule(d, e, side)
+        fp, fw = element.face_rule_r(d, e, side, lev.r)
         fqw = fw * np.prod(np.delete(h, e) / 2.0)
-        fv, fg = element.q2_basis(fp)
+        fv, fg = element.q_basis(lev.r, fp)
         grad = fg * (2.0 / h)                                    # (nq, nloc, d)
-        fpb = element.p1disc_basis(fp)
+        fpb = element.pdisc_basis(lev.r, fp)
         nrm = np.zeros(d)
         nrm[e] = 1.0 if side else -1.0
         for a in range(k + 1):
             xb = X.reshape(k + 1, lev.R + lev.S)[a]
             vel = xb[:lev.R].reshape(lev.n_nodes, d)[lev.cell_nodes[cells]]       # (nc, nloc, d)
-            pres = xb[lev.R:].reshape(lev.n_cells, d + 1)[cells]                   # (nc, d+1)
+            pres = xb[lev.R:].reshape(lev.n_cells, lev.Shat)[cells]                # (nc, dim P)
             gv = np.einsum("qie,kic->kqce", grad, vel)           # d v_c / d x_e at face points
             pq = np.einsum("qm,km->kq", fpb, pres)
             trac = nu * np.einsum("kqce,e->kqc", gv, nrm) - pq[:, :, None] * nrm[None, None, :]

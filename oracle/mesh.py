@@ -21,25 +21,26 @@ class Level:
         self.k = k
         self.cells = spec.cells(level)
         self.h = tuple((spec.hi[i] - spec.lo[i]) / self.cells[i] for i in range(self.dim))
-        self.nn = tuple(2 * c + 1 for c in self.cells)           # Q2 nodes per direction
+        self.r = getattr(spec, "order", 2)                         # velocity order of (Q_r)^d x P_{r-1}disc
+        self.nn = tuple(self.r * c + 1 for c in self.cells)      # Q_r nodes per direction
         self.n_nodes = int(np.prod(self.nn))
         self.n_cells = int(np.prod(self.cells))
+        self.Shat = len(element.pdisc_exponents(self.r, self.dim)) if self.r != 2 else self.dim + 1
         self.R = self.dim * self.n_nodes
-        self.S = (self.dim + 1) * self.n_cells
+        self.S = self.Shat * self.n_cells
         self.N = (k + 1) * (self.R + self.S)
-        self.n_loc_nodes = 3 ** self.dim
+        self.n_loc_nodes = (self.r + 1) ** self.dim
         self.Rhat = self.dim * self.n_loc_nodes
-        self.Shat = self.dim + 1
         self.n_patch = (k + 1) * (self.Rhat + self.Shat)
 
         # cell multi-indices (n_cells, dim), x fastest
         grids = np.meshgrid(*[np.arange(c) for c in self.cells], indexing="ij")
         self.cell_idx = np.stack([g.ravel(order="F") for g in grids], axis=1)
         # global node number of each local node of each cell (n_cells, 3^d)
-        loc = element.local_nodes(self.dim)
+        loc = element.local_nodes_r(self.dim, self.r)
         self.cell_nodes = np.zeros((self.n_cells, self.n_loc_nodes), dtype=np.int64)
         for i, l in enumerate(loc):
-            g = 2 * self.cell_idx + l
+            g = self.r * self.cell_idx + l
             self.cell_nodes[:, i] = self.node_number(g)
         self.dof = self._dof_map()
         # colour(K) = sum_i (c_i & 1) 2^i: cells of one colour share no Q2 node
@@ -69,7 +70,7 @@ class Level:
         return a * (self.R + self.S) + node * self.dim + comp
 
     def pres_index(self, a, cell, m):
-        return a * (self.R + self.S) + self.R + cell * (self.dim + 1) + m
+        return a * (self.R + self.S) + self.R + cell * self.Shat + m
 
     def _dof_map(self) -> np.ndarray:
         """dof[K, mu] for all cells, shape (n_cells, n_patch)."""
@@ -81,7 +82,7 @@ class Level:
             for i in range(self.n_loc_nodes):
                 for c in range(d):
                     out[:, base + i * d + c] = self.vel_index(a, self.cell_nodes[:, i], c)
-            for m in range(d + 1):
+            for m in range(self.Shat):
                 out[:, base + self.Rhat + m] = self.pres_index(a, cells, m)
         return out
 
@@ -119,7 +120,7 @@ class Level:
         return bool(self.spec.dirichlet >> (2 * direction + side) & 1)
 
     def node_coords(self) -> np.ndarray:
-        grids = np.meshgrid(*[self.spec.lo[i] + np.arange(self.nn[i]) * self.h[i] / 2 for i in range(self.dim)],
+        grids = np.meshgrid(*[self.spec.lo[i] + np.arange(self.nn[i]) * self.h[i] / self.r for i in range(self.dim)],
                             indexing="ij")
         return np.stack([g.ravel(order="F") for g in grids], axis=1)
 

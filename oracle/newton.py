@@ -54,15 +54,15 @@ def rhs_nodal(lev, f_nodal, g_nodal, v_prev, nu: float, tau: float,
         if g_nodal is not None:
             gn = g_nodal[a].reshape(lev.n_nodes, d)
             vloc = np.zeros((lev.n_nodes, d))
-            ploc = np.zeros((lev.n_cells, d + 1))
+            ploc = np.zeros((lev.n_cells, lev.Shat))
             for e, side, cells in lev.dirichlet_faces():
-                fp, fw = element.face_rule(d, e, side)
+                fp, fw = element.face_rule_r(d, e, side, lev.r)
                 fqw = fw * np.prod(np.delete(h, e) / 2.0)
-                fv, fg = element.q2_basis(fp)
+                fv, fg = element.q_basis(lev.r, fp)
                 nrm = np.zeros(d)
                 nrm[e] = 1.0 if side == 1 else -1.0
                 dn = (fg * (2.0 / h)) @ nrm
-                fpb = element.p1disc_basis(fp)
+                fpb = element.pdisc_basis(lev.r, fp)
                 gq = np.einsum("qj,kjc->kqc", fv, gn[lev.cell_nodes[cells]])   # g_h at face points
                 gnq = gq @ nrm
                 lv = (-nu * np.einsum("q,qi,kqc->kic", fqw, dn, gq)

@@ -39,7 +39,7 @@ def prolongation(coarse, fine) -> sp.csr_matrix:
     # velocity: evaluate the coarse Q2 functions at the fine nodes
     fx = fine.node_coords()
     cell, ref = _coarse_cell_and_ref(coarse, fx)
-    vals, _ = element.q2_basis(ref)                        # (n_fine_nodes, nloc)
+    vals, _ = element.q_basis(fine.r, ref)                 # (n_fine_nodes, nloc)
     cn = coarse.cell_nodes[cell]                           # (n_fine_nodes, nloc)
     vr, vc, vv = [], [], []
     for c in range(d):
@@ -49,6 +49,10 @@ def prolongation(coarse, fine) -> sp.csr_matrix:
     pv = sp.coo_matrix((np.concatenate(vv), (np.concatenate(vr), np.concatenate(vc))),
                        shape=(fine.R, coarse.R)).tocsr()
     pv.sum_duplicates()
+    if fine.r != 2:
+        pp = _pdisc_prolongation(coarse, fine)
+        blk = sp.block_diag([pv, pp], format="csr")
+        return _mask_dead(fine, sp.block_diag([blk] * (k + 1), format="csr"))
     # pressure: fine P1 coefficients of the coarse P1 function on each child
     centres = fine.cell_centres()
     h = np.asarray(fine.h)
@@ -73,7 +77,35 @@ def prolongation(coarse, fine) -> sp.csr_matrix:
                        shape=(fine.S, coarse.S)).tocsr()
     pp.eliminate_zeros()
     blk = sp.block_diag([pv, pp], format="csr")
-    out = sp.block_diag([blk] * (k + 1), format="csr")
+    return _mask_dead(fine, sp.block_diag([blk] * (k + 1), format="csr"))
+
+
+def _pdisc_prolongation(coarse, fine) -> sp.csr_matrix:
+    """P_{r-1}^disc: the coefficients of the coarse cell's polynomial on each child cell (the
+    space is invariant under the child's affine map, so the fine coefficients solve the
+    interpolation at the child's Gauss points exactly)."""
+    d, r, sh = fine.dim, fine.r, fine.Shat
+    pts, _ = element.cell_rule_r(d, r)                       # child reference points (more than dim P)
+    bf = element.pdisc_basis(r, pts)                         # (nq, sh)
+    rows, cols, vals = [], [], []
+    for child in range(fine.n_cells):
+        ci = fine.cell_idx[child]
+        cc = ci // 2
+        cell_c = int(sum(cc[e] * int(np.prod(coarse.cells[:e])) for e in range(d)))
+        off = ci - 2 * cc                                    # 0 or 1 per direction
+        ref_c = (pts + 1.0) / 2.0 + off[None, :] - 1.0       # child point in the coarse cell
+        bc = element.pdisc_basis(r, ref_c)                   # (nq, sh)
+        m = np.linalg.lstsq(bf, bc, rcond=None)[0]           # fine coefficients of each coarse basis fn
+        for i in range(sh):
+            for j in range(sh):
+                if abs(m[i, j]) > 1e-15:
+                    rows.append(child * sh + i)
+                    cols.append(cell_c * sh + j)
+                    vals.append(m[i, j])
+    return sp.coo_matrix((vals, (rows, cols)), shape=(fine.S, coarse.S)).tocsr()
+
+
+def _mask_dead(fine, out):
     if fine.masked.any():
         # obstacle domain: the fine unknowns without an equation (outside the domain) are not
         # part of the nested space; P sets them to zero, so R = P^T never carries their residual

@@ -35,6 +35,8 @@ class MeshSpec:
     # 2D only: cells removed from the domain, the box [x0, x1) x [y0, y1) of coarsest-level cell
     # indices (empty: none); its faces carry Dirichlet data (no-slip for the obstacle channel)
     obstacle: tuple = ()
+    # velocity order r of the pair (Q_r)^d x P_{r-1}^disc: 2 (the default) or 4 (2D)
+    order: int = 2
 
     def cells(self, level: int) -> tuple:
         f = 2 ** (self.n_levels - 1 - level)
@@ -54,28 +56,34 @@ class MeshSpec:
         return tuple(int(v) * f for v in self.obstacle)
 
 
-def n_nodes(cells: tuple) -> int:
-    return int(np.prod([2 * c + 1 for c in cells]))
+def n_nodes(cells: tuple, order: int = 2) -> int:
+    return int(np.prod([order * c + 1 for c in cells]))
 
 
 def n_cells(cells: tuple) -> int:
     return int(np.prod(cells))
 
 
-def block_sizes(dim: int, cells: tuple) -> tuple:
-    """(R, S) of one time-node block: Q2 velocity and P1disc pressure counts."""
-    return dim * n_nodes(cells), (dim + 1) * n_cells(cells)
+def pressure_dofs(dim: int, order: int = 2) -> int:
+    """dim P_{order-1}: the pressure coefficients of one cell (d + 1 for order 2)."""
+    from math import comb
+    return comb(order - 1 + dim, dim)
 
 
-def n_dofs(dim: int, cells: tuple, k: int) -> int:
-    r, s = block_sizes(dim, cells)
+def block_sizes(dim: int, cells: tuple, order: int = 2) -> tuple:
+    """(R, S) of one time-node block: Q_r velocity and P_{r-1}disc pressure counts."""
+    return dim * n_nodes(cells, order), pressure_dofs(dim, order) * n_cells(cells)
+
+
+def n_dofs(dim: int, cells: tuple, k: int, order: int = 2) -> int:
+    r, s = block_sizes(dim, cells, order)
     return (k + 1) * (r + s)
 
 
 def node_coords(spec: MeshSpec, level: int) -> np.ndarray:
     """Coordinates of the Q2 nodes of one level, shape (n_nodes, dim), x fastest."""
     cells = spec.cells(level)
-    axes = [np.linspace(spec.lo[i], spec.hi[i], 2 * cells[i] + 1) for i in range(spec.dim)]
+    axes = [np.linspace(spec.lo[i], spec.hi[i], spec.order * cells[i] + 1) for i in range(spec.dim)]
     grids = np.meshgrid(*axes, indexing="ij")
     # ravel in Fortran order so that x is the fastest index
     return np.stack([g.ravel(order="F") for g in grids], axis=1)
@@ -145,11 +153,11 @@ def channel_w(spec: MeshSpec, k: int, seed: int = BASE_SEED, u_max: float = 1.5,
     return _repeat_nodes(base + p, k)
 
 
-def split_blocks(x: np.ndarray, dim: int, cells: tuple, k: int):
-    """Views (velocity (k+1, n_nodes, dim), pressure (k+1, n_cells, dim+1)) of a C-ABI vector."""
-    r, s = block_sizes(dim, cells)
+def split_blocks(x: np.ndarray, dim: int, cells: tuple, k: int, order: int = 2):
+    """Views (velocity (k+1, n_nodes, dim), pressure (k+1, n_cells, dim P)) of a C-ABI vector."""
+    r, s = block_sizes(dim, cells, order)
     xb = x.reshape(k + 1, r + s)
-    return xb[:, :r].reshape(k + 1, -1, dim), xb[:, r:].reshape(k + 1, -1, dim + 1)
+    return xb[:, :r].reshape(k + 1, -1, dim), xb[:, r:].reshape(k + 1, -1, pressure_dofs(dim, order))
 
 
 def reference_solution(spec: MeshSpec, k: int, seed: int = BASE_SEED + 1, level: int | None = None) -> np.ndarray:
@@ -158,9 +166,9 @@ def reference_solution(spec: MeshSpec, k: int, seed: int = BASE_SEED + 1, level:
     level = spec.n_levels - 1 if level is None else level
     cells = spec.cells(level)
     rng = np.random.default_rng(seed)
-    x = rng.standard_normal(n_dofs(spec.dim, cells, k))
+    x = rng.standard_normal(n_dofs(spec.dim, cells, k, spec.order))
     if spec.pure_dirichlet():
-        _, p = split_blocks(x, spec.dim, cells, k)
+        _, p = split_blocks(x, spec.dim, cells, k, spec.order)
         p[:, :, 0] -= p[:, :, 0].mean(axis=1, keepdims=True)
     return x
 
