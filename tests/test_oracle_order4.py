@@ -242,10 +242,12 @@ def test_q4_fgmres_matches_dense_solve():
     assert its <= 30
 
 
-def test_q4_exactness_catches_a_short_quadrature(monkeypatch):
-    """With 3 instead of 5 Gauss points per direction the Q4 integrals are no longer exact."""
+def test_q4_exactness_catches_a_weaker_quadrature(monkeypatch):
+    """With the 5-point Gauss-Lobatto rule (exact to degree 7 only) instead of Gauss-Legendre
+    (degree 9), the degree-8 integrands of Q4 are no longer exact and the identity breaks."""
     spec = SPECS["box_outflow"]
     assert residual(spec, 1) < 1e-11
-    short = element.gauss_rule_1d(2)
-    monkeypatch.setattr(element, "gauss_rule_1d", lambda r: short)
+    s37 = np.sqrt(3.0 / 7.0)
+    lobatto = (np.array([-1.0, -s37, 0.0, s37, 1.0]), np.array([0.1, 49.0 / 90.0, 32.0 / 45.0, 49.0 / 90.0, 0.1]))
+    monkeypatch.setattr(element, "gauss_rule_1d", lambda r: lobatto)
     assert residual(spec, 1) > 1e-6
