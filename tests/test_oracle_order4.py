@@ -242,12 +242,39 @@ def test_q4_fgmres_matches_dense_solve():
     assert its <= 30
 
 
-def test_q4_exactness_catches_a_weaker_quadrature(monkeypatch):
-    """With the 5-point Gauss-Lobatto rule (exact to degree 7 only) instead of Gauss-Legendre
-    (degree 9), the degree-8 integrands of Q4 are no longer exact and the identity breaks."""
+def test_q4_exactness_catches_planted_mistakes(monkeypatch):
+    """Galerkin exactness fails for two plausible mistakes: Lagrange functions built on other nodes
+    (Gauss-Lobatto instead of equidistant) than the nodes the unknowns sit at, and a pressure
+    space of degree 2 instead of 3."""
     spec = SPECS["box_outflow"]
     assert residual(spec, 1) < 1e-11
     s37 = np.sqrt(3.0 / 7.0)
-    lobatto = (np.array([-1.0, -s37, 0.0, s37, 1.0]), np.array([0.1, 49.0 / 90.0, 32.0 / 45.0, 49.0 / 90.0, 0.1]))
-    monkeypatch.setattr(element, "gauss_rule_1d", lambda r: lobatto)
+    lob = np.array([-1.0, -s37, 0.0, s37, 1.0])
+    orig = element.lagrange1d_r
+
+    def lagrange_on_lobatto(r, x):
+        x = np.asarray(x, float)
+        if r != 4:
+            return orig(r, x)
+        vals = np.ones(x.shape + (5,))
+        ders = np.zeros(x.shape + (5,))
+        for l in range(5):
+            others = [m for m in range(5) if m != l]
+            den = np.prod([lob[l] - lob[m] for m in others])
+            for m in others:
+                vals[..., l] *= x - lob[m]
+            for q in others:
+                term = np.ones(x.shape)
+                for m in others:
+                    if m != q:
+                        term = term * (x - lob[m])
+                ders[..., l] += term
+            vals[..., l] /= den
+            ders[..., l] /= den
+        return vals, ders
+    monkeypatch.setattr(element, "lagrange1d_r", lagrange_on_lobatto)
+    assert residual(spec, 1) > 1e-6
+    monkeypatch.undo()
+    exps = element.pdisc_exponents
+    monkeypatch.setattr(element, "pdisc_exponents", lambda r, d: [a for a in exps(r, d) if sum(a) <= 2])
     assert residual(spec, 1) > 1e-6
