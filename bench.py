@@ -507,6 +507,7 @@ def gpu_arm(args) -> None:
         import torch
         out["square256"] = square256_report(peak, torch)
         out["cube48"] = cube48_report(peak, torch)
+        out["order4"] = order4_report(peak, torch)
     if world == 1 and not args.no_workloads:
         out["obstacle_march"] = obstacle_march_report()
     if world == 1 and not args.no_warm_start:
@@ -526,7 +527,7 @@ def workload_line(name: str, k: int, form: str, peak: float, torch, reps: int = 
 
     cfg = si.WORKLOADS[name]
     spec = cfg["spec"]
-    w = torch.from_numpy(si.fourier_w(spec, k).ravel()).cuda()
+    w = torch.from_numpy(si.make_w(dict(cfg, k=k)).ravel()).cuda()
     s = Solver(spec, k, cfg["nu"], cfg["tau"], w, nu1=cfg["nu1"], nu2=cfg["nu2"],
                linearisation="newton" if cfg["newton"] else "oseen", **FORMS[form])
     b = s.apply_jacobian(torch.from_numpy(si.reference_solution(spec, k)).cuda())
@@ -543,10 +544,10 @@ def workload_line(name: str, k: int, form: str, peak: float, torch, reps: int = 
             raise RuntimeError(f"{name} k={k} {form}: FGMRES did not converge ({rel:.2e})")
     t_solve = min(time_ms(torch, s.stream, solve) for _ in range(reps))
     per_cycle = si.smoothed_dofs_per_cycle(spec, k, cfg["nu1"], cfg["nu2"])
-    out = {"n_dofs": si.n_dofs(spec.dim, spec.n, k), "setup_ms": t_setup, "time_to_tol_ms": t_solve,
+    out = {"n_dofs": si.n_dofs(spec.dim, spec.n, k, spec.order), "setup_ms": t_setup, "time_to_tol_ms": t_solve,
            "iters": its[0], "finest_variant": variant,
            "value": per_cycle * its[0] / ((t_setup + t_solve) * 1e-3),
-           "smoother": smoother_report(s, spec, k, cfg, form, peak, torch)}
+           "smoother": smoother_report(s, spec, k, cfg, form, peak, torch) if spec.order == 2 else None}
     s.close()
     return out
 
@@ -560,6 +561,20 @@ def square256_report(peak: float, torch) -> dict:
     for k in (1, 2, 3, 4):
         for form in ("f64", "f32", "bf16"):
             out[f"k{k}_{form}"] = workload_line("square256", k, form, peak, torch)
+    return out
+
+
+def order4_report(peak: float, torch) -> dict:
+    """The paper's 2D element (Q4)^2 x P3disc (local systems of 60 (k+1) unknowns) on the channel,
+    352x64 quads -> 44x8: FP64 and FP32 forms, k = 1, 2."""
+    cfg = si.WORKLOADS["channel_q4"]
+    spec = cfg["spec"]
+    out = {"workload": f"channel [0,2.2]x[0,0.41], {spec.n[0]}x{spec.n[1]} quads, {spec.n_levels} levels, "
+                       "(Q4)^2 x P3disc, Newton Jacobian at the seeded channel w, nu=1e-3, tau=0.005, V(2,2), "
+                       "FGMRES to 1e-8"}
+    for k in (1, 2):
+        for form in ("f64", "f32"):
+            out[f"k{k}_{form}"] = workload_line("channel_q4", k, form, peak, torch)
     return out
 
 

@@ -77,6 +77,14 @@ typedef struct {
   double x0, x1, y0, y1, z0, z1;
   unsigned dirichlet_faces;
   int obstacle[4];         /* x_lo, x_hi, y_lo, y_hi in coarsest-level cells (2D)  */
+  int order;               /* velocity order r of (Q_r)^d x P_{r-1}^disc (Sec. 2): 2    */
+                           /* (0 also means 2) or 4 (2D, k <= 2, no obstacle; the pair */
+                           /* of the paper's 2D experiment).  Q_r nodes: r n + 1 per   */
+                           /* direction; P_{r-1}^disc: the monomials of total degree   */
+                           /* <= r - 1 in the cell's reference coordinates, ordered by */
+                           /* degree and then with the x exponent falling (r = 2:      */
+                           /* {1, xi, eta}; r = 4: 10 coefficients).  Newton, the warm */
+                           /* start and the drag/lift entry points need order 2.       */
 } stg_mesh;
 
 typedef struct {

@@ -80,9 +80,17 @@ def face_rule(dim: int, direction: int, side: int):
 
 # ---------------------------------------------------------------- general order r (r = 2 above)
 def gauss_rule_1d(r: int):
-    """(r+1)-point Gauss-Legendre points and weights on [-1, 1] (r = 2: the constants above)."""
+    """(r+1)-point Gauss-Legendre points and weights on [-1, 1] (r = 2: the constants above;
+    r = 4: the closed form, points +-sqrt(5 -+ 2 sqrt(10/7)) / 3 and 0, weights
+    (322 +- 13 sqrt(70)) / 900 and 128/225)."""
     if r == 2:
         return GAUSS_X, GAUSS_W
+    if r == 4:
+        a = np.sqrt(5.0 - 2.0 * np.sqrt(10.0 / 7.0)) / 3.0
+        b = np.sqrt(5.0 + 2.0 * np.sqrt(10.0 / 7.0)) / 3.0
+        wa = (322.0 + 13.0 * np.sqrt(70.0)) / 900.0
+        wb = (322.0 - 13.0 * np.sqrt(70.0)) / 900.0
+        return np.array([-b, -a, 0.0, a, b]), np.array([wb, wa, 128.0 / 225.0, wa, wb])
     x, w = np.polynomial.legendre.leggauss(r + 1)
     return x, w
 

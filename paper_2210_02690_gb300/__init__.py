@@ -49,7 +49,8 @@ class stg_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("n_levels", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("z0", ctypes.c_double),
-                ("z1", ctypes.c_double), ("dirichlet_faces", ctypes.c_uint), ("obstacle", ctypes.c_int * 4)]
+                ("z1", ctypes.c_double), ("dirichlet_faces", ctypes.c_uint), ("obstacle", ctypes.c_int * 4),
+                ("order", ctypes.c_int)]
 
 
 class stg_options(ctypes.Structure):
@@ -141,7 +142,7 @@ def make_mesh(spec) -> stg_mesh:
     hi = list(spec.hi) + [1.0] * (3 - len(spec.hi))
     ob = tuple(getattr(spec, "obstacle", ()) or (0, 0, 0, 0))
     return stg_mesh(spec.dim, n[0], n[1], n[2], spec.n_levels, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2],
-                    spec.dirichlet, (ctypes.c_int * 4)(*ob))
+                    spec.dirichlet, (ctypes.c_int * 4)(*ob), int(getattr(spec, "order", 2)))
 
 
 def make_options(**kw) -> stg_options:

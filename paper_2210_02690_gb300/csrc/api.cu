@@ -25,12 +25,14 @@ Geom make_geom(const stg_mesh& m, int level, int k) {
   g.k = k;
   g.nt = k + 1;
   const int f = 1 << (m.n_levels - 1 - level);
+  g.r = m.order == 4 ? 4 : 2;
+  g.npd = g.r == 2 ? m.dim + 1 : (m.dim == 2 ? 10 : 20);
   const int nf[3] = {m.nx, m.ny, m.dim == 3 ? m.nz : 1};
   const double lo[3] = {m.x0, m.y0, m.z0}, hi[3] = {m.x1, m.y1, m.z1};
   for (int e = 0; e < 3; ++e) {
     if (e < m.dim) {
       g.n[e] = nf[e] / f;
-      g.nn[e] = 2 * g.n[e] + 1;
+      g.nn[e] = g.r * g.n[e] + 1;
       g.lo[e] = lo[e];
       g.h[e] = (hi[e] - lo[e]) / g.n[e];
     } else {
@@ -45,8 +47,8 @@ Geom make_geom(const stg_mesh& m, int level, int k) {
   for (int i = 0; i < 4; ++i) g.ob[i] = m.obstacle[i] * fo;
   if (g.ob[1] <= g.ob[0] || g.ob[3] <= g.ob[2]) g.ob[0] = g.ob[1] = g.ob[2] = g.ob[3] = 0;
   g.NV = g.nt * g.dim;
-  g.NP = g.nt * (g.dim + 1);
-  g.nloc = g.dim == 2 ? 9 : 27;
+  g.NP = g.nt * g.npd;
+  g.nloc = g.dim == 2 ? (g.r + 1) * (g.r + 1) : (g.r + 1) * (g.r + 1) * (g.r + 1);
   g.npatch = g.nloc * g.NV + g.NP;
   g.n_nodes = (long long)g.nn[0] * g.nn[1] * g.nn[2];
   g.n_cells = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -267,9 +269,9 @@ void build_pattern(stg_ctx* c, LevelBufs& L) {
     for (int iy = 0; iy < g.nn[1]; ++iy)
       for (int ix = 0; ix < g.nn[0]; ++ix) {
         int xl, xh, yl, yh, zl, zh;
-        stencil_range(ix, g.nn[0], xl, xh);
-        stencil_range(iy, g.nn[1], yl, yh);
-        stencil_range(iz, g.nn[2], zl, zh);
+        stencil_range(ix, g.nn[0], xl, xh, g.r);
+        stencil_range(iy, g.nn[1], yl, yh, g.r);
+        stencil_range(iz, g.nn[2], zl, zh, g.r);
         for (int jz = zl; jz <= zh; ++jz)
           for (int jy = yl; jy <= yh; ++jy)
             for (int jx = xl; jx <= xh; ++jx) colidx.push_back((int)node_id(g, jx, jy, jz));
@@ -306,7 +308,7 @@ void linearise_internal(stg_ctx* c) {
   auto to_f32 = [&](LevelBufs& L, cudaStream_t s) {
     if (vc64(c)) return;
     if (L.vv32) convert(L.nnzb * L.g.NV * L.g.NV, L.vv, L.vv32, s);
-    const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * (L.g.dim + 1);
+    const long long nvp = L.g.n_cells * L.g.nloc * L.g.nt * L.g.dim * L.g.npd;
     convert(nvp, L.vp, L.vp32, s);
     convert(nvp, L.pv, L.pv32, s);
     if (L.mk32) kron_split(L.g, L.nnzb, L.vv, c->td, L.mk32, L.ak32, s);
@@ -831,9 +833,13 @@ stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
   const double lo[3] = {m->x0, m->y0, m->z0}, hi[3] = {m->x1, m->y1, m->z1};
   for (int e = 0; e < m->dim; ++e)
     if (!(hi[e] > lo[e])) throw Error{STG_EINVAL, "empty domain"};
+  if (m->order != 0 && m->order != 2 && m->order != 4) throw Error{STG_EINVAL, "order must be 2 or 4"};
+  if (m->order == 4 && m->dim != 2) throw Error{STG_EINVAL, "order 4 is supported in 2D only"};
+  if (m->order == 4 && k > 2) throw Error{STG_EINVAL, "order 4 supports k = 0..2"};
   const int* ob = m->obstacle;
   if (ob[0] || ob[1] || ob[2] || ob[3]) {
     const int nc0[2] = {m->nx / f, m->ny / f};
+    if (m->order == 4) throw Error{STG_EINVAL, "an obstacle is supported with order 2 only"};
     if (m->dim != 2) throw Error{STG_EINVAL, "an obstacle is supported in 2D only"};
     if (!(0 <= ob[0] && ob[0] < ob[1] && ob[1] <= nc0[0] && 0 <= ob[2] && ob[2] < ob[3] && ob[3] <= nc0[1]))
       throw Error{STG_EINVAL, "obstacle box outside the coarsest level's cells or empty"};
@@ -914,6 +920,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
     c->td = time_basis(k);
     c->pure_dirichlet = mesh->dirichlet_faces == (1u << (2 * mesh->dim)) - 1u;
     upload_fe_tables();
+    upload_transfer4_tables();
     const int nl = mesh->n_levels;
     c->lv.resize(nl);
     size_t scratch = 0, scratch2 = 0;
@@ -925,7 +932,7 @@ stg_status stg_setup(const stg_mesh* mesh, int k, double nu, double tau, const d
       const Geom& g = L.g;
       build_pattern(c, L);
       L.vv = dalloc<double>(c, L.nnzb * g.NV * g.NV);
-      const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * (g.dim + 1);
+      const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * g.npd;
       L.vp = dalloc<double>(c, nvp);
       L.pv = dalloc<double>(c, nvp);
       if (!f64) {
@@ -1190,6 +1197,10 @@ stg_status stg_newton_slab(stg_ctx* c, const double* v_prev, const double* f, co
                            double rtol, double atol, int maxit, int* newton_steps, int* gmres_iters,
                            double* residual) {
   if (!c || !X || maxit < 0 || rtol < 0 || atol < 0) return STG_EINVAL;
+  if (c->lv.back().g.r != 2) {
+    c->err = "stg_newton_slab needs order 2";
+    return STG_EINVAL;
+  }
   try {
     LevelBufs& F = c->lv.back();
     const Geom& gg = F.g;
@@ -1242,6 +1253,10 @@ stg_status warm_check(stg_ctx* c, const stg_cnn* net) {
 
 stg_status stg_warm_features(stg_ctx* c, const double* X_n, const double* X_prev, float scale_v, float scale_d,
                              float* feat) {
+  if (c && c->lv.back().g.r != 2) {
+    c->err = "stg_warm_features needs order 2";
+    return STG_EINVAL;
+  }
   if (!c || !X_n || !X_prev || !feat || !(scale_v > 0.f) || !(scale_d > 0.f)) return STG_EINVAL;
   const stg_status s = warm_check(c, nullptr);
   if (s != STG_OK) return s;
@@ -1255,6 +1270,10 @@ stg_status stg_warm_features(stg_ctx* c, const double* X_n, const double* X_prev
 
 stg_status stg_warm_target(stg_ctx* c, const double* X_n, const double* X_prev, const double* X_next, float scale_d,
                            float* target) {
+  if (c && c->lv.back().g.r != 2) {
+    c->err = "stg_warm_target needs order 2";
+    return STG_EINVAL;
+  }
   if (!c || !X_n || !X_prev || !X_next || !target || !(scale_d > 0.f)) return STG_EINVAL;
   const stg_status s = warm_check(c, nullptr);
   if (s != STG_OK) return s;
@@ -1268,6 +1287,10 @@ stg_status stg_warm_target(stg_ctx* c, const double* X_n, const double* X_prev, 
 
 stg_status stg_warm_start(stg_ctx* c, stg_cnn* net, const double* X_n, const double* X_prev, float scale_v,
                           float scale_d, double* X0) {
+  if (c && c->lv.back().g.r != 2) {
+    c->err = "stg_warm_start needs order 2";
+    return STG_EINVAL;
+  }
   if (!c || !X_n || !X_prev || !X0 || !(scale_v > 0.f) || !(scale_d > 0.f)) return STG_EINVAL;
   const stg_status s = warm_check(c, net);
   if (s != STG_OK) return s;
@@ -1290,6 +1313,10 @@ stg_status stg_warm_start(stg_ctx* c, stg_cnn* net, const double* X_n, const dou
 }
 
 stg_status stg_warm_scales(stg_ctx* c, const double* X_n, const double* X_prev, double* rms_v, double* rms_dv) {
+  if (c && c->lv.back().g.r != 2) {
+    c->err = "stg_warm_scales needs order 2";
+    return STG_EINVAL;
+  }
   if (!c || !X_n || !X_prev) return STG_EINVAL;
   try {
     const Geom& g = c->lv.back().g;
@@ -1341,14 +1368,14 @@ stg_status stg_get_local_inverse(const stg_ctx* cc, int level, long long cell, d
       return f;
     };
     // paper order: a-major; nodes x comps; then pressure coefficients
-    const int d = g.dim, blk = g.nloc * d + d + 1;
+    const int d = g.dim, blk = g.nloc * d + g.npd;
     auto gpu_index = [&](int mu) {
       const int a = mu / blk, r = mu % blk;
       if (r < g.nloc * d) {
         const int i = r / d, comp = r % d;
         return i * g.NV + a * d + comp;
       }
-      return g.nloc * g.NV + a * (d + 1) + (r - g.nloc * d);
+      return g.nloc * g.NV + a * g.npd + (r - g.nloc * d);
     };
     for (int r = 0; r < n; ++r)
       for (int col = 0; col < n; ++col) out[(size_t)r * n + col] = val(gpu_index(col), gpu_index(r));

@@ -20,6 +20,11 @@ __constant__ double c_L1[5][3];
 __constant__ double c_D1[5][3];
 __constant__ double c_X[5];
 __constant__ double c_GW[3];
+// order 4 (2D): the same at the 5 Gauss points and xi = -1, +1
+__constant__ double c_L4[7][5];
+__constant__ double c_D4[7][5];
+__constant__ double c_X4[7];
+__constant__ double c_GW4[5];
 
 void upload_fe_tables() {
   const double g = std::sqrt(0.6);
@@ -39,6 +44,34 @@ void upload_fe_tables() {
   STG_CUDA_OK(cudaMemcpyToSymbol(c_D1, D1, sizeof(D1)));
   STG_CUDA_OK(cudaMemcpyToSymbol(c_X, X, sizeof(X)));
   STG_CUDA_OK(cudaMemcpyToSymbol(c_GW, GW, sizeof(GW)));
+  // order 4: 1D Q4 Lagrange values / derivatives (nodes -1, -1/2, 0, 1/2, 1) at the 5 Gauss points
+  // and xi = -1, +1; the 5-point Gauss rule
+  const double a5 = std::sqrt(5.0 - 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+  const double b5 = std::sqrt(5.0 + 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+  const double X4[7] = {-b5, -a5, 0.0, a5, b5, -1.0, 1.0};
+  const double wa = (322.0 + 13.0 * std::sqrt(70.0)) / 900.0, wb = (322.0 - 13.0 * std::sqrt(70.0)) / 900.0;
+  const double GW4[5] = {wb, wa, 128.0 / 225.0, wa, wb};
+  const double nd[5] = {-1.0, -0.5, 0.0, 0.5, 1.0};
+  double L4[7][5], D4[7][5];
+  for (int p = 0; p < 7; ++p)
+    for (int l = 0; l < 5; ++l) {
+      double v = 1.0, dsum = 0.0;
+      for (int m = 0; m < 5; ++m)
+        if (m != l) v *= (X4[p] - nd[m]) / (nd[l] - nd[m]);
+      for (int q = 0; q < 5; ++q) {
+        if (q == l) continue;
+        double t = 1.0 / (nd[l] - nd[q]);
+        for (int m = 0; m < 5; ++m)
+          if (m != l && m != q) t *= (X4[p] - nd[m]) / (nd[l] - nd[m]);
+        dsum += t;
+      }
+      L4[p][l] = v;
+      D4[p][l] = dsum;
+    }
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_L4, L4, sizeof(L4)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_D4, D4, sizeof(D4)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_X4, X4, sizeof(X4)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_GW4, GW4, sizeof(GW4)));
 }
 
 namespace {
@@ -574,6 +607,141 @@ __global__ void __launch_bounds__(256) assemble_rhs(Geom g, int colour, TimeData
   }
 }
 
+// ---------------------------------------------------------------- order 4 (2D), (Q4)^2 x P3disc
+// One CTA per cell: the whole element matrix of the space-time block (time coupling, viscous,
+// convection and Newton at w_a, the Nitsche terms of the cell's Dirichlet faces) by quadrature
+// with the 5 x 5 Gauss rule (5 points per face), added into the cell's BCSR blocks, and the
+// velocity-pressure / pressure-velocity blocks.  w = nullptr: the operator at w = 0.
+// P3 monomials xi^a eta^b in the order (0,0) (1,0) (0,1) (2,0) (1,1) (0,2) (3,0) (2,1) (1,2) (0,3).
+__device__ __forceinline__ double p3_monomial(int m, double x, double y) {
+  const int ea[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0}, eb[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+  double v = 1.0;
+  for (int i = 0; i < ea[m]; ++i) v *= x;
+  for (int i = 0; i < eb[m]; ++i) v *= y;
+  return v;
+}
+
+__global__ void __launch_bounds__(256) assemble_cells_q4(Geom g, int colour, TimeData td, AsmCoef cf,
+                                                         const double* __restrict__ w,
+                                                         const int* __restrict__ rowptr, double* __restrict__ vv,
+                                                         double* __restrict__ vp, double* __restrict__ pv) {
+  constexpr int NL = 25, NQ = 25, NF = 5, NPD = 10;
+  __shared__ double phi[NQ][NL];
+  __shared__ double dphi[NQ][NL][2];
+  __shared__ double qwd[NQ];
+  __shared__ double wq[5][NQ][2];
+  __shared__ double gw[5][NQ][2][2];
+  __shared__ int slots[NL * NL];
+  const int nt = g.nt, NV = g.NV;
+  int cx, cy, cz;
+  patch_cell(g, g.coff[colour] + blockIdx.x, cx, cy, cz);
+  const int cc[3] = {cx, cy, 0};
+  const long long cell = cell_id(g, cx, cy, 0);
+  const unsigned faces = face_class<2>(g, cc);
+  const double hx = g.h[0], hy = g.h[1];
+  for (int t = threadIdx.x; t < NQ * NL; t += blockDim.x) {
+    const int q = t / NL, i = t % NL;
+    const int q1 = q % 5, q2 = q / 5, i1 = i % 5, i2 = i / 5;
+    phi[q][i] = c_L4[q1][i1] * c_L4[q2][i2];
+    dphi[q][i][0] = 2.0 / hx * c_D4[q1][i1] * c_L4[q2][i2];
+    dphi[q][i][1] = 2.0 / hy * c_L4[q1][i1] * c_D4[q2][i2];
+    if (i == 0) qwd[q] = c_GW4[q1] * c_GW4[q2] * hx * hy / 4.0;
+  }
+  for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) {
+    const int i = t / NL, j = t % NL;
+    slots[t] = (int)bcsr_slot(g, rowptr, 4 * cx + i % 5, 4 * cy + i / 5, 0, 4 * cx + j % 5, 4 * cy + j / 5, 0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nt * NQ * 2; t += blockDim.x) {
+    const int a = t / (NQ * 2), q = (t / 2) % NQ, c = t % 2;
+    double v = 0.0, g0 = 0.0, g1 = 0.0;
+    if (w)
+      for (int i = 0; i < NL; ++i) {
+        const double wi = w[node_id(g, 4 * cx + i % 5, 4 * cy + i / 5, 0) * NV + a * 2 + c];
+        v += phi[q][i] * wi;
+        g0 += dphi[q][i][0] * wi;
+        g1 += dphi[q][i][1] * wi;
+      }
+    wq[a][q][c] = v;
+    gw[a][q][c][0] = g0;
+    gw[a][q][c][1] = g1;
+  }
+  __syncthreads();
+  // one task per node pair (i, j): the scalar integrals, the Newton and Nitsche d x d blocks
+  for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) {
+    const int i = t / NL, j = t % NL;
+    double mass = 0.0, stiff = 0.0, conv[5] = {0, 0, 0, 0, 0}, newt[5][2][2] = {};
+    for (int q = 0; q < NQ; ++q) {
+      const double wpi = qwd[q] * phi[q][i];
+      mass += wpi * phi[q][j];
+      stiff += qwd[q] * (dphi[q][i][0] * dphi[q][j][0] + dphi[q][i][1] * dphi[q][j][1]);
+      for (int a = 0; a < nt; ++a) {
+        conv[a] += wpi * (wq[a][q][0] * dphi[q][j][0] + wq[a][q][1] * dphi[q][j][1]);
+        if (cf.newton) {
+          const double pp = wpi * phi[q][j];
+          for (int c = 0; c < 2; ++c)
+            for (int e = 0; e < 2; ++e) newt[a][c][e] += pp * gw[a][q][c][e];
+        }
+      }
+    }
+    double fs = 0.0, fn[2][2] = {{0, 0}, {0, 0}};
+    for (int f = 0; f < 4; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      const double nrm = s0 ? 1.0 : -1.0, hf = g.h[e0], hl = g.h[1 - e0];
+      for (int fq = 0; fq < NF; ++fq) {
+        const int p0 = e0 == 0 ? 5 + s0 : fq, p1 = e0 == 1 ? 5 + s0 : fq;
+        const double wt = c_GW4[fq] * hl / 2.0;
+        const double vi = c_L4[p0][i % 5] * c_L4[p1][i / 5], vj = c_L4[p0][j % 5] * c_L4[p1][j / 5];
+        const double di = (e0 == 0 ? 2.0 / hx * c_D4[p0][i % 5] * c_L4[p1][i / 5]
+                                   : 2.0 / hy * c_L4[p0][i % 5] * c_D4[p1][i / 5]) * nrm;
+        const double dj = (e0 == 0 ? 2.0 / hx * c_D4[p0][j % 5] * c_L4[p1][j / 5]
+                                   : 2.0 / hy * c_L4[p0][j % 5] * c_D4[p1][j / 5]) * nrm;
+        fs += wt * (-cf.nu * dj * vi - cf.nu * vj * di + cf.gamma1 * cf.nu / hf * vj * vi);
+        fn[e0][e0] += wt * cf.gamma2 / hf * vj * vi;  // n n^T has the single entry (e0, e0)
+      }
+    }
+    double* blk = vv + (long long)slots[i * NL + j] * NV * NV;
+    for (int a = 0; a < nt; ++a)
+      for (int b = 0; b < nt; ++b)
+        for (int c = 0; c < 2; ++c)
+          for (int e = 0; e < 2; ++e) {
+            double val = c == e ? td.T[a][b] * mass : 0.0;
+            if (a == b) {
+              double sp = fn[c][e] + (cf.newton ? newt[a][c][e] : 0.0);
+              if (c == e) sp += conv[a] + cf.nu * stiff + fs;
+              val += cf.tau * td.w[a] * sp;
+            }
+            blk[(long long)(a * 2 + c) * NV + b * 2 + e] += val;
+          }
+  }
+  // velocity-pressure [cell][i][a][c][m] and pressure-velocity [cell][a][m][i][c] (w-independent:
+  // written by the set-up's call, skipped by re-linearisations, vp == nullptr)
+  if (!vp) return;
+  for (int t = threadIdx.x; t < NL * 2 * NPD; t += blockDim.x) {
+    const int m = t % NPD, c = (t / NPD) % 2, i = t / (NPD * 2);
+    double val = 0.0;
+    for (int q = 0; q < NQ; ++q)
+      val -= qwd[q] * p3_monomial(m, c_X4[q % 5], c_X4[q / 5]) * dphi[q][i][c];
+    for (int f = 0; f < 4; ++f) {
+      if (!(faces >> f & 1u)) continue;
+      const int e0 = f >> 1, s0 = f & 1;
+      if (e0 != c) continue;  // <xi_m n_c, phi_i> with n along e0 only
+      const double nrm = s0 ? 1.0 : -1.0, hl = g.h[1 - e0];
+      for (int fq = 0; fq < NF; ++fq) {
+        const int p0 = e0 == 0 ? 5 + s0 : fq, p1 = e0 == 1 ? 5 + s0 : fq;
+        val += c_GW4[fq] * hl / 2.0 * p3_monomial(m, c_X4[p0], c_X4[p1]) * nrm * c_L4[p0][i % 5] *
+               c_L4[p1][i / 5];
+      }
+    }
+    for (int a = 0; a < nt; ++a) {
+      const double sc = cf.tau * td.w[a];
+      vp[(((cell * NL + i) * nt + a) * 2 + c) * NPD + m] = sc * val;
+      pv[((cell * nt + a) * NPD + m) * (long long)NL * 2 + i * 2 + c] = -sc * val;
+    }
+  }
+}
+
 // Identity rows of the unknowns without an equation (obstacle): I added to the diagonal block
 // of every Q2 node of removed cells only (the pressure of removed cells is handled by the
 // residual and the patch inversion, as the velocity-pressure blocks carry no diagonal).
@@ -595,8 +763,23 @@ long long assemble_table_doubles(int dim, int k) {
   return base + (long long)(k + 1) * (1LL << (2 * dim)) * nd * nd;  // followed by K
 }
 
+static void assemble_level_q4(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int,
+                              const int* rowptr, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st) {
+  STG_CUDA_OK(cudaMemsetAsync(vv, 0, sizeof(double) * nnzb * g.NV * g.NV, st));
+  for (int col = 0; col < 4; ++col) {
+    const long long cnt = g.coff[col + 1] - g.coff[col];
+    if (cnt == 0) continue;
+    assemble_cells_q4<<<(unsigned)cnt, 256, 0, st>>>(g, col, td, cf, w_int, rowptr, vv, vp, pv);
+    STG_LAUNCH_OK();
+  }
+}
+
 void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                     double* tab, double* vv, long long nnzb, double* vp, double* pv, cudaStream_t st) {
+  if (g.r == 4) {  // order 4: the whole operator at w_int (null: w = 0) by the generic kernel
+    assemble_level_q4(g, td, cf, w_int, rowptr, vv, nnzb, vp, pv, st);
+    return;
+  }
   STG_CUDA_OK(cudaMemsetAsync(vv, 0, sizeof(double) * nnzb * g.NV * g.NV, st));
   const unsigned ncls = 1u << (2 * g.dim);
   const int nloc = g.dim == 2 ? 9 : 27;
@@ -629,6 +812,10 @@ void assemble_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const 
 
 void assemble_level_w(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* w_int, const int* rowptr,
                       const double* tab, const double* vconst, double* vv, long long nnzb, cudaStream_t st) {
+  if (g.r == 4) {
+    assemble_level_q4(g, td, cf, w_int, rowptr, vv, nnzb, nullptr, nullptr, st);
+    return;
+  }
   STG_CUDA_OK(cudaMemcpyAsync(vv, vconst, sizeof(double) * nnzb * g.NV * g.NV, cudaMemcpyDeviceToDevice, st));
   const double* K = tab + assemble_table_doubles(g.dim, -1);
   for (int col = 0; col < (1 << g.dim); ++col) {

@@ -486,9 +486,10 @@ __device__ __forceinline__ Cls classify(const Geom& g, int mV, long long t) {
     const int v = (int)(t - node * g.NV);
     const int ix = (int)(node % g.nn[0]);
     const long long pi = node / g.nn[0];
-    c.type = ix & 1;
-    c.slab = ix >> 1;
-    c.loc = (int)(pi * g.NV + v);
+    const int q = ix % g.r;  // 0: vertex plane; else the q-th interior node line of the slab
+    c.type = q ? 1 : 0;
+    c.slab = ix / g.r;
+    c.loc = (int)(((q ? q - 1 : 0) * pn + pi) * g.NV + v);
   } else {
     // The pressure of cell column s belongs to I_s except the cell-constant
     // coefficient of the column's first cell, which joins V_s: with Dirichlet
@@ -497,8 +498,9 @@ __device__ __forceinline__ Cls classify(const Geom& g, int mV, long long t) {
     const long long u = t - g.nvel;
     const long long cell = u / g.NP;
     const int q = (int)(u - cell * g.NP);
-    const int a = q / (g.dim + 1), m = q % (g.dim + 1);
+    const int a = q / g.npd, m = q % g.npd;
     const long long cr = cell / g.n[0];
+    const long long base = (long long)(g.r - 1) * pn * g.NV;  // interior velocity of the slab
     c.slab = (int)(cell % g.n[0]);
     if (cr == 0 && m == 0) {
       c.type = 0;
@@ -508,10 +510,10 @@ __device__ __forceinline__ Cls classify(const Geom& g, int mV, long long t) {
       c.loc = (int)(pn * g.NV + g.nt + a);
     } else if (cr == 0) {
       c.type = 1;
-      c.loc = (int)(pn * g.NV + a * g.dim + m - 1);
+      c.loc = (int)(base + a * (g.npd - 1) + m - 1);
     } else {
       c.type = 1;
-      c.loc = (int)(pn * g.NV + (long long)g.nt * g.dim + (cr - 1) * g.NP + q);
+      c.loc = (int)(base + (long long)g.nt * (g.npd - 1) + (cr - 1) * g.NP + q);
     }
   }
   (void)mV;
@@ -521,7 +523,7 @@ __device__ __forceinline__ Cls classify(const Geom& g, int mV, long long t) {
 __device__ __forceinline__ bool is_pinned(const Geom& g, int pin, long long t) {
   if (!pin || t < g.nvel) return false;
   const long long u = t - g.nvel;
-  return u < g.NP && (u % (g.dim + 1)) == 0;  // cell 0, coefficient 0, every Radau node
+  return u < g.NP && (u % g.npd) == 0;  // cell 0, coefficient 0, every Radau node
 }
 
 template <typename T>
@@ -585,23 +587,24 @@ __global__ void extract_vv(CoarseView<T> v, const int* __restrict__ rowptr, cons
 template <typename T>
 __global__ void extract_vp(CoarseView<T> v, const double* __restrict__ vp, const double* __restrict__ pv) {
   const Geom& g = v.g;
-  const int d = g.dim;
-  const long long per = (long long)g.nloc * g.nt * d * (d + 1);
+  const int d = g.dim, npd = g.npd, r = g.r, r1 = g.r + 1;
+  const long long per = (long long)g.nloc * g.nt * d * npd;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.n_cells * per) return;
   const long long K = t / per;
   int u = (int)(t - K * per);
-  const int m = u % (d + 1);
-  u /= d + 1;
+  const int m = u % npd;
+  u /= npd;
   const int c = u % d;
   u /= d;
   const int a = u % g.nt;
   const int i = u / g.nt;
   const int cx = (int)(K % g.n[0]), cy = (int)((K / g.n[0]) % g.n[1]), cz = (int)(K / ((long long)g.n[0] * g.n[1]));
-  const long long vel = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9) * g.NV + a * d + c;
-  const long long pres = g.nvel + K * g.NP + a * (d + 1) + m;
-  put(v, vel, pres, vp[(((K * g.nloc + i) * g.nt + a) * d + c) * (d + 1) + m]);
-  put(v, pres, vel, pv[((K * g.nt + a) * (d + 1) + m) * (long long)g.nloc * d + i * d + c]);
+  const long long vel =
+      node_id(g, r * cx + i % r1, r * cy + (i / r1) % r1, r * cz + i / (r1 * r1)) * g.NV + a * d + c;
+  const long long pres = g.nvel + K * g.NP + a * npd + m;
+  put(v, vel, pres, vp[(((K * g.nloc + i) * g.nt + a) * d + c) * npd + m]);
+  put(v, pres, vel, pv[((K * g.nt + a) * npd + m) * (long long)g.nloc * d + i * d + c]);
 }
 
 // Identity rows for the unused pressure slots of the last vertex plane (it has
@@ -633,7 +636,8 @@ __global__ void obstacle_diag(CoarseView<T> v) {
     if (!used) v.D[((long long)s * mV + loc) * mV + loc] = (T)1;
     if (used) {
       // the moved coefficient's own slot in I_s (cell row ob[3] >= 1, coefficient 0)
-      const long long il = pn * g.NV + (long long)g.nt * g.dim + (g.ob[3] - 1) * g.NP + a * (g.dim + 1);
+      const long long il = (long long)(g.r - 1) * pn * g.NV + (long long)g.nt * (g.npd - 1) +
+                           (g.ob[3] - 1) * g.NP + a * g.npd;
       v.AII[((long long)s * mI + il) * mI + il] = (T)1;
     }
   }
@@ -720,7 +724,7 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   v.nsv = geom.n[0] + 1;
   const long long pn = (long long)geom.nn[1] * geom.nn[2];
   v.mV = (int)(pn * geom.NV + (has_obstacle(geom) ? 2 : 1) * geom.nt);
-  v.mI = (int)(pn * geom.NV + (long long)geom.n[1] * geom.n[2] * geom.NP - geom.nt);
+  v.mI = (int)((long long)(geom.r - 1) * pn * geom.NV + (long long)geom.n[1] * geom.n[2] * geom.NP - geom.nt);
   const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
   auto alloc = [&](T** p, long long n) {
     STG_CUDA_OK(cudaMalloc(p, sizeof(T) * (n > 0 ? n : 1)));
@@ -1019,7 +1023,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
   STG_CUDA_OK(cudaMemsetAsync(v.U, 0, sizeof(T) * nsv * mV * mV, st));
   extract_vv<T><<<grid_for(g.nvel, 128), 128, 0, st>>>(v, rowptr, colidx, vv);
   STG_LAUNCH_OK();
-  const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * (g.dim + 1);
+  const long long nvp = g.n_cells * g.nloc * g.nt * g.dim * g.npd;
   extract_vp<T><<<grid_for(nvp, 256), 256, 0, st>>>(v, vp, pv);
   STG_LAUNCH_OK();
   pin_diag<T><<<1, 32, 0, st>>>(v);

@@ -5,13 +5,14 @@
 // Eq. (3.2); the entry points permute at the boundary):
 //   vector  = [velocity | pressure]
 //   velocity: node-major, NV = (k+1)*dim values per Q2 node, index a*dim + c
-//   pressure: cell-major, NP = (k+1)*(dim+1) values per cell, index a*(dim+1) + m
+//   pressure: cell-major, NP = (k+1)*npd values per cell, index a*npd + m (npd = dim P_{r-1}:
+//             dim+1 for r = 2, 10 for r = 4 in 2D)
 //   Jvv     : block-CSR over Q2 nodes, dense NV x NV blocks (row (a,c), col (b,e)),
 //             the columns of a row ordered (z, y, x) lexicographically over the
 //             tensor-product stencil of the node
 //   Jvp     : per cell and local node: [cell][i][a][c][m]   (time-diagonal)
 //   Jpv     : per cell: [cell][a][m][i][c]                  (time-diagonal)
-//   patch   : local order [3^d nodes x NV | NP]; npatch = (k+1)(3^d d + d + 1)
+//   patch   : local order [(r+1)^d nodes x NV | NP]; npatch = (k+1)((r+1)^d d + npd)
 //   J_K^{-1}: one column-major npatch x npatch matrix per cell, cells ordered by
 //             colour (colour = sum_e (c_e & 1) 2^e) and lexicographically inside
 //             a colour
@@ -29,6 +30,8 @@ namespace stg {
 
 struct Geom {
   int dim, k, nt;
+  int r;                // velocity order of (Q_r)^d x P_{r-1}^disc: 2, or 4 (2D)
+  int npd;              // pressure coefficients of a cell per time node: dim P_{r-1}
   int n[3];             // cells per direction (1 beyond dim)
   int nn[3];            // Q2 nodes per direction (1 beyond dim)
   double lo[3], h[3];
@@ -64,20 +67,21 @@ __host__ __device__ __forceinline__ long long node_id(const Geom& g, int ix, int
 __host__ __device__ __forceinline__ long long cell_id(const Geom& g, int cx, int cy, int cz) {
   return cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz);
 }
-// Range of Q2 node indices coupled to node index i along one direction:
-// a vertex line (even i) touches two cells, an interior line (odd i) one.
-__host__ __device__ __forceinline__ void stencil_range(int i, int nn, int& lo, int& hi) {
-  const int r = (i & 1) ? 1 : 2;
-  lo = i - r < 0 ? 0 : i - r;
-  hi = i + r > nn - 1 ? nn - 1 : i + r;
+// Range of Q_r node indices coupled to node index i along one direction: a vertex line
+// (i % r == 0) touches two cells (r nodes either side), an interior line the nodes of its cell.
+__host__ __device__ __forceinline__ void stencil_range(int i, int nn, int& lo, int& hi, int r = 2) {
+  const int q = i % r;
+  const int l = q == 0 ? i - r : i - q, h = q == 0 ? i + r : i - q + r;
+  lo = l < 0 ? 0 : l;
+  hi = h > nn - 1 ? nn - 1 : h;
 }
 // Position of column node (jx,jy,jz) in the BCSR row of node (ix,iy,iz).
 __host__ __device__ __forceinline__ long long bcsr_slot(const Geom& g, const int* rowptr, int ix, int iy,
                                                         int iz, int jx, int jy, int jz) {
   int xl, xh, yl, yh, zl, zh;
-  stencil_range(ix, g.nn[0], xl, xh);
-  stencil_range(iy, g.nn[1], yl, yh);
-  stencil_range(iz, g.nn[2], zl, zh);
+  stencil_range(ix, g.nn[0], xl, xh, g.r);
+  stencil_range(iy, g.nn[1], yl, yh, g.r);
+  stencil_range(iz, g.nn[2], zl, zh, g.r);
   const int wx = xh - xl + 1, wy = yh - yl + 1;
   return (long long)rowptr[node_id(g, ix, iy, iz)] + ((long long)(jz - zl) * wy + (jy - yl)) * wx + (jx - xl);
 }
@@ -105,8 +109,13 @@ __host__ __device__ __forceinline__ long long patch_dof(const Geom& g, int cx, i
   const int vel = g.nloc * g.NV;
   if (mu < vel) {
     const int i = mu / g.NV, v = mu - i * g.NV;
-    const int lx = i % 3, ly = (i / 3) % 3, lz = i / 9;
-    return node_id(g, 2 * cx + lx, 2 * cy + ly, 2 * cz + lz) * g.NV + v;
+    if (g.r == 2) {
+      const int lx = i % 3, ly = (i / 3) % 3, lz = i / 9;
+      return node_id(g, 2 * cx + lx, 2 * cy + ly, 2 * cz + lz) * g.NV + v;
+    }
+    const int r1 = g.r + 1;
+    const int lx = i % r1, ly = (i / r1) % r1, lz = i / (r1 * r1);
+    return node_id(g, g.r * cx + lx, g.r * cy + ly, g.r * cz + lz) * g.NV + v;
   }
   return g.nvel + cell_id(g, cx, cy, cz) * g.NP + (mu - vel);
 }
@@ -115,20 +124,20 @@ __host__ __device__ __forceinline__ bool has_obstacle(const Geom& g) { return g.
 __host__ __device__ __forceinline__ bool cell_masked(const Geom& g, int cx, int cy) {
   return cx >= g.ob[0] && cx < g.ob[1] && cy >= g.ob[2] && cy < g.ob[3];
 }
-// Range of cell indices that contain Q2 node index i along one direction.
-__host__ __device__ __forceinline__ void node_cells(int i, int n, int& lo, int& hi) {
-  if (i & 1) {
-    lo = hi = (i - 1) / 2;
+// Range of cell indices that contain Q_r node index i along one direction.
+__host__ __device__ __forceinline__ void node_cells(int i, int n, int& lo, int& hi, int r = 2) {
+  if (i % r) {
+    lo = hi = i / r;
   } else {
-    lo = i / 2 - 1 < 0 ? 0 : i / 2 - 1;
-    hi = i / 2 > n - 1 ? n - 1 : i / 2;
+    lo = i / r - 1 < 0 ? 0 : i / r - 1;
+    hi = i / r > n - 1 ? n - 1 : i / r;
   }
 }
 // Cells containing node (ix, iy): (fluid, removed) counts.
 __host__ __device__ __forceinline__ void node_cell_counts(const Geom& g, int ix, int iy, int& fluid, int& removed) {
   int xl, xh, yl, yh;
-  node_cells(ix, g.n[0], xl, xh);
-  node_cells(iy, g.n[1], yl, yh);
+  node_cells(ix, g.n[0], xl, xh, g.r);
+  node_cells(iy, g.n[1], yl, yh, g.r);
   fluid = removed = 0;
   for (int cy = yl; cy <= yh; ++cy)
     for (int cx = xl; cx <= xh; ++cx) {
@@ -163,9 +172,9 @@ __host__ __device__ __forceinline__ int node_multiplicity(const Geom& g, int ix,
     return f > 0 ? f : r;
   }
   int m = 1;
-  if (!(ix & 1) && ix > 0 && ix < g.nn[0] - 1) m *= 2;
-  if (g.dim > 1 && !(iy & 1) && iy > 0 && iy < g.nn[1] - 1) m *= 2;
-  if (g.dim > 2 && !(iz & 1) && iz > 0 && iz < g.nn[2] - 1) m *= 2;
+  if (ix % g.r == 0 && ix > 0 && ix < g.nn[0] - 1) m *= 2;
+  if (g.dim > 1 && iy % g.r == 0 && iy > 0 && iy < g.nn[1] - 1) m *= 2;
+  if (g.dim > 2 && iz % g.r == 0 && iz > 0 && iz < g.nn[2] - 1) m *= 2;
   return m;
 }
 

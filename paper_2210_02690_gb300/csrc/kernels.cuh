@@ -37,6 +37,8 @@ void assemble_level_w(const Geom& g, const TimeData& td, const AsmCoef& cf, cons
 // right-hand side of Eq. (2.2) from nodal f, g (internal velocity layout) and v_prev ([node][c]);
 // the mass matrix comes from the assembly table of the level (assemble_level first)
 long long rhs_table_doubles(int dim);
+// Q4 transfer weights and P3disc child embeddings into constant memory (order 4).
+void upload_transfer4_tables();
 // Force of the fluid on the obstacle at every Radau node: out[2a + c] (device), x internal.
 void obstacle_forces(const Geom& g, double nu, const double* x_int, double* out, cudaStream_t st);
 void assemble_rhs_level(const Geom& g, const TimeData& td, const AsmCoef& cf, const double* tab, double* rt,

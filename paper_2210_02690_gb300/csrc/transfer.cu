@@ -10,6 +10,8 @@
 // Time nodes are not coarsened.  With an obstacle (2D) the spaces are those of the fluid
 // domain: P is zero on the fine unknowns outside it (Q2 nodes of removed cells only, the
 // pressure of removed cells), and P^T leaves their residual out of the coarse problem.
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -157,8 +159,122 @@ __global__ void restrict_pres(Geom gc, Geom gf, const VT* __restrict__ rf, VT* _
   bc[gc.nvel + t] = acc;
 }
 
+// ---------------------------------------------------------------- order 4 (2D)
+// Q4: a fine node on a coarse node takes its value; a fine node at coarse reference coordinate
+// -3/4, -1/4, 1/4, 3/4 of a coarse cell takes the cell's 5 nodal values with the Q4 Lagrange
+// weights there (c_W4).  P3disc: the child with offset o in {0,1}^2 gets the coefficients of
+// the coarse polynomial in its own reference coordinates, xi_c = xi_f / 2 + (o - 1/2):
+// binomial expansion of each monomial (c_E4[o][fine][coarse]).
+__constant__ double c_W4[4][5];
+__constant__ double c_E4[4][10][10];
+
+template <typename W>
+__device__ __forceinline__ int prolong4_1d(int f, int* idx, W* w) {
+  if (!(f & 1)) {
+    idx[0] = f >> 1;
+    w[0] = (W)1;
+    return 1;
+  }
+  const int cc = f >> 3, k = ((f - 8 * cc) - 1) >> 1;
+  for (int l = 0; l < 5; ++l) {
+    idx[l] = 4 * cc + l;
+    w[l] = (W)c_W4[k][l];
+  }
+  return 5;
+}
+
+// Fine node indices and weights of coarse node c along one direction (row c of P^T).
+template <typename W>
+__device__ __forceinline__ int restrict4_1d(int c, int nnf, int ncells, int* idx, W* w) {
+  int n = 0;
+  idx[n] = 2 * c;
+  w[n] = (W)1;
+  ++n;
+  const int cl = (c % 4 == 0) ? c / 4 - 1 : c / 4, ch = c / 4;
+  for (int cc = cl; cc <= ch; ++cc) {
+    if (cc < 0 || cc >= ncells) continue;
+    const int l = c - 4 * cc;
+    if (l < 0 || l > 4) continue;
+    for (int k = 0; k < 4; ++k) {
+      const int f = 8 * cc + 2 * k + 1;
+      if (f < nnf) {
+        idx[n] = f;
+        w[n] = (W)c_W4[k][l];
+        ++n;
+      }
+    }
+  }
+  return n;
+}
+
+template <typename VT>
+__global__ void prolong_vel4(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gf.nvel) return;
+  const int NV = gf.NV;
+  const long long node = t / NV;
+  const int v = (int)(t - node * NV);
+  const int fx = (int)(node % gf.nn[0]), fy = (int)(node / gf.nn[0]);
+  int ix[5], iy[5];
+  VT wx[5], wy[5];
+  const int nx = prolong4_1d<VT>(fx, ix, wx), ny = prolong4_1d<VT>(fy, iy, wy);
+  VT acc = 0;
+  for (int b = 0; b < ny; ++b)
+    for (int a = 0; a < nx; ++a) acc += wx[a] * wy[b] * xc[node_id(gc, ix[a], iy[b], 0) * NV + v];
+  xf[t] += acc;
+}
+
+template <typename VT>
+__global__ void restrict_vel4(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.nvel) return;
+  const int NV = gc.NV;
+  const long long node = t / NV;
+  const int v = (int)(t - node * NV);
+  const int cx = (int)(node % gc.nn[0]), cy = (int)(node / gc.nn[0]);
+  int ix[9], iy[9];
+  VT wx[9], wy[9];
+  const int nx = restrict4_1d<VT>(cx, gf.nn[0], gc.n[0], ix, wx);
+  const int ny = restrict4_1d<VT>(cy, gf.nn[1], gc.n[1], iy, wy);
+  VT acc = 0;
+  for (int b = 0; b < ny; ++b)
+    for (int a = 0; a < nx; ++a) acc += wx[a] * wy[b] * rf[node_id(gf, ix[a], iy[b], 0) * NV + v];
+  bc[t] = acc;
+}
+
+template <typename VT>
+__global__ void prolong_pres4(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gf.npres) return;
+  const long long K = t / gf.NP;
+  const int q = (int)(t - K * gf.NP);
+  const int a = q / 10, m = q % 10;
+  const int fx = (int)(K % gf.n[0]), fy = (int)(K / gf.n[0]);
+  const int o = (fx & 1) + 2 * (fy & 1);
+  const VT* c = xc + gc.nvel + cell_id(gc, fx >> 1, fy >> 1, 0) * gc.NP + a * 10;
+  VT val = 0;
+  for (int j = 0; j < 10; ++j) val += (VT)c_E4[o][m][j] * c[j];
+  xf[gf.nvel + t] += val;
+}
+
+template <typename VT>
+__global__ void restrict_pres4(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.npres) return;
+  const long long K = t / gc.NP;
+  const int q = (int)(t - K * gc.NP);
+  const int a = q / 10, j = q % 10;
+  const int cx = (int)(K % gc.n[0]), cy = (int)(K / gc.n[0]);
+  VT acc = 0;
+  for (int o = 0; o < 4; ++o) {
+    const VT* f = rf + gf.nvel + cell_id(gf, 2 * cx + (o & 1), 2 * cy + (o >> 1), 0) * gf.NP + a * 10;
+    for (int m = 0; m < 10; ++m) acc += (VT)c_E4[o][m][j] * f[m];
+  }
+  bc[gc.nvel + t] = acc;
+}
+
 __device__ __forceinline__ long long cabi_index(const Geom& g, long long t) {
-  const long long R = (long long)g.dim * g.n_nodes, S = (long long)(g.dim + 1) * g.n_cells;
+  const long long R = (long long)g.dim * g.n_nodes, S = (long long)g.npd * g.n_cells;
   if (t < g.nvel) {
     const long long node = t / g.NV;
     const int v = (int)(t - node * g.NV);
@@ -168,8 +284,8 @@ __device__ __forceinline__ long long cabi_index(const Geom& g, long long t) {
   const long long u = t - g.nvel;
   const long long cell = u / g.NP;
   const int q = (int)(u - cell * g.NP);
-  const int a = q / (g.dim + 1), m = q % (g.dim + 1);
-  return a * (R + S) + R + cell * (g.dim + 1) + m;
+  const int a = q / g.npd, m = q % g.npd;
+  return a * (R + S) + R + cell * g.npd + m;
 }
 
 template <typename VT>
@@ -221,8 +337,52 @@ __global__ void convert_kernel(long long n, const S* __restrict__ in, D* __restr
 
 }  // namespace
 
+void upload_transfer4_tables() {
+  // Q4 Lagrange weights at coarse reference points -3/4, -1/4, 1/4, 3/4 (nodes -1, -1/2, 0, 1/2, 1)
+  double W[4][5];
+  const double nodes[5] = {-1.0, -0.5, 0.0, 0.5, 1.0};
+  for (int k = 0; k < 4; ++k) {
+    const double x = -0.75 + 0.5 * k;
+    for (int l = 0; l < 5; ++l) {
+      double v = 1.0;
+      for (int m = 0; m < 5; ++m)
+        if (m != l) v *= (x - nodes[m]) / (nodes[l] - nodes[m]);
+      W[k][l] = v;
+    }
+  }
+  // P3 monomials (a, b) of x and y exponents, by degree, x exponent falling
+  const int ex[10][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1}, {0, 2}, {3, 0}, {2, 1}, {1, 2}, {0, 3}};
+  auto binom = [](int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+  };
+  double E[4][10][10] = {};
+  for (int o = 0; o < 4; ++o) {
+    const double sx = (o & 1) - 0.5, sy = (o >> 1) - 0.5;
+    for (int j = 0; j < 10; ++j) {      // coarse monomial xi_c^a eta_c^b
+      const int a = ex[j][0], b = ex[j][1];
+      for (int m = 0; m < 10; ++m) {    // fine monomial xi_f^i eta_f^k
+        const int i = ex[m][0], k = ex[m][1];
+        if (i > a || k > b) continue;
+        E[o][m][j] = binom(a, i) * std::pow(0.5, i) * std::pow(sx, a - i) * binom(b, k) * std::pow(0.5, k) *
+                     std::pow(sy, b - k);
+      }
+    }
+  }
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_W4, W, sizeof(W)));
+  STG_CUDA_OK(cudaMemcpyToSymbol(c_E4, E, sizeof(E)));
+}
+
 template <typename VT>
 void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaStream_t st) {
+  if (gf.r == 4) {
+    prolong_vel4<VT><<<grid_for(gf.nvel, 256), 256, 0, st>>>(gc, gf, xc, xf);
+    STG_LAUNCH_OK();
+    prolong_pres4<VT><<<grid_for(gf.npres, 256), 256, 0, st>>>(gc, gf, xc, xf);
+    STG_LAUNCH_OK();
+    return;
+  }
   prolong_vel<VT><<<grid_for(gf.nvel, 256), 256, 0, st>>>(gc, gf, xc, xf);
   STG_LAUNCH_OK();
   prolong_pres<VT><<<grid_for(gf.npres, 256), 256, 0, st>>>(gc, gf, xc, xf);
@@ -231,6 +391,13 @@ void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaSt
 
 template <typename VT>
 void restrict_res(const Geom& gc, const Geom& gf, const VT* rf, VT* bc, cudaStream_t st) {
+  if (gf.r == 4) {
+    restrict_vel4<VT><<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, rf, bc);
+    STG_LAUNCH_OK();
+    restrict_pres4<VT><<<grid_for(gc.npres, 256), 256, 0, st>>>(gc, gf, rf, bc);
+    STG_LAUNCH_OK();
+    return;
+  }
   restrict_vel<VT><<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, rf, bc);
   STG_LAUNCH_OK();
   restrict_pres<VT><<<grid_for(gc.npres, 256), 256, 0, st>>>(gc, gf, rf, bc);

@@ -50,39 +50,36 @@ __global__ void __launch_bounds__(256) op_vel_rows(Geom g, const int* __restrict
   if (t >= g.nvel) return;
   const int NV = g.NV;
   const long long node = t / NV;
-  const int r = (int)(t - node * NV);
+  const int row = (int)(t - node * NV);
   VT acc = 0;
   const int b0 = rowptr[node], b1 = rowptr[node + 1];
 #pragma unroll 4
   for (int blk = b0; blk < b1; ++blk) {
-    const MT* vals = vv + (long long)blk * NV * NV + (long long)r * NV;
+    const MT* vals = vv + (long long)blk * NV * NV + (long long)row * NV;
     const VT* xc = x + (long long)colidx[blk] * NV;
     for (int s = 0; s < NV; ++s) acc += (VT)vals[s] * xc[s];
   }
   const int ix = (int)(node % g.nn[0]);
   const int iy = (int)((node / g.nn[0]) % g.nn[1]);
   const int iz = (int)(node / ((long long)g.nn[0] * g.nn[1]));
-  const int a = r / DIM, c = r % DIM;
+  const int a = row / DIM, c = row % DIM;
   const int id[3] = {ix, iy, iz};
   int clo[3], chi[3];
   for (int e = 0; e < 3; ++e) {
-    if (e >= DIM) {
+    if (e >= DIM)
       clo[e] = chi[e] = 0;
-    } else if (id[e] & 1) {
-      clo[e] = chi[e] = (id[e] - 1) / 2;
-    } else {
-      clo[e] = id[e] / 2 - 1 < 0 ? 0 : id[e] / 2 - 1;
-      chi[e] = id[e] / 2 > g.n[e] - 1 ? g.n[e] - 1 : id[e] / 2;
-    }
+    else
+      node_cells(id[e], g.n[e], clo[e], chi[e], g.r);
   }
+  const int r = g.r, r1 = g.r + 1, npd = g.npd;
   for (int cz = clo[2]; cz <= chi[2]; ++cz)
     for (int cy = clo[1]; cy <= chi[1]; ++cy)
       for (int cx = clo[0]; cx <= chi[0]; ++cx) {
-        const int il = (ix - 2 * cx) + 3 * (iy - 2 * cy) + 9 * (iz - 2 * cz);
+        const int il = (ix - r * cx) + r1 * (iy - r * cy) + r1 * r1 * (iz - r * cz);
         const long long K = cell_id(g, cx, cy, cz);
-        const MT* q = vp + (((K * g.nloc + il) * g.nt + a) * DIM + c) * (DIM + 1);
-        const VT* p = x + g.nvel + K * g.NP + a * (DIM + 1);
-        for (int m = 0; m <= DIM; ++m) acc += (VT)q[m] * p[m];
+        const MT* q = vp + (((K * g.nloc + il) * g.nt + a) * DIM + c) * npd;
+        const VT* p = x + g.nvel + K * g.NP + a * npd;
+        for (int m = 0; m < npd; ++m) acc += (VT)q[m] * p[m];
       }
   out[t] = b ? b[t] - acc : acc;
 }
@@ -248,18 +245,20 @@ __global__ void __launch_bounds__(256) op_pres_rows(Geom g, const MT* __restrict
   if (t >= g.npres) return;
   const long long K = t / g.NP;
   const int q = (int)(t - K * g.NP);
-  const int a = q / (DIM + 1), m = q % (DIM + 1);
+  const int npd = g.npd;
+  const int a = q / npd, m = q % npd;
   const int cx = (int)(K % g.n[0]);
   const int cy = (int)((K / g.n[0]) % g.n[1]);
   const int cz = (int)(K / ((long long)g.n[0] * g.n[1]));
-  const MT* row = pv + ((K * g.nt + a) * (DIM + 1) + m) * (long long)g.nloc * DIM;
+  const MT* row = pv + ((K * g.nt + a) * npd + m) * (long long)g.nloc * DIM;
   VT acc = 0;
   if (DIM == 2 && cell_masked(g, cx, cy)) {  // removed cell: identity row
     out[g.nvel + t] = b ? b[g.nvel + t] - x[g.nvel + t] : x[g.nvel + t];
     return;
   }
+  const int r = g.r, r1 = g.r + 1;
   for (int i = 0; i < g.nloc; ++i) {
-    const long long nd = node_id(g, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9);
+    const long long nd = node_id(g, r * cx + i % r1, r * cy + (i / r1) % r1, r * cz + i / (r1 * r1));
     const VT* xv = x + nd * g.NV + a * DIM;
     for (int e = 0; e < DIM; ++e) acc += (VT)row[i * DIM + e] * xv[e];
   }
@@ -279,6 +278,7 @@ __global__ void __launch_bounds__(256) invert_kernel(Geom g, long long p0, const
                                                      long long stride, int* status, int equil, CT* scratch,
                                                      const int* __restrict__ only) {
   const int n = g.npatch, NV = g.NV, nloc = g.nloc, dim = g.dim, nt = g.nt;
+  const int gr = g.r, gr1 = g.r + 1, npd = g.npd;
   const long long p = p0 + blockIdx.x;
   if (only && !only[p]) return;  // block-uniform: only the patches a pivot-free pass flagged
   int cx, cy, cz;
@@ -312,18 +312,18 @@ __global__ void __launch_bounds__(256) invert_kernel(Geom g, long long p0, const
   const int nvv = nloc * nloc * NV * NV;
   for (int t = tid; t < nvv; t += nth) {
     const int s = t % NV, r = (t / NV) % NV, j = (t / (NV * NV)) % nloc, i = t / (NV * NV * nloc);
-    const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9,
-                                     2 * cx + j % 3, 2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+    const long long slot = bcsr_slot(g, rowptr, gr * cx + i % gr1, gr * cy + (i / gr1) % gr1, gr * cz + i / (gr1 * gr1),
+                                     gr * cx + j % gr1, gr * cy + (j / gr1) % gr1, gr * cz + j / (gr1 * gr1));
     A[(i * NV + r) * n + j * NV + s] = (CT)vv[slot * NV * NV + r * NV + s];
   }
-  const int nvp = nloc * nt * dim * (dim + 1);
+  const int nvp = nloc * nt * dim * npd;
   const int voff = nloc * NV;
   for (int t = tid; t < nvp; t += nth) {
-    const int m = t % (dim + 1), c = (t / (dim + 1)) % dim, a = (t / ((dim + 1) * dim)) % nt;
-    const int i = t / ((dim + 1) * dim * nt);
-    const int vrow = i * NV + a * dim + c, prow = voff + a * (dim + 1) + m;
-    A[vrow * n + prow] = (CT)vp[(((cell * nloc + i) * nt + a) * dim + c) * (dim + 1) + m];
-    A[prow * n + vrow] = (CT)pv[((cell * nt + a) * (dim + 1) + m) * (long long)nloc * dim + i * dim + c];
+    const int m = t % npd, c = (t / npd) % dim, a = (t / (npd * dim)) % nt;
+    const int i = t / (npd * dim * nt);
+    const int vrow = i * NV + a * dim + c, prow = voff + a * npd + m;
+    A[vrow * n + prow] = (CT)vp[(((cell * nloc + i) * nt + a) * dim + c) * npd + m];
+    A[prow * n + vrow] = (CT)pv[((cell * nt + a) * npd + m) * (long long)nloc * dim + i * dim + c];
   }
   __syncthreads();
 
@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(256) invert_warp_kernel(Geom g, const int* __r
                                                           long long stride, int* status, int equil,
                                                           const int* __restrict__ only) {
   const int n = g.npatch, NV = g.NV, nloc = g.nloc, dim = g.dim, nt = g.nt;
+  const int gr = g.r, gr1 = g.r + 1, npd = g.npd;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int per = n * n + 3 * n;
@@ -455,17 +456,17 @@ __global__ void __launch_bounds__(256) invert_warp_kernel(Geom g, const int* __r
     const int nvv = nloc * nloc * NV * NV;
     for (int t = lane; t < nvv; t += 32) {
       const int s = t % NV, r = (t / NV) % NV, j = (t / (NV * NV)) % nloc, i = t / (NV * NV * nloc);
-      const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9,
-                                       2 * cx + j % 3, 2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+      const long long slot = bcsr_slot(g, rowptr, gr * cx + i % gr1, gr * cy + (i / gr1) % gr1, gr * cz + i / (gr1 * gr1),
+                                       gr * cx + j % gr1, gr * cy + (j / gr1) % gr1, gr * cz + j / (gr1 * gr1));
       A[(i * NV + r) * n + j * NV + s] = (CT)vv[slot * NV * NV + r * NV + s];
     }
-    const int nvp = nloc * nt * dim * (dim + 1);
+    const int nvp = nloc * nt * dim * npd;
     for (int t = lane; t < nvp; t += 32) {
-      const int m = t % (dim + 1), c = (t / (dim + 1)) % dim, a = (t / ((dim + 1) * dim)) % nt;
-      const int i = t / ((dim + 1) * dim * nt);
-      const int vrow = i * NV + a * dim + c, prow = voff + a * (dim + 1) + m;
-      A[vrow * n + prow] = (CT)vp[(((cell * nloc + i) * nt + a) * dim + c) * (dim + 1) + m];
-      A[prow * n + vrow] = (CT)pv[((cell * nt + a) * (dim + 1) + m) * (long long)nloc * dim + i * dim + c];
+      const int m = t % npd, c = (t / npd) % dim, a = (t / (npd * dim)) % nt;
+      const int i = t / (npd * dim * nt);
+      const int vrow = i * NV + a * dim + c, prow = voff + a * npd + m;
+      A[vrow * n + prow] = (CT)vp[(((cell * nloc + i) * nt + a) * dim + c) * npd + m];
+      A[prow * n + vrow] = (CT)pv[((cell * nt + a) * npd + m) * (long long)nloc * dim + i * dim + c];
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
@@ -911,23 +912,24 @@ __device__ __forceinline__ float patch_entry(const Geom& g, const int* __restric
                                              const MT* __restrict__ vp, const MT* __restrict__ pv, int cx, int cy,
                                              int cz, long long cell, int mu, int nu) {
   const int n = g.npatch, NV = g.NV, dim = g.dim, nloc = g.nloc, vel = nloc * NV;
+  const int gr = g.r, gr1 = g.r + 1, npd = g.npd;
   if (mu >= n || nu >= n) return mu == nu ? 1.f : 0.f;
   if (mu < vel) {
     const int i = mu / NV, v = mu - i * NV;
     if (nu < vel) {
       const int j = nu / NV, s2 = nu - j * NV;
-      const long long slot = bcsr_slot(g, rowptr, 2 * cx + i % 3, 2 * cy + (i / 3) % 3, 2 * cz + i / 9,
-                                       2 * cx + j % 3, 2 * cy + (j / 3) % 3, 2 * cz + j / 9);
+      const long long slot = bcsr_slot(g, rowptr, gr * cx + i % gr1, gr * cy + (i / gr1) % gr1, gr * cz + i / (gr1 * gr1),
+                                       gr * cx + j % gr1, gr * cy + (j / gr1) % gr1, gr * cz + j / (gr1 * gr1));
       return (float)vv[(slot * NV + v) * NV + s2];
     }
-    const int q = nu - vel, a = q / (dim + 1), m = q - a * (dim + 1);
+    const int q = nu - vel, a = q / npd, m = q - a * npd;
     const int ta = v / dim, c = v - ta * dim;
-    return ta == a ? (float)vp[(((cell * nloc + i) * g.nt + a) * dim + c) * (dim + 1) + m] : 0.f;
+    return ta == a ? (float)vp[(((cell * nloc + i) * g.nt + a) * dim + c) * npd + m] : 0.f;
   }
   if (nu >= vel) return 0.f;
-  const int q = mu - vel, a = q / (dim + 1), m = q - a * (dim + 1);
+  const int q = mu - vel, a = q / npd, m = q - a * npd;
   const int j = nu / NV, s2 = nu - j * NV, tb = s2 / dim, e = s2 - tb * dim;
-  return tb == a ? (float)pv[((cell * g.nt + a) * (dim + 1) + m) * (long long)nloc * dim + j * dim + e] : 0.f;
+  return tb == a ? (float)pv[((cell * g.nt + a) * npd + m) * (long long)nloc * dim + j * dim + e] : 0.f;
 }
 
 // Register-tiled variant for the larger patches (2D k >= 2, 3D): one CTA per patch, the
@@ -942,7 +944,7 @@ __device__ __forceinline__ float patch_entry(const Geom& g, const int* __restric
 // and the threads of column block cb write the new column j (-f_r / pivot; 1 / pivot on the pivot
 // row).  B x B FMAs per step read 2 B values from shared memory.
 template <int NPAD, int B, typename MT, typename FT>
-__global__ void __launch_bounds__((NPAD / B) * (NPAD / B), NPAD <= 64 ? 8 : (NPAD <= 88 ? 4 : (NPAD <= 112 ? 2 : 1)))
+__global__ void __launch_bounds__((NPAD / B) * (NPAD / B), NPAD <= 64 ? 8 : (NPAD <= 88 ? 4 : (NPAD <= 120 ? 2 : 1)))
     invert_tiles_kernel(Geom g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
                         const MT* __restrict__ vp, const MT* __restrict__ pv, FT* __restrict__ jinv,
                         long long stride, int* __restrict__ flags) {
@@ -1341,7 +1343,7 @@ void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const M
   STG_LAUNCH_OK();
 }
 
-bool kron_supported(const Geom& g) { return g.dim == 2 && g.nt >= 2 && g.nt <= 5; }
+bool kron_supported(const Geom& g) { return g.dim == 2 && g.r == 2 && g.nt >= 2 && g.nt <= 5; }
 
 void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData& td, float* Mk, float* Ak,
                 cudaStream_t st) {
@@ -1413,7 +1415,8 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
       else run(invert_pairs_kernel<42, 3, double, FT>, 3, 21 * 3, vv, vp, pv);
     }
     only = flags;
-  } else if (compute_f32 && flags && (n == 63 || n == 84 || n == 105 || n == 85 || n == 170)) {
+  } else if (compute_f32 && flags &&
+             (n == 63 || n == 84 || n == 105 || n == 85 || n == 170 || n == 60 || n == 120 || n == 180)) {
     // larger patches: register tiles, pivot-free, then the pivoting kernel for flagged patches
     STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
     auto tiles = [&](auto kern, int threads_t, auto* V, auto* VP, auto* PV) {
@@ -1421,9 +1424,15 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
       STG_LAUNCH_OK();
     };
     const bool f32src = vv32 != nullptr;
-    if (n == 63) {
+    if (n == 63 || n == 60) {
       if (f32src) tiles(invert_tiles_kernel<64, 8, float, FT>, 64, vv32, vp32, pv32);
       else tiles(invert_tiles_kernel<64, 8, double, FT>, 64, vv, vp, pv);
+    } else if (n == 120) {  // order 4, k = 1
+      if (f32src) tiles(invert_tiles_kernel<120, 8, float, FT>, 225, vv32, vp32, pv32);
+      else tiles(invert_tiles_kernel<120, 8, double, FT>, 225, vv, vp, pv);
+    } else if (n == 180) {  // order 4, k = 2: 12 x 12 tiles keep the 256 threads within the register file
+      if (f32src) tiles(invert_tiles_kernel<192, 12, float, FT>, 256, vv32, vp32, pv32);
+      else tiles(invert_tiles_kernel<192, 12, double, FT>, 256, vv, vp, pv);
     } else if (n == 84 || n == 85) {
       if (f32src) tiles(invert_tiles_kernel<88, 8, float, FT>, 121, vv32, vp32, pv32);
       else tiles(invert_tiles_kernel<88, 8, double, FT>, 121, vv, vp, pv);

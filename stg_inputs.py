@@ -196,6 +196,10 @@ WORKLOADS = {
     # 3D unit cube 48^3 -> 6^3, dG(1)
     "cube48_k1": dict(spec=MeshSpec(3, (48, 48, 48), (0.0,) * 3, (1.0,) * 3, 4, ALL3), k=1, nu=1e-3,
                       tau=0.01, newton=False, w="fourier", nu1=2, nu2=2),
+    # the paper's 2D element (Q4)^2 x P3disc on the channel, 352x64 quads -> 44x8 (4 levels): the
+    # same Q_r node grid as the 704x128 Q2 channel
+    "channel_q4": dict(spec=MeshSpec(2, (352, 64), (0.0, 0.0), (2.2, 0.41), 4, FACE_XLO | FACE_YLO | FACE_YHI,
+                                     order=4), k=1, nu=1e-3, tau=0.005, newton=True, w="channel", nu1=2, nu2=2),
     # 3D unit cube 32^3 -> 4^3 for the robustness study in k = 0, 1, 2 (Sec. 4, Table 3.2)
     "cube32": dict(spec=MeshSpec(3, (32, 32, 32), (0.0,) * 3, (1.0,) * 3, 4, ALL3), k=1, nu=1e-3,
                    tau=0.01, newton=False, w="fourier", nu1=2, nu2=2),
@@ -217,7 +221,7 @@ def scaled(spec: MeshSpec, factor: int, n_levels: int | None = None) -> MeshSpec
 
 def smoothed_dofs_per_cycle(spec: MeshSpec, k: int, nu1: int, nu2: int) -> int:
     """Space-time DoFs smoothed by one V-cycle: sum over levels >= 1 of (nu1 + nu2) N_l."""
-    return sum((nu1 + nu2) * n_dofs(spec.dim, spec.cells(l), k) for l in range(1, spec.n_levels))
+    return sum((nu1 + nu2) * n_dofs(spec.dim, spec.cells(l), k, spec.order) for l in range(1, spec.n_levels))
 
 
 

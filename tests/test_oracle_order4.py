@@ -167,6 +167,8 @@ def test_q4_element_and_rules():
     for q in range(10):
         assert abs(np.dot(w, x ** q) - (2 / (q + 1) if q % 2 == 0 else 0)) < 1e-14
     assert abs(np.dot(w, x ** 10) - 2 / 11) > 1e-6
+    xl, wl = np.polynomial.legendre.leggauss(5)            # the closed form is the Gauss-Legendre rule
+    assert np.allclose(x, xl, rtol=0, atol=1e-15) and np.allclose(w, wl, rtol=0, atol=1e-15)
     assert len(element.pdisc_exponents(4, 2)) == 10
     lev = mesh.Level(SPECS["box_dirichlet"], 0, 1)
     assert (lev.n_patch, lev.nn) == (60 * 2, (9, 9))
