@@ -346,7 +346,7 @@ def gpu_arm(args) -> None:
     seed = si.BASE_SEED + rank
     w_np = si.channel_w(spec, k, seed=seed)
     xs_np = si.reference_solution(spec, k, seed=seed + 1)
-    opts = dict(nu1=cfg["nu1"], nu2=cfg["nu2"], linearisation="newton")
+    opts = dict(nu1=cfg["nu1"], nu2=cfg["nu2"], linearisation="newton", overlap_launches=args.overlap)
     w = torch.from_numpy(w_np.ravel()).cuda()
     forms = {"f32": dict(vcycle_prec="f32", factor_prec="f32"), "f64": dict(vcycle_prec="f64", factor_prec="f64"),
              "bf16": dict(vcycle_prec="f32", factor_prec="bf16")}
@@ -470,7 +470,8 @@ def gpu_arm(args) -> None:
                    "smoothed_dofs_per_vcycle": per_cycle, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (FP32 J_K^{-1} of the finest level: "
                          f"{spec.n[0] * spec.n[1] * npatch * npatch * 4 / 1e6:.0f} MB)",
-                   "step": "update_linearisation (assembly + local inverses + coarse factorisation) + FGMRES to 1e-8"},
+                   "step": "update_linearisation (assembly + local inverses + coarse factorisation) + FGMRES to 1e-8",
+                   "launch_overlap": bool(args.overlap)},
         "fgmres_iters": r32["iters"], "rel_res": r32["rel_res"], "setup_ms": r32["setup_ms"],
         "autotune": r32["autotune"],
         "time_to_tol_ms": r32["time_to_tol_ms"],
@@ -811,6 +812,9 @@ def main():
                     help="precision forms to time (f32, the headline, always runs; e.g. 'f32' for profiler runs)")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the finest mesh by this factor (small cases for profiler captures)")
+    ap.add_argument("--overlap", type=int, choices=[0, 1], default=1,
+                    help="overlap_launches of the headline workload's solvers (programmatic dependent "
+                         "launch of the V-cycle kernels; 1 is the library default)")
     ap.add_argument("--levels", type=int, default=0,
                     help="with --scale: number of levels of the smaller copy (e.g. --scale 4 --levels 2 "
                          "keeps the 88x16 coarse level)")

@@ -110,6 +110,12 @@ typedef struct {
                            /* FP64 solve per cycle, no refinement, but an FP64       */
                            /* factorisation ~20x slower on GB300); the FP64 V-cycle  */
                            /* always uses FP64 coarse factors                         */
+  int overlap_launches;    /* 1 (default): the V-cycle's kernels are launched with    */
+                           /* programmatic dependent launch, so each launch may begin */
+                           /* before its predecessor is retired; every such kernel    */
+                           /* waits for its predecessor's completion before touching  */
+                           /* memory, so results are identical with 0.  Not applied   */
+                           /* inside the branches of a stg_batch graph.               */
 } stg_options;
 
 /* Fills the defaults listed above.  Returns STG_EINVAL for a null pointer. */
@@ -227,9 +233,11 @@ stg_status stg_get_sizes(const stg_ctx* ctx, int level, long long* n_dofs, long 
 stg_status stg_get_local_inverse(const stg_ctx* ctx, int level, long long cell, double* out);
 
 /* Instrumentation.  stg_profile(ctx, 1) records CUDA events on the context's
- * stream around every launch of the smoother's colour kernel on the finest
- * level (y_K = J_K^{-1} R_K r for the cells of one colour, Eq. (3.4)) and
- * accumulates their device time; stg_profile(ctx, 0) stops and resets.  The
+ * stream around the launches of the smoother's colour kernel on the finest
+ * level (y_K = J_K^{-1} R_K r for the cells of one colour, Eq. (3.4)) in one
+ * sweep per V-cycle (the last post-smoothing sweep, or the last pre-smoothing
+ * sweep when nu2 = 0; the last sweep of stg_smooth) and accumulates their
+ * device time; stg_profile(ctx, 0) stops and resets.  The
  * V-cycle graph is recaptured when the setting changes.  stg_profile_read
  * returns the accumulated milliseconds, the number of launches and the number
  * of patches they processed (host pointers, each may be NULL). */

@@ -59,7 +59,7 @@ class stg_options(ctypes.Structure):
                 ("gamma2", ctypes.c_double), ("factor_prec", ctypes.c_int), ("vcycle_prec", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
                 ("gmres_atol", ctypes.c_double), ("use_graph", ctypes.c_int), ("coarse_refine", ctypes.c_int),
-                ("coarse_prec", ctypes.c_int)]
+                ("coarse_prec", ctypes.c_int), ("overlap_launches", ctypes.c_int)]
 
 
 class stg_cnn_desc(ctypes.Structure):

@@ -18,6 +18,11 @@ long long& launch_counter() {
   return n;
 }
 
+bool& launch_overlap() {
+  static thread_local bool on = false;
+  return on;
+}
+
 // ------------------------------------------------------------------ geometry
 Geom make_geom(const stg_mesh& m, int level, int k) {
   Geom g{};
@@ -413,6 +418,11 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
   const FT* jinv = (const FT*)L.jinv;
   const int ncol = 1 << g.dim;
   for (int s = 0; s < sweeps; ++s) {
+    // with profiling on, the colour launches of one sweep per V-cycle are bracketed by events
+    // (the last post-smoothing sweep of the finest level; the last pre-smoothing sweep when
+    // there is no post-smoothing): each event node is a graph node of its own, so a sample
+    // keeps the timed cycle close to the uninstrumented one
+    const bool prof_sweep = s == sweeps - 1 && (!x_zero || c->opt.nu2 == 0);
     if (c->opt.smoother == STG_VANKA_AVERAGED) {
       const VT* res = b;
       if (!(x_zero && s == 0)) {
@@ -420,7 +430,8 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
         res = r;
       }
       for (int col = 0; col < ncol; ++col) {
-        const bool prof = c->prof_on && l == (int)c->lv.size() - 1 && c->prof_used + 2 <= (int)c->prof_ev.size();
+        const bool prof = prof_sweep && c->prof_on && l == (int)c->lv.size() - 1 &&
+                          c->prof_used + 2 <= (int)c->prof_ev.size();
         if (prof) record_event(c->prof_ev[c->prof_used], c->st);
         vanka_colour<VT, FT>(g, col, jinv, res, z, (VT)1, c->st, L.colour_variant);
         if (prof) {
@@ -437,7 +448,8 @@ void smooth_level(stg_ctx* c, int l, int sweeps, bool x_zero) {
           residual<VT>(c, L, x, b, r);
           res = r;
         }
-        const bool prof = c->prof_on && l == (int)c->lv.size() - 1 && c->prof_used + 2 <= (int)c->prof_ev.size();
+        const bool prof = prof_sweep && c->prof_on && l == (int)c->lv.size() - 1 &&
+                          c->prof_used + 2 <= (int)c->prof_ev.size();
         if (prof) record_event(c->prof_ev[c->prof_used], c->st);
         vanka_colour<VT, FT>(g, col, jinv, res, x, (VT)c->opt.omega, c->st, L.colour_variant);
         if (prof) {
@@ -498,7 +510,7 @@ void vcycle_level(stg_ctx* c, int l) {
   }
   LevelBufs& L = c->lv[l];
   LevelBufs& Lc = c->lv[l - 1];
-  STG_CUDA_OK(cudaMemsetAsync(L.x, 0, sizeof(VT) * L.g.N, c->st));
+  fill_zero<VT>(L.g.N, (VT*)L.x, c->st);
   smooth_level<VT, FT>(c, l, c->opt.nu1, true);
   residual<VT>(c, L, (const VT*)L.x, (const VT*)L.b, (VT*)L.r);
   restrict_res<VT>(Lc.g, L.g, (const VT*)L.r, (VT*)Lc.b, c->st);
@@ -509,6 +521,7 @@ void vcycle_level(stg_ctx* c, int l) {
 
 // V-cycle from c->vin (FP64 internal) to c->vout (FP64 internal)
 void vcycle_body(stg_ctx* c) {
+  const OverlapScope overlap(c->opt.overlap_launches != 0);
   LevelBufs& F = c->lv.back();
   const int top = (int)c->lv.size() - 1;
   if (vc64(c)) {
@@ -857,6 +870,7 @@ stg_status validate(const stg_mesh* m, int k, const stg_options* o) {
   if (o->coarse_refine < 0 || o->coarse_refine > 20) throw Error{STG_EINVAL, "coarse_refine must be in 0..20"};
   if (o->coarse_prec != STG_F64 && o->coarse_prec != STG_F32)
     throw Error{STG_EINVAL, "coarse_prec must be STG_F64 or STG_F32"};
+  if (o->overlap_launches != 0 && o->overlap_launches != 1) throw Error{STG_EINVAL, "overlap_launches must be 0 or 1"};
   return STG_OK;
 }
 
@@ -889,6 +903,7 @@ stg_status stg_options_default(stg_options* o) {
   o->use_graph = 1;
   o->coarse_refine = 1;
   o->coarse_prec = STG_F32;
+  o->overlap_launches = 1;
   return STG_OK;
 }
 
@@ -1389,7 +1404,7 @@ stg_status stg_profile(stg_ctx* c, int enable) {
   if (!c) return STG_EINVAL;
   try {
     if (enable && c->prof_ev.empty()) {
-      const int per_cycle = 2 * (c->opt.nu1 + c->opt.nu2) * (1 << c->mesh.dim);
+      const int per_cycle = 2 * (1 << c->mesh.dim);  // one sweep's colour launches per V-cycle
       c->prof_ev.resize(per_cycle);
       for (auto& e : c->prof_ev) STG_CUDA_OK(cudaEventCreate(&e));
     }
@@ -1565,6 +1580,10 @@ stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out) {
         stg_ctx* c = B->ctx[p];
         const cudaStream_t saved = c->st;
         c->st = B->branch[p];
+        // branch bodies are captured with ordinary launches: programmatic edges are not
+        // relied on inside conditional-node bodies
+        const int saved_overlap = c->opt.overlap_launches;
+        c->opt.overlap_launches = 0;
         const long long before = launch_counter();
         cudaError_t ce = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0,
                                                        cudaStreamCaptureModeThreadLocal);
@@ -1575,6 +1594,7 @@ stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out) {
             cudaGraph_t g2 = nullptr;
             cudaStreamEndCapture(c->st, &g2);
             c->st = saved;
+            c->opt.overlap_launches = saved_overlap;
             launch_counter() = before;
             throw;
           }
@@ -1582,6 +1602,7 @@ stg_status stg_batch_create(int n, stg_ctx* const* ctxs, stg_batch** out) {
           ce = cudaStreamEndCapture(c->st, &g2);
         }
         c->st = saved;
+        c->opt.overlap_launches = saved_overlap;
         B->branch_kernels[p] = launch_counter() - before;
         launch_counter() = before;  // capturing enqueues nothing; launches are counted per live branch
         STG_CUDA_OK(ce);

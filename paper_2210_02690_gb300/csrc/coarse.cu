@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(1024) gj_unpermute_kernel(int m, T* const* As,
 template <typename T>
 __global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, T alpha, const T* const* As, int lda,
                                                     const T* const* xs, T beta, T* const* ys) {
+  pdl_wait();
   const T* A = As[blockIdx.y];
   const T* x = xs[blockIdx.y];
   T* y = ys[blockIdx.y];
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(256) bgemv2_kernel(int M, int N0, int N1, T al
                                                      const T* const* x0s, const T* const* A1s,
                                                      const T* const* x1s, const T* const* cs, T beta,
                                                      T* const* ys) {
+  pdl_wait();
   const int b = blockIdx.y;
   const int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
   if (row >= M) return;
@@ -672,6 +674,7 @@ __global__ void schur_combine(CoarseView<T> v, const T* __restrict__ C) {
 
 template <typename T>
 __global__ void gather_rhs(CoarseView<T> v, const double* __restrict__ b, T* __restrict__ bV, T* __restrict__ bI) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= v.g.N) return;
   const Cls c = classify(v.g, v.mV, t);
@@ -685,6 +688,7 @@ __global__ void gather_rhs(CoarseView<T> v, const double* __restrict__ b, T* __r
 template <typename T>
 __global__ void scatter_sol(CoarseView<T> v, const T* __restrict__ xV, const T* __restrict__ xI,
                             double* __restrict__ x) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= v.g.N) return;
   const Cls c = classify(v.g, v.mV, t);
@@ -694,6 +698,7 @@ __global__ void scatter_sol(CoarseView<T> v, const T* __restrict__ xV, const T* 
 // bV[t] -= cI[t-1](lower half) + cI[t](upper half)
 template <typename T>
 __global__ void rhs_combine(CoarseView<T> v, const T* __restrict__ cI, T* __restrict__ bV) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int mV = v.mV;
   if (t >= (long long)(v.nsi + 1) * mV) return;
@@ -987,8 +992,7 @@ static void gemv(int M, int N, T alpha, const T* const* A, int lda, const T* con
                  int batch, cudaStream_t st) {
   if (batch <= 0) return;
   dim3 grid((M + 7) / 8, batch);
-  bgemv_kernel<T><<<grid, 256, 0, st>>>(M, N, alpha, A, lda, x, beta, y);
-  STG_LAUNCH_OK();
+  launch_k(bgemv_kernel<T>, grid, 256, 0, st, M, N, alpha, A, lda, x, beta, y);
 }
 
 template <typename T>
@@ -1005,8 +1009,7 @@ static void gemv2(int M, int N0, int N1, T alpha, const T* const* A0, const T* c
                   const T* const* x1, const T* const* c, T beta, T* const* y, int batch, cudaStream_t st) {
   if (batch <= 0) return;
   dim3 grid((M + 7) / 8, batch);
-  bgemv2_kernel<T><<<grid, 256, 0, st>>>(M, N0, N1, alpha, A0, x0, A1, x1, c, beta, y);
-  STG_LAUNCH_OK();
+  launch_k(bgemv2_kernel<T>, grid, 256, 0, st, M, N0, N1, alpha, A0, x0, A1, x1, c, beta, y);
 }
 
 template <typename T>
@@ -1058,14 +1061,12 @@ template <typename T>
 void CoarseSolver<T>::solve(const double* b, double* x, cudaStream_t st) {
   const Geom& g = v.g;
   const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
-  STG_CUDA_OK(cudaMemsetAsync(bV, 0, sizeof(T) * nsv * mV, st));  // unused slots stay zero
-  gather_rhs<T><<<grid_for(g.N, 256), 256, 0, st>>>(v, b, bV, bI);
-  STG_LAUNCH_OK();
+  fill_zero<T>(nsv * mV, bV, st);  // unused slots stay zero
+  launch_k(gather_rhs<T>, grid_for(g.N, 256), 256, 0, st, v, b, bV, bI);
   const T one = 1, zero = 0, mone = -1;
   gemv<T>((int)mI, (int)mI, one, d_AII, (int)mI, d_bI, zero, d_gI, (int)nsi, st);
   gemv<T>((int)(2 * mV), (int)mI, one, d_AVI, (int)mI, d_gI, zero, d_cI, (int)nsi, st);
-  rhs_combine<T><<<grid_for(nsv * mV, 256), 256, 0, st>>>(v, cI, bV);
-  STG_LAUNCH_OK();
+  launch_k(rhs_combine<T>, grid_for(nsv * mV, 256), 256, 0, st, v, cI, bV);
   const int m = (int)mV;
   for (const auto& lv : levels) {
     // t_i = D_i^{-1} b_i (odd planes), then b_j -= L_j t_{j-st} + U_j t_{j+st} in one launch
@@ -1080,8 +1081,7 @@ void CoarseSolver<T>::solve(const double* b, double* x, cudaStream_t st) {
   }
   // x_I = g_I - W [x_V,s ; x_V,s+1]
   gemv2<T>((int)mI, (int)(2 * mV), 0, mone, d_W, d_xVs, nullptr, nullptr, d_gI, zero, d_xI, (int)nsi, st);
-  scatter_sol<T><<<grid_for(g.N, 256), 256, 0, st>>>(v, xV, xI, x);
-  STG_LAUNCH_OK();
+  launch_k(scatter_sol<T>, grid_for(g.N, 256), 256, 0, st, v, xV, xI, x);
 }
 
 template <typename T>

@@ -109,6 +109,9 @@ void inject_w(const Geom& gc, const Geom& gf, const double* wf, double* wc, cuda
 
 template <typename D, typename S>
 void convert(long long n, const S* in, D* out, cudaStream_t st);
+// x[0 .. n) = 0 by a kernel (not a memset), so that it takes part in launch overlap.
+template <typename VT>
+void fill_zero(long long n, VT* x, cudaStream_t st);
 
 // ---- BLAS-1 in FP64 (krylov.cu)
 // h[i] = <V_i, w>, i < m, V row-major (m x n, leading dim ldv); partial sums per block -> h.

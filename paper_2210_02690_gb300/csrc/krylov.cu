@@ -82,6 +82,7 @@ __global__ void multi_axpy_kernel(long long n, int m, const double* __restrict__
 }
 
 __global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) y[t] = a * x[t] + (b == 0.0 ? 0.0 : b * y[t]);
 }
@@ -116,8 +117,7 @@ void multi_axpy_add(long long n, int m, const double* Z, long long ldz, const do
 }
 
 void axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t st) {
-  axpby_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, x, b, y);
-  STG_LAUNCH_OK();
+  launch_k(axpby_kernel, grid_for(n, 256), 256, 0, st, n, a, x, b, y);
 }
 
 size_t dot_partial_doubles() { return (size_t)kDotBlocks * kMaxVec; }

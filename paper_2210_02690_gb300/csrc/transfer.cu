@@ -69,6 +69,7 @@ __device__ __forceinline__ int restrict_1d(int c, int nnf, int* idx, W* w) {
 
 template <typename VT>
 __global__ void prolong_vel(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gf.nvel) return;
   const int NV = gf.NV;
@@ -90,6 +91,7 @@ __global__ void prolong_vel(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __r
 
 template <typename VT>
 __global__ void prolong_pres(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gf.npres) return;
   const int d = gf.dim;
@@ -112,6 +114,7 @@ __global__ void prolong_pres(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __
 
 template <typename VT>
 __global__ void restrict_vel(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gc.nvel) return;
   const int NV = gc.NV;
@@ -135,6 +138,7 @@ __global__ void restrict_vel(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __
 
 template <typename VT>
 __global__ void restrict_pres(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gc.npres) return;
   const int d = gc.dim;
@@ -209,6 +213,7 @@ __device__ __forceinline__ int restrict4_1d(int c, int nnf, int ncells, int* idx
 
 template <typename VT>
 __global__ void prolong_vel4(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gf.nvel) return;
   const int NV = gf.NV;
@@ -226,6 +231,7 @@ __global__ void prolong_vel4(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __
 
 template <typename VT>
 __global__ void restrict_vel4(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gc.nvel) return;
   const int NV = gc.NV;
@@ -244,6 +250,7 @@ __global__ void restrict_vel4(Geom gc, Geom gf, const VT* __restrict__ rf, VT* _
 
 template <typename VT>
 __global__ void prolong_pres4(Geom gc, Geom gf, const VT* __restrict__ xc, VT* __restrict__ xf) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gf.npres) return;
   const long long K = t / gf.NP;
@@ -259,6 +266,7 @@ __global__ void prolong_pres4(Geom gc, Geom gf, const VT* __restrict__ xc, VT* _
 
 template <typename VT>
 __global__ void restrict_pres4(Geom gc, Geom gf, const VT* __restrict__ rf, VT* __restrict__ bc) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= gc.npres) return;
   const long long K = t / gc.NP;
@@ -329,8 +337,16 @@ __global__ void replicate_kernel(Geom g, const double* __restrict__ xp, double* 
   x0[t] = xp[(long long)(g.nt - 1) * blk + t % blk];
 }
 
+template <typename VT>
+__global__ void zero_kernel(long long n, VT* __restrict__ x) {
+  pdl_wait();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (VT)0;
+}
+
 template <typename D, typename S>
 __global__ void convert_kernel(long long n, const S* __restrict__ in, D* __restrict__ out) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) out[t] = cvt<D>(in[t]);
 }
@@ -377,31 +393,23 @@ void upload_transfer4_tables() {
 template <typename VT>
 void prolongate_add(const Geom& gc, const Geom& gf, const VT* xc, VT* xf, cudaStream_t st) {
   if (gf.r == 4) {
-    prolong_vel4<VT><<<grid_for(gf.nvel, 256), 256, 0, st>>>(gc, gf, xc, xf);
-    STG_LAUNCH_OK();
-    prolong_pres4<VT><<<grid_for(gf.npres, 256), 256, 0, st>>>(gc, gf, xc, xf);
-    STG_LAUNCH_OK();
+    launch_k(prolong_vel4<VT>, grid_for(gf.nvel, 256), 256, 0, st, gc, gf, xc, xf);
+    launch_k(prolong_pres4<VT>, grid_for(gf.npres, 256), 256, 0, st, gc, gf, xc, xf);
     return;
   }
-  prolong_vel<VT><<<grid_for(gf.nvel, 256), 256, 0, st>>>(gc, gf, xc, xf);
-  STG_LAUNCH_OK();
-  prolong_pres<VT><<<grid_for(gf.npres, 256), 256, 0, st>>>(gc, gf, xc, xf);
-  STG_LAUNCH_OK();
+  launch_k(prolong_vel<VT>, grid_for(gf.nvel, 256), 256, 0, st, gc, gf, xc, xf);
+  launch_k(prolong_pres<VT>, grid_for(gf.npres, 256), 256, 0, st, gc, gf, xc, xf);
 }
 
 template <typename VT>
 void restrict_res(const Geom& gc, const Geom& gf, const VT* rf, VT* bc, cudaStream_t st) {
   if (gf.r == 4) {
-    restrict_vel4<VT><<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, rf, bc);
-    STG_LAUNCH_OK();
-    restrict_pres4<VT><<<grid_for(gc.npres, 256), 256, 0, st>>>(gc, gf, rf, bc);
-    STG_LAUNCH_OK();
+    launch_k(restrict_vel4<VT>, grid_for(gc.nvel, 256), 256, 0, st, gc, gf, rf, bc);
+    launch_k(restrict_pres4<VT>, grid_for(gc.npres, 256), 256, 0, st, gc, gf, rf, bc);
     return;
   }
-  restrict_vel<VT><<<grid_for(gc.nvel, 256), 256, 0, st>>>(gc, gf, rf, bc);
-  STG_LAUNCH_OK();
-  restrict_pres<VT><<<grid_for(gc.npres, 256), 256, 0, st>>>(gc, gf, rf, bc);
-  STG_LAUNCH_OK();
+  launch_k(restrict_vel<VT>, grid_for(gc.nvel, 256), 256, 0, st, gc, gf, rf, bc);
+  launch_k(restrict_pres<VT>, grid_for(gc.npres, 256), 256, 0, st, gc, gf, rf, bc);
 }
 
 template <typename VT>
@@ -431,13 +439,20 @@ void replicate_end_value(const Geom& g, const double* xp, double* x0, cudaStream
   STG_LAUNCH_OK();
 }
 
+template <typename VT>
+void fill_zero(long long n, VT* x, cudaStream_t st) {
+  if (n <= 0) return;
+  launch_k(zero_kernel<VT>, grid_for(n, 256), 256, 0, st, n, x);
+}
+
 template <typename D, typename S>
 void convert(long long n, const S* in, D* out, cudaStream_t st) {
   if (n <= 0) return;
-  convert_kernel<D, S><<<grid_for(n, 256), 256, 0, st>>>(n, in, out);
-  STG_LAUNCH_OK();
+  launch_k(convert_kernel<D, S>, grid_for(n, 256), 256, 0, st, n, in, out);
 }
 
+template void fill_zero<double>(long long, double*, cudaStream_t);
+template void fill_zero<float>(long long, float*, cudaStream_t);
 template void prolongate_add<double>(const Geom&, const Geom&, const double*, double*, cudaStream_t);
 template void prolongate_add<float>(const Geom&, const Geom&, const float*, float*, cudaStream_t);
 template void restrict_res<double>(const Geom&, const Geom&, const double*, double*, cudaStream_t);

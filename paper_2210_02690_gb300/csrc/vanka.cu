@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) op_vel_rows(Geom g, const int* __restrict
                                                    const int* __restrict__ colidx, const MT* __restrict__ vv,
                                                    const MT* __restrict__ vp, const VT* __restrict__ x,
                                                    const VT* __restrict__ b, VT* __restrict__ out) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.nvel) return;
   const int NV = g.NV;
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const 
                                                         const float* __restrict__ Mk, const float* __restrict__ Ak,
                                                         const float* __restrict__ vp, const float* __restrict__ x,
                                                         const float* __restrict__ b, float* __restrict__ out) {
+  pdl_wait();
   constexpr int D = 2, NV = NT * D;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (node, a) pairs < 2^31 (checked by the caller)
   if (t >= g.n_nodes * NT) return;
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const 
 template <int DIM, typename MT, typename VT>
 __global__ void __launch_bounds__(256) op_pres_rows(Geom g, const MT* __restrict__ pv, const VT* __restrict__ x,
                                                     const VT* __restrict__ b, VT* __restrict__ out) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.npres) return;
   const long long K = t / g.NP;
@@ -555,143 +558,6 @@ __global__ void __launch_bounds__(256) invert_warp_kernel(Geom g, const int* __r
   }
 }
 
-// Register-resident variant for 2D patches (n = 21(k+1) <= 63): one thread per
-// row, PPB patches per CTA.  Gauss-Jordan without row interchanges on the
-// equilibrated J_K (eliminating the velocity unknowns before the pressure
-// unknowns of the saddle-point matrix needs none on these problems); a pivot
-// below 1e-3 (entries are O(1) after equilibration) flags the patch and the
-// pivoting kernel redoes it.  The columns are rotated by one position per step,
-// so the pivot column is always register 0 and the elimination loop needs no
-// dynamic register indexing; after n steps the columns are back in order.
-template <int N, int PPB, typename MT, typename FT>
-__global__ void __launch_bounds__(N * PPB, N == 42 ? 6 : 1) invert_rows_kernel(Geom g, const int* __restrict__ rowptr,
-                                                              const MT* __restrict__ vv, const MT* __restrict__ vp,
-                                                              const MT* __restrict__ pv, FT* __restrict__ jinv,
-                                                              long long stride, int* __restrict__ flags) {
-  constexpr int DIM = 2, NL = 9, NT = N / 21, NV = NT * DIM, NP = NT * (DIM + 1), VOFF = NL * NV;
-  static_assert(VOFF + NP == N, "2D Q2/P1disc patch");
-  constexpr int NR = (N + 3) / 4 * 4;  // pivot-row stride: float4 reads
-  __shared__ float s_abs[PPB][N][N + 1];
-  __shared__ __align__(16) float s_row[2][PPB][NR];  // double-buffered pivot row
-  __shared__ float s_cs[PPB][N];
-  __shared__ float s_rs[PPB][N];
-  __shared__ int s_bad[PPB];
-  const int pl = threadIdx.x / N, row = threadIdx.x % N;
-  for (long long p0 = (long long)blockIdx.x * PPB; p0 < g.n_cells; p0 += (long long)gridDim.x * PPB) {
-    const long long p = p0 + pl;
-    int cx = 0, cy = 0, cz = 0;
-    if (p < g.n_cells) patch_cell(g, p, cx, cy, cz);
-    const bool removed = p < g.n_cells && cell_masked(g, cx, cy);
-    const bool live = p < g.n_cells && !removed;
-    float a[N];
-    if (live) {
-      const long long cell = cell_id(g, cx, cy, cz);
-      if (row < VOFF) {
-        const int i = row / NV, v = row % NV, ta = v / DIM, c = v % DIM;
-        const int ix = 2 * cx + i % 3, iy = 2 * cy + i / 3;
-#pragma unroll
-        for (int j = 0; j < NL; ++j) {
-          const long long slot = bcsr_slot(g, rowptr, ix, iy, 0, 2 * cx + j % 3, 2 * cy + j / 3, 0);
-          const MT* b = vv + slot * NV * NV + v * NV;
-#pragma unroll
-          for (int s2 = 0; s2 < NV; ++s2) a[j * NV + s2] = (float)b[s2];
-        }
-        const MT* q = vp + (((cell * NL + i) * NT + ta) * DIM + c) * (DIM + 1);
-#pragma unroll
-        for (int m = 0; m < NP; ++m) a[VOFF + m] = (m / (DIM + 1) == ta) ? (float)q[m % (DIM + 1)] : 0.f;
-      } else {
-        const int qq = row - VOFF, ta = qq / (DIM + 1), m = qq % (DIM + 1);
-        const MT* q = pv + ((cell * NT + ta) * (DIM + 1) + m) * (long long)NL * DIM;
-#pragma unroll
-        for (int col = 0; col < VOFF; ++col) {
-          const int j = col / NV, s2 = col % NV;
-          a[col] = (s2 / DIM == ta) ? (float)q[j * DIM + s2 % DIM] : 0.f;
-        }
-#pragma unroll
-        for (int m2 = 0; m2 < NP; ++m2) a[VOFF + m2] = 0.f;
-      }
-    } else {
-#pragma unroll
-      for (int l = 0; l < N; ++l) a[l] = row == l ? 1.f : 0.f;  // identity keeps idle threads harmless
-    }
-    // equilibration: row scale, then column scale through a transposed copy
-    float mx = 0.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) mx = fmaxf(mx, fabsf(a[l]));
-    const float rs = mx > 0.f ? 1.f / mx : 1.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      a[l] *= rs;
-      s_abs[pl][l][row] = fabsf(a[l]);
-    }
-    s_rs[pl][row] = rs;
-    if (row == 0) s_bad[pl] = 0;
-    __syncthreads();
-    {
-      float cm = 0.f;
-#pragma unroll
-      for (int r = 0; r < N; ++r) cm = fmaxf(cm, s_abs[pl][row][r]);
-      s_cs[pl][row] = cm > 0.f ? 1.f / cm : 1.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int l = 0; l < N; ++l) a[l] *= s_cs[pl][l];
-    // elimination; column j sits in register 0 at step j.  The pivot row of step j goes to
-    // buffer j & 1: the next step writes the other buffer, so one barrier per step suffices
-    // (a thread that reaches step j + 2's write has passed step j + 1's barrier, which every
-    // thread reaches only after its reads of step j).
-    for (int j = 0; j < N; ++j) {
-      const bool isp = row == j;
-      float* sr = s_row[j & 1][pl];
-      if (isp) {
-        const float piv = a[0];
-        if (!(fabsf(piv) > 1e-3f) || isinf(piv)) s_bad[pl] = 1;
-        const float inv = 1.f / piv;
-        sr[0] = inv;
-#pragma unroll
-        for (int l = 1; l < N; ++l) sr[l] = a[l] * inv;
-      }
-      __syncthreads();
-      const float f = a[0];
-      float rv0 = 0.f;
-      // a[l] <- pivot row[l + 1] (pivot thread) or a[l + 1] - f row[l + 1], four entries a read;
-      // a[l + 1] is read before it is overwritten
-#pragma unroll
-      for (int l4 = 0; l4 < NR / 4; ++l4) {
-        const float4 q = reinterpret_cast<const float4*>(sr)[l4];
-        const float qv[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = 4 * l4 + u;  // pivot-row column; updates a[c - 1]
-          if (c == 0) {
-            rv0 = qv[u];
-          } else if (c < N) {
-            a[c - 1] = isp ? qv[u] : fmaf(-f, qv[u], a[c]);
-          }
-        }
-      }
-      a[N - 1] = isp ? rv0 : -f * rv0;
-    }
-    __syncthreads();
-    if (live) {
-      if (s_bad[pl]) {
-        if (row == 0) flags[p] = 1;
-      } else {
-        // J_K^{-1} = Dc A'^{-1} Dr, column-major: element (row, col) at col * N + row
-        FT* out = jinv + p * stride;
-        const float csr = s_cs[pl][row];
-#pragma unroll
-        for (int col = 0; col < N; ++col) out[col * N + row] = cvt<FT>(a[col] * csr * s_rs[pl][col]);
-      }
-    } else if (removed) {
-      FT* out = jinv + p * stride;
-      const float one = patch_entry_dead(g, cx, cy, row) ? 1.f : 0.f;
-      for (int col = 0; col < N; ++col) out[col * N + row] = cvt<FT>(col == row ? one : 0.f);
-    }
-    __syncthreads();
-  }
-}
-
 // Row r of the 2D local matrix J_K (local order: time node, 9 Q2 nodes x 2 components,
 // then the 3 P1disc coefficients per time node), gathered from the block-CSR velocity
 // blocks and the per-cell velocity-pressure blocks and rounded to FP32.
@@ -742,18 +608,18 @@ __device__ __forceinline__ float4 pack4(const float (&x)[N], int l4) {
   return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// One step of the rotated Gauss-Jordan elimination of invert_pairs_kernel for the two rows
-// (x, y) of a thread.  The pivot row is read unscaled from shared memory as float4 (raw[0] the
+// One step of the rotated Gauss-Jordan elimination of invert_triples_kernel for the three rows
+// (x, y, z) of a lane.  The pivot row is read unscaled from shared memory as float4 (raw[0] the
 // pivot); every row, the pivot row included, takes x[c - 1] = x[c] - (fx / pivot) raw[c]: with
 // fx = pivot - 1 the pivot row becomes x / pivot (up to about eps max(1, |pivot|)), so no row
-// needs a select per entry and the pivot row needs no scaling pass before the barrier.  ex = 1 on
-// the pivot row supplies the new last column, 1 / pivot.
+// needs a select per entry and the pivot row needs no scaling pass before it is published.
+// ex = 1 on the pivot row supplies the new last column, 1 / pivot; the other rows get -f / pivot.
 template <int N>
-__device__ __forceinline__ void pairs_update(float (&x)[N], float (&y)[N], const float* raw, float fx, float fy,
-                                             float ex, float ey) {
+__device__ __forceinline__ void triples_update(float (&x)[N], float (&y)[N], float (&z)[N], const float* raw,
+                                               float fx, float fy, float fz, float ex, float ey, float ez) {
   constexpr int NR = (N + 3) / 4 * 4;
   const float inv = 1.f / raw[0];
-  const float gx = fx * inv, gy = fy * inv;
+  const float gx = fx * inv, gy = fy * inv, gz = fz * inv;
 #pragma unroll
   for (int l4 = 0; l4 < NR / 4; ++l4) {
     const float4 q = reinterpret_cast<const float4*>(raw)[l4];
@@ -764,143 +630,160 @@ __device__ __forceinline__ void pairs_update(float (&x)[N], float (&y)[N], const
       if (c >= 1 && c < N) {
         x[c - 1] = fmaf(-gx, qv[u], x[c]);
         y[c - 1] = fmaf(-gy, qv[u], y[c]);
+        z[c - 1] = fmaf(-gz, qv[u], z[c]);
       }
     }
   }
   x[N - 1] = fmaf(-fx, inv, ex);
   y[N - 1] = fmaf(-fy, inv, ey);
+  z[N - 1] = fmaf(-fz, inv, ez);
 }
 
-// Register-resident variant for 2D patches with two rows per thread (rows 2t and 2t + 1;
-// (N + 1) / 2 threads per patch, PPB patches per CTA): each pivot-row value read from shared
-// memory feeds two FMAs, and the pivot row needs no per-entry select, so a step costs about
-// half the instructions of invert_rows_kernel per row.  Same method: Gauss-Jordan without row
-// interchanges on the equilibrated J_K, columns rotated so that the pivot column is always
-// register 0, a pivot below 1e-3 flags the patch for the pivoting kernel.
-template <int N, int PPB, typename MT, typename FT>
-__global__ void __launch_bounds__(((N + 1) / 2) * PPB, 6)
-    invert_pairs_kernel(Geom g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
-                        const MT* __restrict__ vp, const MT* __restrict__ pv, FT* __restrict__ jinv,
-                        long long stride, int* __restrict__ flags) {
-  constexpr int TP = (N + 1) / 2;
+// Elimination steps s L .. s L + L - 1 of invert_triples_kernel: their pivot rows are register set
+// S (0: x, 1: y, 2: z) of lanes 0 .. L - 1 of each group.  Pivot rows alternate between the two
+// buffers by the parity of the step, so one __syncwarp per step orders a buffer's next write
+// after every lane's reads of it.
+template <int N, int L, int S>
+__device__ __forceinline__ void triples_phase(float (&x)[N], float (&y)[N], float (&z)[N], float* buf0, float* buf1,
+                                              int t, bool& bad) {
   constexpr int NR = (N + 3) / 4 * 4;
-  static_assert(N % 2 == 0, "two rows per thread: even patch size");
-  __shared__ float s_abs[PPB][N][N + 1];
-  __shared__ __align__(16) float s_row[2][PPB][NR];
-  __shared__ float s_cs[PPB][N];
-  __shared__ float s_rs[PPB][N];
-  __shared__ int s_bad[PPB];
-  const int pl = threadIdx.x / TP, t = threadIdx.x % TP;
-  const int r0 = 2 * t, r1 = 2 * t + 1;
-  for (long long p0 = (long long)blockIdx.x * PPB; p0 < g.n_cells; p0 += (long long)gridDim.x * PPB) {
-    const long long p = p0 + pl;
+#pragma unroll 1
+  for (int jj = 0; jj < L; ++jj) {
+    const bool own = t == jj;
+    float* sr = ((S * L + jj) & 1) ? buf1 : buf0;
+    if (own) {
+      const float piv = S == 0 ? x[0] : S == 1 ? y[0] : z[0];
+      if (!(fabsf(piv) > 1e-3f) || isinf(piv)) bad = true;
+#pragma unroll
+      for (int l4 = 0; l4 < NR / 4; ++l4)
+        reinterpret_cast<float4*>(sr)[l4] = S == 0 ? pack4<N>(x, l4) : S == 1 ? pack4<N>(y, l4) : pack4<N>(z, l4);
+    }
+    __syncwarp();
+    const float fx = (S == 0 && own) ? x[0] - 1.f : x[0];
+    const float fy = (S == 1 && own) ? y[0] - 1.f : y[0];
+    const float fz = (S == 2 && own) ? z[0] - 1.f : z[0];
+    triples_update<N>(x, y, z, sr, fx, fy, fz, (S == 0 && own) ? 1.f : 0.f, (S == 1 && own) ? 1.f : 0.f,
+                      (S == 2 && own) ? 1.f : 0.f);
+  }
+}
+
+// Warp-synchronous variant for the 2D patches of 21 and 42 unknowns: a warp holds 32 / G patches
+// in lane groups of G (a power of two), L = N / 3 lanes of a group hold three rows each (rows t,
+// t + L, t + 2 L), the others hold zero rows.  Pivot rows pass through a per-warp shared buffer
+// behind __syncwarp only; with no CTA barrier in the elimination, one warp's step latency
+// (publish, synchronise, load, reciprocal) hides behind the other warps' FMAs, and each pivot
+// value loaded feeds three FMAs.  The method: Gauss-Jordan without row
+// interchanges on the equilibrated J_K (eliminating the velocity unknowns before the pressure
+// unknowns of the saddle-point matrix needs none on these problems), columns rotated by one
+// position per step so that the pivot column is always register 0 (no dynamic register
+// indexing; after n steps the columns are back in order); a pivot below 1e-3 (entries are O(1)
+// after equilibration) flags the patch and the pivoting kernel redoes it.
+template <int N, int WPB, int MAXR, typename MT, typename FT>
+__global__ void __launch_bounds__(32 * WPB) __maxnreg__(MAXR)
+    invert_triples_kernel(Geom g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
+                          const MT* __restrict__ vp, const MT* __restrict__ pv, FT* __restrict__ jinv,
+                          long long stride, int* __restrict__ flags) {
+  constexpr int L = N / 3;
+  constexpr int G = L <= 8 ? 8 : 16;
+  constexpr int PPW = 32 / G;
+  constexpr int NR = (N + 3) / 4 * 4;
+  static_assert(N % 3 == 0 && L <= 16, "three rows per lane, at most 16 lanes per patch");
+  __shared__ __align__(16) float s_row[WPB][2][PPW][NR];
+  __shared__ float s_rs[WPB][PPW][N];
+  __shared__ float s_cs[WPB][PPW][N];
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32, h = lane / G, t = lane % G;
+  const bool act = t < L;
+  const int r0 = t, r1 = t + L, r2 = t + 2 * L;
+  const long long groups = (g.n_cells + PPW - 1) / PPW;
+  for (long long q = (long long)blockIdx.x * WPB + w; q < groups; q += (long long)gridDim.x * WPB) {
+    const long long p = q * PPW + h;
     int cx = 0, cy = 0, cz = 0;
     if (p < g.n_cells) patch_cell(g, p, cx, cy, cz);
     const bool removed = p < g.n_cells && cell_masked(g, cx, cy);
-    const bool live = p < g.n_cells && !removed;
-    float a[N], b[N];
+    const bool live = p < g.n_cells && !removed && act;
+    float a[N], b[N], c[N];
     if (live) {
       const long long cell = cell_id(g, cx, cy, cz);
       gather_patch_row<N, MT>(g, rowptr, vv, vp, pv, cx, cy, cell, r0, a);
       gather_patch_row<N, MT>(g, rowptr, vv, vp, pv, cx, cy, cell, r1, b);
+      gather_patch_row<N, MT>(g, rowptr, vv, vp, pv, cx, cy, cell, r2, c);
     } else {
 #pragma unroll
-      for (int l = 0; l < N; ++l) {
-        a[l] = r0 == l ? 1.f : 0.f;  // identity keeps idle threads harmless
-        b[l] = r1 == l ? 1.f : 0.f;
+      for (int l = 0; l < N; ++l) {  // identity rows keep idle patches harmless; idle lanes hold zeros
+        a[l] = act && r0 == l ? 1.f : 0.f;
+        b[l] = act && r1 == l ? 1.f : 0.f;
+        c[l] = act && r2 == l ? 1.f : 0.f;
       }
     }
-    // equilibration: row scales, then column scales through a transposed copy
-    float ma = 0.f, mb = 0.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      ma = fmaxf(ma, fabsf(a[l]));
-      mb = fmaxf(mb, fabsf(b[l]));
-    }
-    const float rsa = ma > 0.f ? 1.f / ma : 1.f, rsb = mb > 0.f ? 1.f / mb : 1.f;
-#pragma unroll
-    for (int l = 0; l < N; ++l) {
-      a[l] *= rsa;
-      b[l] *= rsb;
-      s_abs[pl][l][r0] = fabsf(a[l]);
-      s_abs[pl][l][r1] = fabsf(b[l]);
-    }
-    s_rs[pl][r0] = rsa;
-    s_rs[pl][r1] = rsb;
-    if (t == 0) s_bad[pl] = 0;
-    __syncthreads();
+    // equilibration: row scales, then column scales by a butterfly maximum over the group (the
+    // scales need no rounding guarantee: the output undoes exactly the scales applied)
     {
-      float c0 = 0.f, c1 = 0.f;
-#pragma unroll 6
-      for (int r = 0; r < N; ++r) {
-        c0 = fmaxf(c0, s_abs[pl][r0][r]);
-        c1 = fmaxf(c1, s_abs[pl][r1][r]);
+      float ma = 0.f, mb = 0.f, mc = 0.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        ma = fmaxf(ma, fabsf(a[l]));
+        mb = fmaxf(mb, fabsf(b[l]));
+        mc = fmaxf(mc, fabsf(c[l]));
       }
-      s_cs[pl][r0] = c0 > 0.f ? 1.f / c0 : 1.f;
-      s_cs[pl][r1] = c1 > 0.f ? 1.f / c1 : 1.f;
+      const float ra = ma > 0.f ? __fdividef(1.f, ma) : 1.f, rb = mb > 0.f ? __fdividef(1.f, mb) : 1.f,
+                  rc = mc > 0.f ? __fdividef(1.f, mc) : 1.f;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        a[l] *= ra;
+        b[l] *= rb;
+        c[l] *= rc;
+      }
+      if (act) {
+        s_rs[w][h][r0] = ra;
+        s_rs[w][h][r1] = rb;
+        s_rs[w][h][r2] = rc;
+      }
     }
-    __syncthreads();
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      a[l] *= s_cs[pl][l];
-      b[l] *= s_cs[pl][l];
-    }
-    // two elimination steps per iteration: step j takes its pivot from row a (j even) or
-    // b (j odd) of thread j / 2, so the pivot row is a compile-time register array.  The
-    // pivot row of step j goes to buffer j & 1 unscaled (one barrier per step, as in
-    // invert_rows_kernel); each thread scales by the pivot itself.  The loop stays rolled:
-    // the rotation x[c - 1] = f(x[c]) keeps every array element in its own register.
-    for (int j = 0; j < N; j += 2) {
-      const bool own = t == (j >> 1);
-      {
-        float* sr = s_row[0][pl];
-        if (own) {
-          if (!(fabsf(a[0]) > 1e-3f) || isinf(a[0])) s_bad[pl] = 1;
+      float m = fmaxf(fabsf(a[l]), fmaxf(fabsf(b[l]), fabsf(c[l])));
 #pragma unroll
-          for (int l4 = 0; l4 < NR / 4; ++l4)
-            reinterpret_cast<float4*>(sr)[l4] = pack4<N>(a, l4);
-        }
-        __syncthreads();
-        const float fa = own ? a[0] - 1.f : a[0];
-        pairs_update<N>(a, b, sr, fa, b[0], own ? 1.f : 0.f, 0.f);
-      }
-      {
-        float* sr = s_row[1][pl];
-        if (own) {
-          if (!(fabsf(b[0]) > 1e-3f) || isinf(b[0])) s_bad[pl] = 1;
-#pragma unroll
-          for (int l4 = 0; l4 < NR / 4; ++l4)
-            reinterpret_cast<float4*>(sr)[l4] = pack4<N>(b, l4);
-        }
-        __syncthreads();
-        const float fb = own ? b[0] - 1.f : b[0];
-        pairs_update<N>(a, b, sr, a[0], fb, 0.f, own ? 1.f : 0.f);
-      }
+      for (int o = G / 2; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const float cs = m > 0.f ? __fdividef(1.f, m) : 1.f;
+      a[l] *= cs;
+      b[l] *= cs;
+      c[l] *= cs;
+      if (t == 0) s_cs[w][h][l] = cs;
     }
-    __syncthreads();
+    bool bad = false;
+    float* buf0 = s_row[w][0][h];
+    float* buf1 = s_row[w][1][h];
+    triples_phase<N, L, 0>(a, b, c, buf0, buf1, t, bad);
+    triples_phase<N, L, 1>(a, b, c, buf0, buf1, t, bad);
+    triples_phase<N, L, 2>(a, b, c, buf0, buf1, t, bad);
+    const unsigned votes = __ballot_sync(0xffffffffu, bad);
+    const bool patch_bad = ((votes >> (h * G)) & ((G == 32 ? 0xffffffffu : (1u << G) - 1u))) != 0u;
     if (live) {
-      if (s_bad[pl]) {
+      if (patch_bad) {
         if (t == 0) flags[p] = 1;
       } else {
         // J_K^{-1} = Dc A'^{-1} Dr, column-major: element (row, col) at col * N + row
         FT* out = jinv + p * stride;
-        const float ca = s_cs[pl][r0], cb = s_cs[pl][r1];
+        const float ca = s_cs[w][h][r0], cb = s_cs[w][h][r1], cc = s_cs[w][h][r2];
 #pragma unroll
         for (int col = 0; col < N; ++col) {
-          const float rc = s_rs[pl][col];
-          out[col * N + r0] = cvt<FT>(a[col] * ca * rc);
-          out[col * N + r1] = cvt<FT>(b[col] * cb * rc);
+          const float rs = s_rs[w][h][col];
+          out[col * N + r0] = cvt<FT>(a[col] * ca * rs);
+          out[col * N + r1] = cvt<FT>(b[col] * cb * rs);
+          out[col * N + r2] = cvt<FT>(c[col] * cc * rs);
         }
       }
-    } else if (removed) {
+    } else if (removed && act) {
       FT* out = jinv + p * stride;
-      const float o0 = patch_entry_dead(g, cx, cy, r0) ? 1.f : 0.f, o1 = patch_entry_dead(g, cx, cy, r1) ? 1.f : 0.f;
+      const float o0 = patch_entry_dead(g, cx, cy, r0) ? 1.f : 0.f, o1 = patch_entry_dead(g, cx, cy, r1) ? 1.f : 0.f,
+                  o2 = patch_entry_dead(g, cx, cy, r2) ? 1.f : 0.f;
       for (int col = 0; col < N; ++col) {
         out[col * N + r0] = cvt<FT>(col == r0 ? o0 : 0.f);
         out[col * N + r1] = cvt<FT>(col == r1 ? o1 : 0.f);
+        out[col * N + r2] = cvt<FT>(col == r2 ? o2 : 0.f);
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -935,7 +818,7 @@ __device__ __forceinline__ float patch_entry(const Geom& g, const int* __restric
 // Register-tiled variant for the larger patches (2D k >= 2, 3D): one CTA per patch, the
 // (padded) NPAD x NPAD matrix spread over a T x T grid of threads (T = NPAD / B), each holding a
 // B x B tile in registers.  Gauss-Jordan without row interchanges on the equilibrated J_K (the
-// velocity unknowns come before the pressure unknowns, as in invert_rows_kernel); a pivot below
+// velocity unknowns come before the pressure unknowns, as in invert_triples_kernel); a pivot below
 // 1e-3 flags the patch for the pivoting kernel.  Step j = cb B + jj runs over column blocks cb
 // and, unrolled, their columns jj, so a thread's pivot-row and pivot-column registers are
 // compile-time indices: the threads of column block cb publish column j, those of row block cb
@@ -1084,6 +967,7 @@ template <typename VT, typename FT, int RPL, int CB>
 __global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
                                                            long long stride, const VT* __restrict__ r,
                                                            VT* __restrict__ z, VT scale) {
+  pdl_wait();
   using AT = typename AccT<VT>::type;
   const int n = g.npatch;
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1228,6 +1112,7 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
                                                                  long long stride, const VT* __restrict__ r,
                                                                  VT* __restrict__ z, VT scale, unsigned bytes,
                                                                  unsigned stage_bytes) {
+  pdl_wait();
   using AT = typename AccT<VT>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int n = g.npatch;
@@ -1312,6 +1197,7 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
 
 template <typename VT>
 __global__ void vanka_update_kernel(Geom g, VT* __restrict__ d, VT* __restrict__ z, double omega) {
+  pdl_wait();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.N) return;
   int mult = 1;
@@ -1332,15 +1218,12 @@ template <typename MT, typename VT>
 void apply_operator(const Geom& g, const int* rowptr, const int* colidx, const MT* vv, const MT* vp, const MT* pv,
                     const VT* x, const VT* b, VT* out, cudaStream_t st) {
   if (g.dim == 2) {
-    op_vel_rows<2, MT, VT><<<grid_for(g.nvel, 256), 256, 0, st>>>(g, rowptr, colidx, vv, vp, x, b, out);
-    STG_LAUNCH_OK();
-    op_pres_rows<2, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
+    launch_k(op_vel_rows<2, MT, VT>, grid_for(g.nvel, 256), 256, 0, st, g, rowptr, colidx, vv, vp, x, b, out);
+    launch_k(op_pres_rows<2, MT, VT>, grid_for(g.npres, 256), 256, 0, st, g, pv, x, b, out);
   } else {
-    op_vel_rows<3, MT, VT><<<grid_for(g.nvel, 256), 256, 0, st>>>(g, rowptr, colidx, vv, vp, x, b, out);
-    STG_LAUNCH_OK();
-    op_pres_rows<3, MT, VT><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
+    launch_k(op_vel_rows<3, MT, VT>, grid_for(g.nvel, 256), 256, 0, st, g, rowptr, colidx, vv, vp, x, b, out);
+    launch_k(op_pres_rows<3, MT, VT>, grid_for(g.npres, 256), 256, 0, st, g, pv, x, b, out);
   }
-  STG_LAUNCH_OK();
 }
 
 bool kron_supported(const Geom& g) { return g.dim == 2 && g.r == 2 && g.nt >= 2 && g.nt <= 5; }
@@ -1367,14 +1250,12 @@ void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, c
     for (int c = 0; c < 5; ++c) tf.T[a][c] = (float)td.T[a][c];
   const unsigned grid = grid_for(g.n_nodes * g.nt, 256);
   switch (g.nt) {
-    case 2: op_vel_rows_kron<2><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
-    case 3: op_vel_rows_kron<3><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
-    case 4: op_vel_rows_kron<4><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
-    default: op_vel_rows_kron<5><<<grid, 256, 0, st>>>(g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    case 2: launch_k(op_vel_rows_kron<2>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    case 3: launch_k(op_vel_rows_kron<3>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    case 4: launch_k(op_vel_rows_kron<4>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    default: launch_k(op_vel_rows_kron<5>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
   }
-  STG_LAUNCH_OK();
-  op_pres_rows<2, float, float><<<grid_for(g.npres, 256), 256, 0, st>>>(g, pv, x, b, out);
-  STG_LAUNCH_OK();
+  launch_k(op_pres_rows<2, float, float>, grid_for(g.npres, 256), 256, 0, st, g, pv, x, b, out);
 }
 
 size_t invert_scratch_bytes(const Geom& g, int compute_f32) {
@@ -1407,12 +1288,17 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
       kern<<<(unsigned)grid, nthreads, 0, st>>>(g, rowptr, V, VP, PV, jinv, stride, flags);
       STG_LAUNCH_OK();
     };
+    // warp-synchronous kernels, 4 patches a warp (n = 21) or 2 (n = 42).  At n = 42 registers
+    // are allocated per SM sub-partition (16K each): 168 a thread leave 3 warps on each, 200 only
+    // 2.  The 168 cap costs a few spill slots outside the elimination loop and measured faster
+    // than both the spill-free 200 cap and the two-rows-per-thread CTA kernel this replaced
+    // (finest channel set-up 4.98 ms against 5.23 and 5.29 ms).
     if (vv32) {
-      if (n == 21) run(invert_rows_kernel<21, 8, float, FT>, 8, 21 * 8, vv32, vp32, pv32);
-      else run(invert_pairs_kernel<42, 3, float, FT>, 3, 21 * 3, vv32, vp32, pv32);
+      if (n == 21) run(invert_triples_kernel<21, 4, 128, float, FT>, 16, 128, vv32, vp32, pv32);
+      else run(invert_triples_kernel<42, 2, 168, float, FT>, 4, 64, vv32, vp32, pv32);
     } else {
-      if (n == 21) run(invert_rows_kernel<21, 8, double, FT>, 8, 21 * 8, vv, vp, pv);
-      else run(invert_pairs_kernel<42, 3, double, FT>, 3, 21 * 3, vv, vp, pv);
+      if (n == 21) run(invert_triples_kernel<21, 4, 128, double, FT>, 16, 128, vv, vp, pv);
+      else run(invert_triples_kernel<42, 2, 168, double, FT>, 4, 64, vv, vp, pv);
     }
     only = flags;
   } else if (compute_f32 && flags &&
@@ -1524,9 +1410,12 @@ bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, 
   if (resident < 1) return false;
   const long long want = (long long)sms * std::min(ctas_per_sm, resident);
   const unsigned grid = (unsigned)(cnt < want ? cnt : want);
-  vanka_colour_bulk_kernel<VT, FT, S><<<grid, threads, smem, st>>>(g, colour, jinv, stride, r, z, scale, bytes,
-                                                                    stage_bytes);
-  STG_LAUNCH_OK();
+  // an ordinary launch: the grid is one wave with a static split of the patches, which needs the
+  // CTAs spread evenly over idle SMs; scheduled early into the SMs that the previous kernel frees
+  // first, some SMs would take two CTAs and the launch would wait for them
+  const OverlapScope serial(false);
+  launch_k(vanka_colour_bulk_kernel<VT, FT, S>, grid, threads, smem, st, g, colour, jinv, stride, r, z, scale, bytes,
+           stage_bytes);
   return true;
 }
 
@@ -1572,7 +1461,7 @@ void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z,
   const size_t sm = (size_t)wpb * n * sizeof(VT);
   const unsigned grid = grid_for(cnt, wpb);
 #define STG_VC(RPL, CB) \
-  vanka_colour_kernel<VT, FT, RPL, CB><<<grid, threads, sm, st>>>(g, colour, jinv, stride, r, z, scale)
+  launch_k(vanka_colour_kernel<VT, FT, RPL, CB>, grid, threads, sm, st, g, colour, jinv, stride, r, z, scale)
 #define STG_VCB(RPL)      \
   if (cb_idx == 0)        \
     STG_VC(RPL, 4);       \
@@ -1595,13 +1484,11 @@ void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z,
   }
 #undef STG_VCB
 #undef STG_VC
-  STG_LAUNCH_OK();
 }
 
 template <typename VT>
 void vanka_update(const Geom& g, VT* d, VT* z, double omega, cudaStream_t st) {
-  vanka_update_kernel<VT><<<grid_for(g.N, 256), 256, 0, st>>>(g, d, z, omega);
-  STG_LAUNCH_OK();
+  launch_k(vanka_update_kernel<VT>, grid_for(g.N, 256), 256, 0, st, g, d, z, omega);
 }
 
 // explicit instantiations
