@@ -359,22 +359,6 @@ __global__ void __launch_bounds__(1024) gj_unpermute_kernel(int m, T* const* As,
   }
 }
 
-// y = alpha A x + beta y, batched; one warp per row.
-template <typename T>
-__global__ void __launch_bounds__(256) bgemv_kernel(int M, int N, T alpha, const T* const* As, int lda,
-                                                    const T* const* xs, T beta, T* const* ys) {
-  pdl_wait();
-  const T* A = As[blockIdx.y];
-  const T* x = xs[blockIdx.y];
-  T* y = ys[blockIdx.y];
-  const int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (row >= M) return;
-  T acc = 0;
-  for (int c = lane; c < N; c += 32) acc += A[(long long)row * lda + c] * x[c];
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if (lane == 0) y[row] = alpha * acc + (beta == (T)0 ? (T)0 : beta * y[row]);
-}
-
 // C = alpha (A0 B0 + A1 B1) + beta C, batched through pointer arrays, row-major (A: M x K, B:
 // K x N, C: M x N); a null A0/A1 (per item) drops its product.  64 x 64 tiles, 16-deep k slices
 // staged in shared memory, 4 x 4 outputs per thread.
@@ -436,36 +420,46 @@ __global__ void __launch_bounds__(256) bgemm2_kernel(int M, int N, int K, T alph
     }
 }
 
-// y = alpha (A0 x0 + A1 x1) + c + beta y, batched, one warp per row; a null A0/A1 (per item)
-// drops its term, a null c array drops c.  A0 is M x N0, A1 is M x N1, both row-major.
+// Row `item % M` of batch item `item / M` of a kMV step, by one warp.
 template <typename T>
-__global__ void __launch_bounds__(256) bgemv2_kernel(int M, int N0, int N1, T alpha, const T* const* A0s,
-                                                     const T* const* x0s, const T* const* A1s,
-                                                     const T* const* x1s, const T* const* cs, T beta,
-                                                     T* const* ys) {
-  pdl_wait();
-  const int b = blockIdx.y;
-  const int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (row >= M) return;
-  const T* A0 = A0s ? A0s[b] : nullptr;
-  const T* A1 = A1s ? A1s[b] : nullptr;
-  T acc = 0;
+__device__ __forceinline__ void mv_row(const CStep<T>& s, long long item, int lane) {
+  const int b = (int)(item / s.M), row = (int)(item - (long long)b * s.M);
+  const T* A0 = s.A0 ? s.A0[b] : nullptr;
+  const T* A1 = s.A1 ? s.A1[b] : nullptr;
+  const T* A2 = s.A2 ? s.A2[b] : nullptr;
+  T acc = 0, acc2 = 0;
   if (A0) {
-    const T* x = x0s[b];
-    for (int c = lane; c < N0; c += 32) acc += A0[(long long)row * N0 + c] * x[c];
+    const T* x = s.x0[b];
+    for (int c = lane; c < s.N0; c += 32) acc += A0[(long long)row * s.N0 + c] * x[c];
   }
   if (A1) {
-    const T* x = x1s[b];
-    for (int c = lane; c < N1; c += 32) acc += A1[(long long)row * N1 + c] * x[c];
+    const T* x = s.x1[b];
+    for (int c = lane; c < s.N1; c += 32) acc += A1[(long long)row * s.N1 + c] * x[c];
+  }
+  if (A2) {
+    const T* x = s.x2[b];
+    for (int c = lane; c < s.N2; c += 32) acc2 += A2[(long long)row * s.N2 + c] * x[c];
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (A2)  // the same for the whole warp
+    for (int off = 16; off > 0; off >>= 1) acc2 += __shfl_down_sync(0xffffffffu, acc2, off);
   if (lane == 0) {
-    T* y = ys[b];
-    T val = alpha * acc;
-    if (cs) val += cs[b][row];
-    if (beta != (T)0) val += beta * y[row];
+    T* y = s.y[b];
+    T val = s.alpha * acc;
+    if (A2) val += acc2;
+    if (s.c && s.c[b]) val += s.c[b][row];
+    if (s.beta != (T)0) val += s.beta * y[row];
     y[row] = val;
   }
+}
+
+// One kMV step as a launch of its own: 8 rows per CTA, one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) bgemv2_kernel(CStep<T> s) {
+  pdl_wait();
+  const int row = blockIdx.x * 8 + threadIdx.x / 32;
+  if (row >= s.M) return;
+  mv_row(s, (long long)blockIdx.y * s.M + row, threadIdx.x % 32);
 }
 
 // ---------------------------------------------------------------- DoF classification
@@ -695,20 +689,6 @@ __global__ void scatter_sol(CoarseView<T> v, const T* __restrict__ xV, const T* 
   x[t] = (double)(c.type == 0 ? xV[(long long)c.slab * v.mV + c.loc] : xI[(long long)c.slab * v.mI + c.loc]);
 }
 
-// bV[t] -= cI[t-1](lower half) + cI[t](upper half)
-template <typename T>
-__global__ void rhs_combine(CoarseView<T> v, const T* __restrict__ cI, T* __restrict__ bV) {
-  pdl_wait();
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int mV = v.mV;
-  if (t >= (long long)(v.nsi + 1) * mV) return;
-  const int s = (int)(t / mV), i = (int)(t % mV);
-  T val = bV[t];
-  if (s > 0) val -= cI[(long long)(s - 1) * 2 * mV + mV + i];
-  if (s < v.nsi) val -= cI[(long long)s * 2 * mV + i];
-  bV[t] = val;
-}
-
 template <typename T>
 T** upload_ptrs(const std::vector<T*>& h, std::vector<void*>& owned) {
   if (h.empty()) return nullptr;
@@ -770,11 +750,9 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
       gjb.olds = upload_ptrs(ho, owned);
     }
   }
-  alloc(&tV, nsv * mV);
   alloc(&xV, nsv * mV);
   alloc(&bI, nsi * mI);
   alloc(&gI, nsi * mI);
-  alloc(&cI, nsi * 2 * mV);
   alloc(&xI, nsi * mI);
   int* st = nullptr;
   STG_CUDA_OK(cudaMalloc(&st, sizeof(int) * 2));
@@ -782,7 +760,7 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   v.status = st;
 
   // per-slab pointer arrays for the interior elimination
-  std::vector<T*> pAII, pAIV, pAVI, pW, pC, pbI, pgI, pcI, pxVs, pxI;
+  std::vector<T*> pAII, pAIV, pAVI, pW, pC, pbI, pgI, pxVs, pxI;
   for (long long s = 0; s < nsi; ++s) {
     pAII.push_back(v.AII + s * mI * mI);
     pAIV.push_back(v.AIV + s * mI * 2 * mV);
@@ -791,7 +769,6 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
     pC.push_back(C + s * 4 * mV * mV);
     pbI.push_back(bI + s * mI);
     pgI.push_back(gI + s * mI);
-    pcI.push_back(cI + s * 2 * mV);
     pxVs.push_back(xV + s * mV);  // [x_V,s ; x_V,s+1] are contiguous
     pxI.push_back(xI + s * mI);
   }
@@ -802,7 +779,6 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   d_C = upload_ptrs(pC, owned);
   d_bI = upload_ptrs(pbI, owned);
   d_gI = upload_ptrs(pgI, owned);
-  d_cI = upload_ptrs(pcI, owned);
   d_xVs = upload_ptrs(pxVs, owned);
   d_xI = upload_ptrs(pxI, owned);
 
@@ -818,13 +794,9 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   for (long long st_ = 1; st_ < nsv; st_ *= 2) {
     CrLevel<T> lv{};
     lv.stride = st_;
-    // odd planes: D_i^{-1} (in place), GL_i, GU_i; forward t_i = D_i^{-1} b_i
-    std::vector<T*> oD, ob, ot, gA, gB, gC;
-    for (long long i = st_; i < nsv; i += 2 * st_) {
-      oD.push_back(blk(v.D, i));
-      ob.push_back(bV + i * mV);
-      ot.push_back(tV + i * mV);
-    }
+    // odd planes: D_i^{-1} (in place), GL_i, GU_i
+    std::vector<T*> oD, gA, gB, gC;
+    for (long long i = st_; i < nsv; i += 2 * st_) oD.push_back(blk(v.D, i));
     lv.n_odd = (int)oD.size();
     for (int pass = 0; pass < 2; ++pass)
       for (long long i = st_; i < nsv; i += 2 * st_) {
@@ -833,26 +805,30 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
         gC.push_back(blk(pass == 0 ? GL : GU, i));
       }
     lv.oD = upload_ptrs(oD, owned);
-    lv.ob = upload_ptrs(ob, owned);
-    lv.ot = upload_ptrs(ot, owned);
     lv.gA = upload_ptrs(gA, owned);
     lv.gB = upload_ptrs(gB, owned);
     lv.gC = upload_ptrs(gC, owned);
     // even planes with a neighbour: D update and the forward right-hand-side update share the
     // products' left factors (this level's L_j, U_j); new L/U blocks for the next level
-    std::vector<T*> eA0, ex0, eA1, ex1, ey, dB0, dB1, dC, uA, uB, uC;
+    std::vector<T*> eA0, eA1, ey, fA0, fx0, fA1, fx1, dB0, dB1, dC, uA, uB, uC, pB, pC;
     std::vector<T*> newL(curL), newU(curU);
     int n_left = 0, n_right = 0;
-    std::vector<T*> uAr, uBr, uCr;
+    std::vector<T*> uAr, uBr, uCr, pBr, pCr;
     for (long long j = 0; j < nsv; j += 2 * st_) {
       const bool has_l = j - st_ >= 0, has_r = j + st_ < nsv;
       if (!has_l && !has_r) continue;
+      T* pl = nullptr;
+      T* pr = nullptr;
+      if (has_l) alloc(&pl, mV * mV);
+      if (has_r) alloc(&pr, mV * mV);
       eA0.push_back(has_l ? curL[j] : nullptr);
-      ex0.push_back(has_l ? tV + (j - st_) * mV : nullptr);
       dB0.push_back(has_l ? blk(GU, j - st_) : nullptr);
       eA1.push_back(has_r ? curU[j] : nullptr);
-      ex1.push_back(has_r ? tV + (j + st_) * mV : nullptr);
       dB1.push_back(has_r ? blk(GL, j + st_) : nullptr);
+      fA0.push_back(pl);
+      fx0.push_back(has_l ? bV + (j - st_) * mV : nullptr);
+      fA1.push_back(pr);
+      fx1.push_back(has_r ? bV + (j + st_) * mV : nullptr);
       ey.push_back(bV + j * mV);
       dC.push_back(blk(v.D, j));
       if (has_l) {
@@ -861,6 +837,8 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
         uA.push_back(curL[j]);
         uB.push_back(blk(GL, j - st_));
         uC.push_back(p);
+        pB.push_back(blk(v.D, j - st_));  // D_{j-st}^{-1} once inverted
+        pC.push_back(pl);
         newL[j] = p;
         ++n_left;
       }
@@ -870,6 +848,8 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
         uAr.push_back(curU[j]);
         uBr.push_back(blk(GU, j + st_));
         uCr.push_back(p);
+        pBr.push_back(blk(v.D, j + st_));
+        pCr.push_back(pr);
         newU[j] = p;
         ++n_right;
       }
@@ -877,13 +857,17 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
     uA.insert(uA.end(), uAr.begin(), uAr.end());
     uB.insert(uB.end(), uBr.begin(), uBr.end());
     uC.insert(uC.end(), uCr.begin(), uCr.end());
+    pB.insert(pB.end(), pBr.begin(), pBr.end());
+    pC.insert(pC.end(), pCr.begin(), pCr.end());
     lv.n_left = n_left;
     lv.n_right = n_right;
     lv.n_even = (int)ey.size();
     lv.eA0 = upload_ptrs(eA0, owned);
-    lv.ex0 = upload_ptrs(ex0, owned);
     lv.eA1 = upload_ptrs(eA1, owned);
-    lv.ex1 = upload_ptrs(ex1, owned);
+    lv.fA0 = upload_ptrs(fA0, owned);
+    lv.fx0 = upload_ptrs(fx0, owned);
+    lv.fA1 = upload_ptrs(fA1, owned);
+    lv.fx1 = upload_ptrs(fx1, owned);
     lv.ey = upload_ptrs(ey, owned);
     lv.dB0 = upload_ptrs(dB0, owned);
     lv.dB1 = upload_ptrs(dB1, owned);
@@ -891,18 +875,20 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
     lv.uA = upload_ptrs(uA, owned);
     lv.uB = upload_ptrs(uB, owned);
     lv.uC = upload_ptrs(uC, owned);
-    // back substitution of the odd planes: x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}
-    std::vector<T*> bx, bt, bGL, bxl, qA1, qx1;
+    lv.pB = upload_ptrs(pB, owned);
+    lv.pC = upload_ptrs(pC, owned);
+    // back substitution of the odd planes: x_i = D_i^{-1} b_i - GL_i x_{i-st} - GU_i x_{i+st}
+    std::vector<T*> bx, bb, bGL, bxl, qA1, qx1;
     for (long long i = st_; i < nsv; i += 2 * st_) {
       bx.push_back(xV + i * mV);
-      bt.push_back(tV + i * mV);
+      bb.push_back(bV + i * mV);
       bGL.push_back(blk(GL, i));
       bxl.push_back(xV + (i - st_) * mV);
       qA1.push_back(i + st_ < nsv ? blk(GU, i) : nullptr);
       qx1.push_back(i + st_ < nsv ? xV + (i + st_) * mV : nullptr);
     }
     lv.bx = upload_ptrs(bx, owned);
-    lv.bt = upload_ptrs(bt, owned);
+    lv.bb = upload_ptrs(bb, owned);
     lv.bGL = upload_ptrs(bGL, owned);
     lv.bxl = upload_ptrs(bxl, owned);
     lv.qA1 = upload_ptrs(qA1, owned);
@@ -915,6 +901,53 @@ void CoarseSolver<T>::init(const Geom& geom, bool pure_dirichlet) {
   d_top = upload_ptrs(top, owned);
   d_topb = upload_ptrs(topb, owned);
   d_topx = upload_ptrs(topx, owned);
+
+  // the vertex-plane right-hand side update from the interiors: b_V,s -= A_VI,s-1 (upper rows)
+  // g_I,s-1 + A_VI,s (lower rows) g_I,s, with g_I = A_II^{-1} b_I
+  {
+    std::vector<T*> cA0, cx0, cA1, cx1, cy;
+    for (long long s = 0; s < nsv; ++s) {
+      cA0.push_back(s >= 1 ? v.AVI + (s - 1) * 2 * mV * mI + mV * mI : nullptr);
+      cx0.push_back(s >= 1 ? gI + (s - 1) * mI : nullptr);
+      cA1.push_back(s < nsi ? v.AVI + s * 2 * mV * mI : nullptr);
+      cx1.push_back(s < nsi ? gI + s * mI : nullptr);
+      cy.push_back(bV + s * mV);
+    }
+    d_cA0 = upload_ptrs(cA0, owned);
+    d_cx0 = upload_ptrs(cx0, owned);
+    d_cA1 = upload_ptrs(cA1, owned);
+    d_cx1 = upload_ptrs(cx1, owned);
+    d_cy = upload_ptrs(cy, owned);
+  }
+
+  // the solve plan: interior right-hand sides, reduction down the levels, the top block, back
+  // substitution up the levels, the interiors, the scatter.  Slots of bV that no unknown maps to
+  // are zeroed once (here) and stay zero: the rows of every operator the plan applies vanish there.
+  STG_CUDA_OK(cudaMemset(bV, 0, sizeof(T) * nsv * mV));
+  const T one = 1, zero = 0, mone = -1;
+  const int m = (int)mV;
+  auto mv = [&](int M, int N0, int N1, int N2, T alpha, T* const* A0, T* const* x0, T* const* A1, T* const* x1,
+                T* const* A2, T* const* x2, T beta, T* const* y, long long batch) {
+    if (batch <= 0) return;
+    plan.push_back(CStep<T>{kMV, M, N0, N1, N2, (int)batch, alpha, beta, A0, x0, A1, x1, A2, x2, nullptr, y});
+  };
+  auto element = [&](int kind) {
+    plan.push_back(CStep<T>{kind, 0, 0, 0, 0, 0, zero, zero, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                            nullptr, nullptr});
+  };
+  plan.clear();
+  element(kGather);
+  mv((int)mI, (int)mI, 0, 0, one, d_AII, d_bI, nullptr, nullptr, nullptr, nullptr, zero, d_gI, nsi);
+  mv(m, (int)mI, (int)mI, 0, mone, d_cA0, d_cx0, d_cA1, d_cx1, nullptr, nullptr, one, d_cy, nsv);
+  for (const auto& lv : levels)  // b_j -= PL_j b_{j-st} + PR_j b_{j+st} (even planes)
+    mv(m, m, m, 0, mone, lv.fA0, lv.fx0, lv.fA1, lv.fx1, nullptr, nullptr, one, lv.ey, lv.n_even);
+  mv(m, m, 0, 0, one, d_top, d_topb, nullptr, nullptr, nullptr, nullptr, zero, d_topx, 1);
+  for (auto it = levels.rbegin(); it != levels.rend(); ++it)  // x_i = D_i^{-1} b_i - GL_i x_{i-st} - GU_i x_{i+st}
+    mv(m, m, m, m, mone, it->bGL, it->bxl, it->qA1, it->qx1, it->oD, it->bb, zero, it->bx, it->n_odd);
+  // x_I = g_I - W [x_V,s ; x_V,s+1]
+  plan.push_back(CStep<T>{kMV, (int)mI, (int)(2 * mV), 0, 0, (int)nsi, mone, zero, d_W, d_xVs, nullptr, nullptr,
+                          nullptr, nullptr, d_gI, d_xI});
+  element(kScatter);
 }
 
 template <typename T>
@@ -988,14 +1021,6 @@ static void gj(int m, T* const* A, int batch, int* status, T* scratch, int* perm
 }
 
 template <typename T>
-static void gemv(int M, int N, T alpha, const T* const* A, int lda, const T* const* x, T beta, T* const* y,
-                 int batch, cudaStream_t st) {
-  if (batch <= 0) return;
-  dim3 grid((M + 7) / 8, batch);
-  launch_k(bgemv_kernel<T>, grid, 256, 0, st, M, N, alpha, A, lda, x, beta, y);
-}
-
-template <typename T>
 static void gemm2(int M, int N, int K, T alpha, const T* const* A0, const T* const* B0, const T* const* A1,
                   const T* const* B1, T beta, T* const* C, int batch, cudaStream_t st) {
   if (batch <= 0) return;
@@ -1004,12 +1029,16 @@ static void gemm2(int M, int N, int K, T alpha, const T* const* A0, const T* con
   STG_LAUNCH_OK();
 }
 
+// One plan step as a launch of its own.
 template <typename T>
-static void gemv2(int M, int N0, int N1, T alpha, const T* const* A0, const T* const* x0, const T* const* A1,
-                  const T* const* x1, const T* const* c, T beta, T* const* y, int batch, cudaStream_t st) {
-  if (batch <= 0) return;
-  dim3 grid((M + 7) / 8, batch);
-  launch_k(bgemv2_kernel<T>, grid, 256, 0, st, M, N0, N1, alpha, A0, x0, A1, x1, c, beta, y);
+static void run_step(const CStep<T>& s, const CoarseView<T>& v, const double* b, double* x, T* bV, T* bI,
+                     const T* xV, const T* xI, cudaStream_t st) {
+  if (s.kind == kGather)
+    launch_k(gather_rhs<T>, grid_for(v.g.N, 256), 256, 0, st, v, b, bV, bI);
+  else if (s.kind == kMV)
+    launch_k(bgemv2_kernel<T>, dim3((s.M + 7) / 8, s.batch), 256, 0, st, s);
+  else
+    launch_k(scatter_sol<T>, grid_for(v.g.N, 256), 256, 0, st, v, xV, xI, x);
 }
 
 template <typename T>
@@ -1049,6 +1078,8 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
     gj<T>(m, lv.oD, lv.n_odd, v.status, gj_scr, gj_perm, gj_fail, gjb, st);
     // [GL_i | GU_i] = D_i^{-1} [L_i | U_i]
     gemm2<T>(m, m, m, one, lv.gA, lv.gB, nullptr, nullptr, zero, lv.gC, 2 * lv.n_odd, st);
+    // PL_j = L_j D_{j-st}^{-1}, PR_j = U_j D_{j+st}^{-1} (the solve's forward products)
+    gemm2<T>(m, m, m, one, lv.uA, lv.pB, nullptr, nullptr, zero, lv.pC, lv.n_left + lv.n_right, st);
     // D_j -= L_j GU_{j-st} + U_j GL_{j+st}
     gemm2<T>(m, m, m, mone, lv.eA0, lv.dB0, lv.eA1, lv.dB1, one, lv.dC, lv.n_even, st);
     // L_j <- -L_j GL_{j-st}, U_j <- -U_j GU_{j+st}, into new blocks
@@ -1059,29 +1090,7 @@ void CoarseSolver<T>::factor(const int* rowptr, const int* colidx, const double*
 
 template <typename T>
 void CoarseSolver<T>::solve(const double* b, double* x, cudaStream_t st) {
-  const Geom& g = v.g;
-  const long long mV = v.mV, mI = v.mI, nsi = v.nsi, nsv = v.nsv;
-  fill_zero<T>(nsv * mV, bV, st);  // unused slots stay zero
-  launch_k(gather_rhs<T>, grid_for(g.N, 256), 256, 0, st, v, b, bV, bI);
-  const T one = 1, zero = 0, mone = -1;
-  gemv<T>((int)mI, (int)mI, one, d_AII, (int)mI, d_bI, zero, d_gI, (int)nsi, st);
-  gemv<T>((int)(2 * mV), (int)mI, one, d_AVI, (int)mI, d_gI, zero, d_cI, (int)nsi, st);
-  launch_k(rhs_combine<T>, grid_for(nsv * mV, 256), 256, 0, st, v, cI, bV);
-  const int m = (int)mV;
-  for (const auto& lv : levels) {
-    // t_i = D_i^{-1} b_i (odd planes), then b_j -= L_j t_{j-st} + U_j t_{j+st} in one launch
-    gemv<T>(m, m, one, lv.oD, m, lv.ob, zero, lv.ot, lv.n_odd, st);
-    gemv2<T>(m, m, m, mone, lv.eA0, lv.ex0, lv.eA1, lv.ex1, nullptr, one, lv.ey, lv.n_even, st);
-  }
-  gemv<T>(m, m, one, d_top, m, d_topb, zero, d_topx, 1, st);
-  for (auto it = levels.rbegin(); it != levels.rend(); ++it) {
-    const auto& lv = *it;
-    // x_i = t_i - GL_i x_{i-st} - GU_i x_{i+st}
-    gemv2<T>(m, m, m, mone, lv.bGL, lv.bxl, lv.qA1, lv.qx1, lv.bt, zero, lv.bx, lv.n_odd, st);
-  }
-  // x_I = g_I - W [x_V,s ; x_V,s+1]
-  gemv2<T>((int)mI, (int)(2 * mV), 0, mone, d_W, d_xVs, nullptr, nullptr, d_gI, zero, d_xI, (int)nsi, st);
-  launch_k(scatter_sol<T>, grid_for(g.N, 256), 256, 0, st, v, xV, xI, x);
+  for (const CStep<T>& s : plan) run_step<T>(s, v, b, x, bV, bI, xV, xI, st);
 }
 
 template <typename T>
