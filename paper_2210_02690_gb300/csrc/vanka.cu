@@ -7,6 +7,8 @@
 // accumulated colour by colour: cells of one colour share no velocity DoF and
 // pressure DoFs belong to one cell, so one colour's scatters never collide
 // (no atomics, deterministic order).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -962,6 +964,169 @@ __global__ void __launch_bounds__((NPAD / B) * (NPAD / B), NPAD <= 64 ? 8 : (NPA
   }
 }
 
+// The register-tiled elimination of invert_tiles_kernel for patches too large for one CTA's
+// register file (3D k = 2: n_K = 255, padded to NPAD = 256): a cluster of two CTAs per patch,
+// CTA q holding columns [q NPAD/2, (q + 1) NPAD/2) as B x B tiles of a (NPAD/B) x (NPAD/2B)
+// thread grid.  Per step the threads owning column j write it into both CTAs' shared memory
+// (the other CTA's through the cluster's distributed shared memory), the threads of row block
+// j / B publish their half of row j locally, and one cluster barrier separates publication from
+// use (double-buffered, as in the one-CTA kernel).  The pivot is read from the column.  Row
+// scales need both halves: each CTA sends its row maxima to the other before the scales are
+// formed, so both CTAs scale identically.  Same method and flagging as invert_tiles_kernel.
+template <int NPAD, int B, typename MT, typename FT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((NPAD / B) * (NPAD / B / 2), 1)
+    invert_tiles2_kernel(Geom g, const int* __restrict__ rowptr, const MT* __restrict__ vv,
+                         const MT* __restrict__ vp, const MT* __restrict__ pv, FT* __restrict__ jinv,
+                         long long stride, int* __restrict__ flags) {
+  namespace cg = cooperative_groups;
+  constexpr int TR = NPAD / B, TC = NPAD / B / 2, HALF = NPAD / 2;
+  static_assert(NPAD % (2 * B) == 0 && B % 4 == 0, "tile layout");
+  __shared__ __align__(16) float s_col[2][NPAD];
+  __shared__ __align__(16) float s_row[2][HALF];
+  __shared__ float s_red[NPAD][TR + 1];
+  __shared__ float s_rmax[2][NPAD];  // row maxima of each CTA's half
+  __shared__ float s_rs[NPAD], s_cs[NPAD];
+  __shared__ int s_bad;
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank(), other = q ^ 1;
+  const int n = g.npatch;
+  const int tid = threadIdx.x, rg = tid % TR, cgl = tid / TR, cgg = q * TC + cgl;
+  const long long p = blockIdx.x / 2;
+  int cx, cy, cz;
+  patch_cell(g, p, cx, cy, cz);
+  const long long cell = cell_id(g, cx, cy, cz);
+  float a[B][B];
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int c = 0; c < B; ++c) a[r][c] = patch_entry<MT>(g, rowptr, vv, vp, pv, cx, cy, cz, cell, rg * B + r, cgg * B + c);
+  if (tid == 0) s_bad = 0;
+  // row scales: this half's maxima, exchanged with the other CTA
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < B; ++c) mx = fmaxf(mx, fabsf(a[r][c]));
+    s_red[rg * B + r][cgl] = mx;
+  }
+  __syncthreads();
+  float* rmax_other = cl.map_shared_rank(&s_rmax[q][0], other);
+  for (int i = tid; i < NPAD; i += TR * TC) {
+    float mx = 0.f;
+    for (int t = 0; t < TC; ++t) mx = fmaxf(mx, s_red[i][t]);
+    s_rmax[q][i] = mx;
+    rmax_other[i] = mx;
+  }
+  cl.sync();
+  for (int i = tid; i < NPAD; i += TR * TC) {
+    const float mx = fmaxf(s_rmax[0][i], s_rmax[1][i]);
+    s_rs[i] = mx > 0.f ? 1.f / mx : 1.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const float rs = s_rs[rg * B + r];
+#pragma unroll
+    for (int c = 0; c < B; ++c) a[r][c] *= rs;
+  }
+  // column scales: whole columns are local; both CTAs need all of them for the output
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    float mx = 0.f;
+#pragma unroll
+    for (int r = 0; r < B; ++r) mx = fmaxf(mx, fabsf(a[r][c]));
+    s_red[cgl * B + c][rg] = mx;
+  }
+  __syncthreads();
+  float* cs_other = cl.map_shared_rank(&s_cs[0], other);
+  for (int i = tid; i < HALF; i += TR * TC) {
+    float mx = 0.f;
+    for (int t = 0; t < TR; ++t) mx = fmaxf(mx, s_red[i][t]);
+    const float cs = mx > 0.f ? 1.f / mx : 1.f;
+    s_cs[q * HALF + i] = cs;
+    cs_other[q * HALF + i] = cs;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const float cs = s_cs[q * HALF + cgl * B + c];
+#pragma unroll
+    for (int r = 0; r < B; ++r) a[r][c] *= cs;
+  }
+  float* col_other[2] = {cl.map_shared_rank(&s_col[0][0], other), cl.map_shared_rank(&s_col[1][0], other)};
+  for (int cb = 0; cb < TR; ++cb) {
+    const bool colown = cgg == cb, rowown = rg == cb;
+#pragma unroll
+    for (int jj = 0; jj < B; ++jj) {
+      const int j = cb * B + jj;
+      float* col = s_col[jj & 1];
+      float* row = s_row[jj & 1];
+      if (colown)
+#pragma unroll
+        for (int r4 = 0; r4 < B / 4; ++r4) {
+          const float4 v = make_float4(a[4 * r4][jj], a[4 * r4 + 1][jj], a[4 * r4 + 2][jj], a[4 * r4 + 3][jj]);
+          reinterpret_cast<float4*>(col + rg * B)[r4] = v;
+          reinterpret_cast<float4*>(col_other[jj & 1] + rg * B)[r4] = v;
+        }
+      if (rowown)
+#pragma unroll
+        for (int c4 = 0; c4 < B / 4; ++c4)
+          reinterpret_cast<float4*>(row + cgl * B)[c4] =
+              make_float4(a[jj][4 * c4], a[jj][4 * c4 + 1], a[jj][4 * c4 + 2], a[jj][4 * c4 + 3]);
+      cl.sync();
+      const float piv = col[j];
+      if (tid == 0 && (!(fabsf(piv) > 1e-3f) || isinf(piv))) s_bad = 1;
+      const float inv = 1.f / piv;
+      float f[B], qv[B];
+#pragma unroll
+      for (int r4 = 0; r4 < B / 4; ++r4) {
+        const float4 v = reinterpret_cast<const float4*>(col + rg * B)[r4];
+        f[4 * r4] = v.x;
+        f[4 * r4 + 1] = v.y;
+        f[4 * r4 + 2] = v.z;
+        f[4 * r4 + 3] = v.w;
+        const float4 w = reinterpret_cast<const float4*>(row + cgl * B)[r4];
+        qv[4 * r4] = w.x;
+        qv[4 * r4 + 1] = w.y;
+        qv[4 * r4 + 2] = w.z;
+        qv[4 * r4 + 3] = w.w;
+      }
+#pragma unroll
+      for (int r = 0; r < B; ++r) {
+        const float gr = ((rowown && r == jj) ? f[r] - 1.f : f[r]) * inv;
+#pragma unroll
+        for (int c = 0; c < B; ++c) a[r][c] = fmaf(-gr, qv[c], a[r][c]);
+      }
+      if (colown)
+#pragma unroll
+        for (int r = 0; r < B; ++r) a[r][jj] = (rowown && r == jj) ? inv : -f[r] * inv;
+    }
+  }
+  __syncthreads();
+  const bool bad = s_bad != 0;
+  // neither CTA may leave while the other can still address its shared memory
+  cl.sync();
+  if (bad) {
+    if (tid == 0 && q == 0) flags[p] = 1;
+    return;
+  }
+  // J_K^{-1} = Dc A'^{-1} Dr, column-major: element (row, col) at col * n + row
+  FT* out = jinv + p * stride;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const int colx = cgg * B + c;
+    if (colx >= n) continue;
+    const float rc = s_rs[colx];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      const int rowx = rg * B + r;
+      if (rowx < n) {
+        out[(long long)colx * n + rowx] = cvt<FT>(a[r][c] * s_cs[rowx] * rc);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ smoother
 template <typename VT, typename FT, int RPL, int CB>
 __global__ void __launch_bounds__(512) vanka_colour_kernel(Geom g, int colour, const FT* __restrict__ jinv,
@@ -1302,7 +1467,8 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     }
     only = flags;
   } else if (compute_f32 && flags &&
-             (n == 63 || n == 84 || n == 105 || n == 85 || n == 170 || n == 60 || n == 120 || n == 180)) {
+             (n == 63 || n == 84 || n == 105 || n == 85 || n == 170 || n == 60 || n == 120 || n == 180 ||
+              n == 255)) {
     // larger patches: register tiles, pivot-free, then the pivoting kernel for flagged patches
     STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
     auto tiles = [&](auto kern, int threads_t, auto* V, auto* VP, auto* PV) {
@@ -1319,6 +1485,13 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     } else if (n == 180) {  // order 4, k = 2: 12 x 12 tiles keep the 256 threads within the register file
       if (f32src) tiles(invert_tiles_kernel<192, 12, float, FT>, 256, vv32, vp32, pv32);
       else tiles(invert_tiles_kernel<192, 12, double, FT>, 256, vv, vp, pv);
+    } else if (n == 255) {  // 3D k = 2: a cluster of two CTAs per patch
+      const unsigned grid2 = (unsigned)(2 * g.n_cells);
+      if (f32src)
+        invert_tiles2_kernel<256, 8, float, FT><<<grid2, 512, 0, st>>>(g, rowptr, vv32, vp32, pv32, jinv, stride, flags);
+      else
+        invert_tiles2_kernel<256, 8, double, FT><<<grid2, 512, 0, st>>>(g, rowptr, vv, vp, pv, jinv, stride, flags);
+      STG_LAUNCH_OK();
     } else if (n == 84 || n == 85) {
       if (f32src) tiles(invert_tiles_kernel<88, 8, float, FT>, 121, vv32, vp32, pv32);
       else tiles(invert_tiles_kernel<88, 8, double, FT>, 121, vv, vp, pv);

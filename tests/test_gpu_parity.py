@@ -143,6 +143,26 @@ def refined_inverse(A, X):
     return Xl.astype(float)
 
 
+@pytest.mark.parametrize("name", ["channel_k1_newton", "square_k0_dirichlet", "square_k2_dirichlet", "square_k3",
+                                  "channel_k4", "cube_k0", "cube_k1_outflow", "cube_k2"])
+def test_f32_local_inverses(name):
+    """FP32 J_K^{-1} (the register kernels: three rows per lane for n_K = 21, 42; register tiles for
+    63 .. 170; the two-CTA cluster for the 255 unknowns of 3D k = 2; the pivoting kernel for flagged
+    patches) against LAPACK's inverse of the oracle's J_K, every cell of every level: within
+    50 cond(J_K) eps_32 normwise, the forward-error bound of an FP32 elimination with a margin."""
+    from oracle import vanka as ov
+    gpu, ref = pair(name, vcycle_prec="f32", factor_prec="f32")
+    for lvl in range(1, len(ref.levels)):
+        lev = ref.levels[lvl]
+        local = ov.local_matrices(ref.J[lvl], lev)
+        for cell in range(lev.n_cells):
+            inv = ref.jinv[lvl][cell]
+            cond = np.linalg.cond(local[cell])
+            g = gpu.local_inverse(lvl, cell)
+            err = np.linalg.norm(g - inv) / np.linalg.norm(inv)
+            assert err < 50 * cond * 6e-8, (lvl, cell, err, cond)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_local_inverses(name):
     """J_K^{-1} against the oracle's J_K: LAPACK's inverse refined in extended precision is the
