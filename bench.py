@@ -280,6 +280,9 @@ def time_ms(torch, stream, fn, reps: int = 1) -> float:
     return e0.elapsed_time(e1)
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
+
+
 def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, peak: float) -> dict:
     """HBM fraction of the finest level's colour kernels (2D): algorithmic bytes (every J_K^{-1}
     in the form's factor precision, r gathered, z read and written) over their CUDA-event time."""
@@ -289,8 +292,16 @@ def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, p
     per_launch = n * (n * fs + 3 * vs) * patches / max(launches, 1)
     avg = ms / max(launches, 1)
     gbs = per_launch / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
-    return {"bytes_per_launch": per_launch, "avg_launch_ms": avg, "gbs": gbs, "frac": gbs / peak,
-            "launches": launches}
+    out = {"bytes_per_launch": per_launch, "avg_launch_ms": avg, "gbs": gbs, "frac": gbs / peak,
+           "launches": launches}
+    if form == "f64":
+        # the FP64 form's product J_K^{-1} r runs in FP64 FMAs: 2 n_K^2 flops per patch against the
+        # GB300's nominal FP64 rate (no measured FP64 peak is recorded)
+        flops = 2.0 * n * n * patches / max(launches, 1)
+        tflops = flops / (avg * 1e-3) / 1e12 if avg > 0 else 0.0
+        out["fp64"] = {"tflops": tflops, "peak_nominal_tflops": FP64_NOMINAL_TFLOPS,
+                       "frac": tflops / FP64_NOMINAL_TFLOPS}
+    return out
 
 
 def smoother_report(solver, spec, k, cfg, form: str, peak: float, torch, sweeps: int = 20) -> dict:

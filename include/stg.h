@@ -288,7 +288,7 @@ stg_status stg_autotune(stg_ctx* ctx, int* variant, double* sweep_ms);
  * negative limit. */
 stg_status stg_set_wait_limit(long long spins);
 
-/* Colour-kernel variant of level `level` >= 1 (0..12, as timed by stg_autotune):
+/* Colour-kernel variant of level `level` >= 1 (0..16, as timed by stg_autotune):
  * read it, or set it (the V-cycle graph is recaptured), e.g. to replay a choice
  * made in another run.  STG_EINVAL for a level or variant out of range. */
 stg_status stg_get_colour_variant(const stg_ctx* ctx, int level, int* variant);

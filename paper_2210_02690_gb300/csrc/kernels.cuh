@@ -63,9 +63,11 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
 // `colour`; accumulate (averaged mode: z += y) or apply (coloured mode: z += omega y).
 // variant = 3 * column-batch index (4, 8, 16 columns in flight) + CTA-size index (128, 256, 512)
 // Variants 0..8: one warp per patch, loads straight from global memory (3 column-batch depths x
-// 3 CTA sizes); 9..12: factors staged in shared memory by bulk copies (stages x CTAs per SM).
+// 3 CTA sizes); 9..12: factors staged in shared memory by bulk copies (4 pipeline shapes), one
+// row per thread; 13..16: the same shapes with two adjacent rows per thread (one vector load per
+// column and row pair; even patch sizes, else they run as 9..12).
 constexpr int kColourWarpVariants = 9;
-constexpr int kColourVariants = 13;
+constexpr int kColourVariants = 17;
 constexpr int kColourWarpDefault = 4;  // 8 columns, 256 threads
 constexpr int kColourDefault = 9;      // 4 stages, 8 CTAs per SM (falls back to the warp form)
 template <typename VT, typename FT>

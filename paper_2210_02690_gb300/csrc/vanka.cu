@@ -1272,7 +1272,28 @@ __host__ __device__ __forceinline__ unsigned bulk_rl_bytes(int n) {
   return (unsigned)((n * sizeof(VT) + 127) / 128 * 128);
 }
 
-template <typename VT, typename FT, int S>
+// RPT adjacent rows of a column-major factor column as accumulator values (one vector load for
+// RPT = 2: rows 2t, 2t + 1 are adjacent, and the address is aligned for even n).
+template <typename AT, typename FT, int RPT>
+__device__ __forceinline__ void load_rows(const FT* p, AT (&a)[RPT]) {
+  if constexpr (RPT == 1) {
+    a[0] = cvt<AT>(p[0]);
+  } else if constexpr (std::is_same<FT, float>::value) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a[0] = v.x;
+    a[1] = v.y;
+  } else if constexpr (std::is_same<FT, double>::value) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a[0] = v.x;
+    a[1] = v.y;
+  } else {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    a[0] = v.x;
+    a[1] = v.y;
+  }
+}
+
+template <typename VT, typename FT, int S, int RPT>
 __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int colour, const FT* __restrict__ jinv,
                                                                  long long stride, const VT* __restrict__ r,
                                                                  VT* __restrict__ z, VT scale, unsigned bytes,
@@ -1290,13 +1311,16 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
   const FT* base = jinv + g.coff[colour] * stride;
   const int* cc = g.ccount[colour];
   const long long spins = g_colour_wait_spins;
-  auto dof = [&](long long li) {
+  // thread tid owns rows row0 .. row0 + RPT - 1 of every patch (RPT = 2 only for even n)
+  const int row0 = tid * RPT;
+  const bool act = row0 < n;
+  auto dof = [&](long long li, int row) {
     long long rem = li;
     const int jx = (int)(rem % cc[0]);
     rem /= cc[0];
     const int jy = (int)(rem % cc[1]);
     const int jz = (int)(rem / cc[1]);
-    return patch_dof(g, 2 * jx + (colour & 1), 2 * jy + ((colour >> 1) & 1), 2 * jz + ((colour >> 2) & 1), tid);
+    return patch_dof(g, 2 * jx + (colour & 1), 2 * jy + ((colour >> 1) & 1), 2 * jz + ((colour >> 2) & 1), row);
   };
   if (tid == 0) {
     for (int s = 0; s < S; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + s)));
@@ -1308,12 +1332,20 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
     }
   }
   __syncthreads();  // no thread may poll a barrier before thread 0 has initialised it
-  long long gi = 0;
-  VT zold = 0;
-  if (tid < n && first < cnt) {
-    gi = dof(first);
-    rl[tid] = r[gi];
-    zold = z[gi];  // no other patch of this colour touches these entries
+  long long gi[RPT];
+  VT zold[RPT];
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    gi[u] = 0;
+    zold[u] = 0;
+  }
+  if (act && first < cnt) {
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      gi[u] = dof(first, row0 + u);
+      rl[row0 + u] = r[gi[u]];
+      zold[u] = z[gi[u]];  // no other patch of this colour touches these entries
+    }
   }
   int it = 0;
   for (long long li = first; li < cnt; li += step, ++it) {
@@ -1339,24 +1371,47 @@ __global__ void __launch_bounds__(1024) vanka_colour_bulk_kernel(Geom g, int col
     }
     // gather of the next patch, in flight while this one is computed
     const long long ln = li + step;
-    long long gn = 0;
-    VT rn = 0, zn = 0;
-    if (tid < n && ln < cnt) {
-      gn = dof(ln);
-      rn = r[gn];
-      zn = z[gn];
+    long long gn[RPT];
+    VT rn[RPT], zn[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      gn[u] = 0;
+      rn[u] = 0;
+      zn[u] = 0;
     }
-    if (tid < n) {
+    if (act && ln < cnt) {
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        gn[u] = dof(ln, row0 + u);
+        rn[u] = r[gn[u]];
+        zn[u] = z[gn[u]];
+      }
+    }
+    if (act) {
       const FT* A = reinterpret_cast<const FT*>(stages + s * stage_bytes);
       const VT* rc = rl + (it & 1) * n;
-      AT acc = 0;
+      AT acc[RPT];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) acc[u] = 0;
 #pragma unroll 6
-      for (int col = 0; col < n; ++col) acc += cvt<AT>(A[col * n + tid]) * (AT)rc[col];
-      z[gi] = zold + scale * (VT)acc;
-      rl[((it + 1) & 1) * n + tid] = rn;
+      for (int col = 0; col < n; ++col) {
+        AT av[RPT];
+        load_rows<AT, FT, RPT>(A + col * n + row0, av);
+        const AT rv = (AT)rc[col];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) acc[u] += av[u] * rv;
+      }
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        z[gi[u]] = zold[u] + scale * (VT)acc[u];
+        rl[((it + 1) & 1) * n + row0 + u] = rn[u];
+      }
     }
-    gi = gn;
-    zold = zn;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      gi[u] = gn[u];
+      zold[u] = zn[u];
+    }
   }
 }
 
@@ -1553,20 +1608,22 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
 namespace {
 
 struct BulkShape {
-  int stages, ctas_per_sm;
+  int stages, ctas_per_sm, rows_per_thread;
 };
-constexpr BulkShape kBulkShapes[kColourVariants - kColourWarpVariants] = {{4, 32}, {3, 32}, {2, 32}, {6, 32}};
+constexpr BulkShape kBulkShapes[kColourVariants - kColourWarpVariants] = {
+    {4, 32, 1}, {3, 32, 1}, {2, 32, 1}, {6, 32, 1}, {4, 32, 2}, {3, 32, 2}, {2, 32, 2}, {6, 32, 2}};
 
-template <typename VT, typename FT, int S>
+template <typename VT, typename FT, int S, int RPT>
 bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, VT scale, cudaStream_t st,
                  int ctas_per_sm) {
   const int n = g.npatch;
+  if (RPT == 2 && (n & 1)) return false;  // two rows per thread need an even patch size
   const long long cnt = g.coff[colour + 1] - g.coff[colour];
   const long long stride = patch_stride(n);
   const unsigned bytes = (unsigned)((n * n * sizeof(FT) + 15) / 16 * 16);  // <= stride * sizeof(FT)
   const unsigned stage_bytes = (bytes + 127) / 128 * 128;
   const size_t smem = 128 + bulk_rl_bytes<VT>(2 * n) + (size_t)S * stage_bytes;
-  const int threads = (n + 31) / 32 * 32;
+  const int threads = ((n + RPT - 1) / RPT + 31) / 32 * 32;
   if (smem > 200 * 1024 || threads > 1024) return false;
   // queried per launch (a host-side attribute read): contexts on different devices may share
   // this process
@@ -1574,11 +1631,11 @@ bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, 
   STG_CUDA_OK(cudaGetDevice(&dev));
   STG_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (smem > 48 * 1024)
-    STG_CUDA_OK(cudaFuncSetAttribute(vanka_colour_bulk_kernel<VT, FT, S>,
+    STG_CUDA_OK(cudaFuncSetAttribute(vanka_colour_bulk_kernel<VT, FT, S, RPT>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   // every CTA resident at once: the grid is capped by the occupancy the launch can reach
   int resident = 0;
-  STG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, vanka_colour_bulk_kernel<VT, FT, S>,
+  STG_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, vanka_colour_bulk_kernel<VT, FT, S, RPT>,
                                                             threads, smem));
   if (resident < 1) return false;
   const long long want = (long long)sms * std::min(ctas_per_sm, resident);
@@ -1587,7 +1644,7 @@ bool launch_bulk(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z, 
   // CTAs spread evenly over idle SMs; scheduled early into the SMs that the previous kernel frees
   // first, some SMs would take two CTAs and the launch would wait for them
   const OverlapScope serial(false);
-  launch_k(vanka_colour_bulk_kernel<VT, FT, S>, grid, threads, smem, st, g, colour, jinv, stride, r, z, scale, bytes,
+  launch_k(vanka_colour_bulk_kernel<VT, FT, S, RPT>, grid, threads, smem, st, g, colour, jinv, stride, r, z, scale, bytes,
            stage_bytes);
   return true;
 }
@@ -1618,12 +1675,22 @@ void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z,
   if (variant >= kColourWarpVariants) {
     const BulkShape b = kBulkShapes[(variant - kColourWarpVariants) % (kColourVariants - kColourWarpVariants)];
     bool done = false;
-    if (b.stages == 2)
-      done = launch_bulk<VT, FT, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
-    else if (b.stages == 4)
-      done = launch_bulk<VT, FT, 4>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
-    else
-      done = launch_bulk<VT, FT, 6>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+    if (b.rows_per_thread == 2) {
+      if (b.stages == 2)
+        done = launch_bulk<VT, FT, 2, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+      else if (b.stages == 4)
+        done = launch_bulk<VT, FT, 4, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+      else
+        done = launch_bulk<VT, FT, 6, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+    }
+    if (!done) {  // one row per thread (also for an odd patch size)
+      if (b.stages == 2)
+        done = launch_bulk<VT, FT, 2, 1>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+      else if (b.stages == 4)
+        done = launch_bulk<VT, FT, 4, 1>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+      else
+        done = launch_bulk<VT, FT, 6, 1>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+    }
     if (done) return;
     variant = kColourWarpDefault;  // patch too large for the staged form
   }

@@ -268,14 +268,14 @@ def test_vcycle_coloured_smoother():
     assert err < FP64_BAR, err
 
 
-N_VARIANTS = 13
+N_VARIANTS = 17
 
 
 @pytest.mark.parametrize("variant", range(N_VARIANTS))
 def test_every_colour_variant_matches_oracle(variant):
     """Every colour-kernel variant the autotuner can pick (one warp per patch: 9 shapes; factors
-    staged by bulk copies: 4 pipeline shapes), set on all levels: FP64 sweeps and V-cycles at the
-    FP64 bar, the FP32 form's V-cycle at the FP32 bar."""
+    staged by bulk copies: 4 pipeline shapes with one or two rows per thread), set on all levels:
+    FP64 sweeps and V-cycles at the FP64 bar, the FP32 form's V-cycle at the FP32 bar."""
     gpu, ref = pair("channel_k1_newton")
     saved = gpu.colour_variants()
     gpu.set_colour_variants([variant] * len(saved))
@@ -299,6 +299,26 @@ def test_every_colour_variant_matches_oracle(variant):
         assert rel(cpu(g32.vcycle(torch.from_numpy(bc).cuda())), ref.vcycle(bc)) < 1e-4
     finally:
         g32.set_colour_variants(saved)
+
+
+@pytest.mark.parametrize("form", [dict(), dict(vcycle_prec="f32", factor_prec="f32"),
+                                  dict(vcycle_prec="f32", factor_prec="bf16")])
+def test_two_rows_per_thread_variants_are_bit_identical(form):
+    """The staged colour kernel with two rows per thread (variants 13..16) sums every row over the
+    columns in the same order as with one row per thread (9..12): V-cycles are bit-identical in
+    every precision form (n_K = 42; sizes there are even)."""
+    gpu, ref = pair("channel_k1_newton", **form)
+    saved = gpu.colour_variants()
+    bc = torch.from_numpy(consistent_rhs(ref)).cuda()
+    try:
+        for v in range(9, 13):
+            gpu.set_colour_variants([v] * len(saved))
+            one = gpu.vcycle(bc)
+            gpu.set_colour_variants([v + 4] * len(saved))
+            two = gpu.vcycle(bc)
+            assert torch.equal(one, two), v
+    finally:
+        gpu.set_colour_variants(saved)
 
 
 @pytest.mark.parametrize("name", ["channel_k1_newton", "square_k0_dirichlet", "cube_k1_outflow"])
