@@ -774,6 +774,43 @@ def setup_profile(args) -> None:
     s.close()
 
 
+def vcycle_profile(args) -> None:
+    """One V-cycle of the headline channel (with --scale/--levels) in one precision form inside the
+    profiler range (`ncu --profile-from-start off`), after three untimed ones; the colour-kernel
+    variants of --colour-variants (that form's entry) replace the autotuner's choice."""
+    import torch
+
+    from paper_2210_02690_gb300 import Solver
+
+    form = args.vcycle_profile
+    cfg = si.WORKLOADS[WORKLOAD]
+    spec = cfg["spec"]
+    if args.scale > 1 or args.levels:
+        spec = si.scaled(spec, args.scale, args.levels or None)
+    k = cfg["k"]
+    w = torch.from_numpy(si.channel_w(spec, k).ravel()).cuda()
+    s = Solver(spec, k, cfg["nu"], cfg["tau"], w, nu1=cfg["nu1"], nu2=cfg["nu2"], linearisation="newton",
+               **FORMS[form])
+    if args.colour_variants:
+        s.set_colour_variants([int(v) for v in args.colour_variants[form].split(",")])
+    else:
+        s.autotune()
+    b = s.apply_jacobian(torch.from_numpy(si.reference_solution(spec, k)).cuda())
+    for _ in range(3):
+        s.vcycle(b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record(s.stream)
+    s.vcycle(b)
+    e1.record(s.stream)
+    torch.cuda.profiler.stop()
+    torch.cuda.synchronize()
+    print(json.dumps({"form": form, "cells": list(spec.n), "levels": spec.n_levels,
+                      "variants": s.colour_variants(), "vcycle_ms": e0.elapsed_time(e1)}), flush=True)
+    s.close()
+
+
 # ----------------------------------------------------------------------------- reference arm
 def reference_arm(args) -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -815,6 +852,9 @@ def main():
     ap.add_argument("--setup-profile", default=None, metavar="WORKLOAD",
                     help="profiler case: one untimed and one profiled re-linearisation (FP32 form) of a "
                          "workload of stg_inputs.WORKLOADS (with --scale/--levels), then exit")
+    ap.add_argument("--vcycle-profile", default=None, choices=["f32", "f64", "bf16"],
+                    help="profiler case: one V-cycle of the headline channel (with --scale/--levels) in "
+                         "this form inside the profiler range, after three untimed ones, then exit")
     ap.add_argument("--colour-variants", default=None, metavar="F32;F64;BF16",
                     help="skip the autotuner and set the colour-kernel variants of levels 1.. per form, "
                          "e.g. '11,11,11;4,4,4;11,11,11' (the 'variants' a plain run reports), for "
@@ -841,6 +881,8 @@ def main():
         reference_arm(args)
     elif args.setup_profile:
         setup_profile(args)
+    elif args.vcycle_profile:
+        vcycle_profile(args)
     else:
         gpu_arm(args)
 
