@@ -223,13 +223,16 @@ def aggregate_rate(units_per_rank_step: float, steps: int, world: int, ms_max: f
 # DRAM bytes per patch (dram__bytes_read.sum + dram__bytes_write.sum, ncu) of the colour-kernel
 # variants captured on the 352x64 copy of the workload (5632 patches per launch, factors larger
 # than L2); the traffic of a full-size launch scales with its patch count.
-MEASURED_TRAFFIC_PER_PATCH = {11: 43.10e6 / 5632}
+# Keyed by (form, variant).
+MEASURED_TRAFFIC_PER_PATCH = {("f32", 11): 43.10e6 / 5632, ("bf16", 15): 22.93e6 / 5632, ("f64", 11): 85.46e6 / 5632}
 
 
 def colour_kernel_name(variant: int) -> str:
-    """Kernel behind a colour-kernel variant number of the library's autotuner (2D, k = 1)."""
+    """Kernel behind a colour-kernel variant number of the library's autotuner (2D, k = 1, FP32)."""
     if variant >= 9:
-        return f"vanka_colour_bulk_kernel<float,float,{(4, 3, 2, 6)[variant - 9]}> (finest level, bulk-copy staged)"
+        stages, rows = ((4, 1), (3, 1), (2, 1), (6, 1), (4, 2), (3, 2), (2, 2), (6, 2))[variant - 9]
+        return (f"vanka_colour_bulk_kernel<float,float,{stages},{rows}> (finest level, bulk-copy staged, "
+                f"{rows} row(s) per thread)")
     return (f"vanka_colour_kernel<float,float,2,{(4, 8, 16)[(variant // 3) % 3]}> "
             f"({128 << (variant % 3)} threads, finest level)")
 
@@ -283,7 +286,8 @@ def time_ms(torch, stream, fn, reps: int = 1) -> float:
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
 
 
-def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, peak: float) -> dict:
+def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, peak: float,
+                    variant: int | None = None) -> dict:
     """HBM fraction of the finest level's colour kernels (2D): algorithmic bytes (every J_K^{-1}
     in the form's factor precision, r gathered, z read and written) over their CUDA-event time."""
     n = 21 * (k + 1)
@@ -294,6 +298,10 @@ def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, p
     gbs = per_launch / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
     out = {"bytes_per_launch": per_launch, "avg_launch_ms": avg, "gbs": gbs, "frac": gbs / peak,
            "launches": launches}
+    per_patch = MEASURED_TRAFFIC_PER_PATCH.get((form, variant))
+    if per_patch and k == 1:
+        out["traffic"] = per_patch * patches / max(launches, 1)
+        out["traffic_source"] = f"ncu dram bytes of variant {variant} on the 352x64 case, scaled by patches"
     if form == "f64":
         # the FP64 form's product J_K^{-1} r runs in FP64 FMAs: 2 n_K^2 flops per patch against the
         # GB300's nominal FP64 rate (no measured FP64 peak is recorded)
@@ -416,7 +424,7 @@ def gpu_arm(args) -> None:
         pms, plaunch, ppatch = solver.profile_read()
         res["colour_kernel"] = (pms, plaunch, ppatch)
         solver.profile(False)
-        res["colour_kernel_frac"] = colour_fraction(k, name, pms, plaunch, ppatch, peak)
+        res["colour_kernel_frac"] = colour_fraction(k, name, pms, plaunch, ppatch, peak, tuned[0])
         if world == 1:
             res["smoother"] = smoother_report(solver, spec, k, cfg, name, peak, torch)
         if name == "f32":
@@ -460,7 +468,7 @@ def gpu_arm(args) -> None:
     per_launch_bytes = bytes_per_patch * ppatch / max(plaunch, 1)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     variant = r32["autotune"]["finest_variant"]
-    per_patch = MEASURED_TRAFFIC_PER_PATCH.get(variant)
+    per_patch = MEASURED_TRAFFIC_PER_PATCH.get(("f32", variant))
     traffic = per_patch * ppatch / max(plaunch, 1) if per_patch else None
     roofline = {"bound": "hbm", "kernel": colour_kernel_name(variant),
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -1678,6 +1678,8 @@ void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z,
     if (b.rows_per_thread == 2) {
       if (b.stages == 2)
         done = launch_bulk<VT, FT, 2, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+      else if (b.stages == 3)
+        done = launch_bulk<VT, FT, 3, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
       else if (b.stages == 4)
         done = launch_bulk<VT, FT, 4, 2>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
       else
@@ -1686,6 +1688,8 @@ void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z,
     if (!done) {  // one row per thread (also for an odd patch size)
       if (b.stages == 2)
         done = launch_bulk<VT, FT, 2, 1>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
+      else if (b.stages == 3)
+        done = launch_bulk<VT, FT, 3, 1>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
       else if (b.stages == 4)
         done = launch_bulk<VT, FT, 4, 1>(g, colour, jinv, r, z, scale, st, b.ctas_per_sm);
       else
