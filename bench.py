@@ -224,7 +224,8 @@ def aggregate_rate(units_per_rank_step: float, steps: int, world: int, ms_max: f
 # variants captured on the 352x64 copy of the workload (5632 patches per launch, factors larger
 # than L2); the traffic of a full-size launch scales with its patch count.
 # Keyed by (form, variant).
-MEASURED_TRAFFIC_PER_PATCH = {("f32", 11): 43.10e6 / 5632, ("bf16", 15): 22.93e6 / 5632, ("f64", 11): 85.46e6 / 5632}
+MEASURED_TRAFFIC_PER_PATCH = {("f32", 11): 43.10e6 / 5632, ("f32", 15): 43.11e6 / 5632, ("f32", 10): 43.11e6 / 5632,
+                              ("bf16", 15): 22.93e6 / 5632, ("f64", 11): 85.46e6 / 5632}
 
 
 def colour_kernel_name(variant: int) -> str:
