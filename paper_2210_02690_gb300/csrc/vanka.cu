@@ -205,7 +205,12 @@ __global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const 
     tr[bb] = v;
   }
   float acc0 = 0.f, acc1 = 0.f;
-  const int s0 = rowptr[node];
+  // first block slot of the row in closed form (no dependent load of rowptr): with r = 2 a node
+  // couples to w(i) = 5 nodes per direction at interior even indices and to 3 elsewhere, so
+  // the rows before (ix, iy) hold P(iy) S_x + w(iy) P(ix) slots, with the prefix
+  // P(i) = sum_{i' < i} w(i') = 3 i + 2 max(0, (i + 1) / 2 - 1) and S_x = P(nx - 1) + 3
+  auto prefix = [](int i) { return 3 * i + 2 * max(0, (i + 1) / 2 - 1); };
+  const int s0 = prefix(iy) * (prefix(nx - 1) + 3) + (yh - yl + 1) * prefix(ix);
   const float* Mp = Mk + s0;
   const float4* Ap = reinterpret_cast<const float4*>(Ak) + (long long)s0 * NT + a;  // Ahat_a (2 x 2)
   const int wx = xh - xl + 1;
