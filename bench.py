@@ -314,7 +314,7 @@ def colour_fraction(k: int, form: str, ms: float, launches: int, patches: int, p
 
 
 def smoother_report(solver, spec, k, cfg, form: str, peak: float, torch, sweeps: int = 20) -> dict:
-    """Sweep- and cycle-level smoothed DoF/s (SURVEY's metric 1) and the finest sweep's HBM fraction.
+    """Sweep- and cycle-level smoothed DoF/s and the finest sweep's HBM fraction.
     One sweep (residual + colour kernels + update) is timed as the difference of stg_smooth with
     2 + sweeps and 2 sweeps on the finest level (the C-ABI conversions cancel); a V-cycle as the
     mean of `sweeps` stg_vcycle calls."""
