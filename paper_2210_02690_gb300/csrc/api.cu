@@ -395,7 +395,7 @@ void record_event(cudaEvent_t ev, cudaStream_t st) {
 template <typename VT>
 void residual(stg_ctx* c, const LevelBufs& L, const VT* x, const VT* b, VT* r) {
   if (std::is_same<VT, float>::value && L.mk32)
-    apply_operator_kron(L.g, c->td, L.rowptr, L.mk32, L.ak32, L.vp32, L.pv32, (const float*)x, (const float*)b,
+    apply_operator_kron(L.g, c->td, L.mk32, L.ak32, L.vp32, L.pv32, (const float*)x, (const float*)b,
                         (float*)r, c->st);
   else
     apply_operator<VT, VT>(L.g, L.rowptr, L.colidx, Ops<VT>::vv(L), Ops<VT>::vp(L), Ops<VT>::pv(L), x, b, r, c->st);

@@ -79,7 +79,7 @@ void vanka_colour(const Geom& g, int colour, const FT* jinv, const VT* r, VT* z,
 bool kron_supported(const Geom& g);
 void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData& td, float* Mk, float* Ak,
                 cudaStream_t st);
-void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, const float* Mk, const float* Ak,
+void apply_operator_kron(const Geom& g, const TimeData& td, const float* Mk, const float* Ak,
                          const float* vp, const float* pv, const float* x, const float* b, float* out,
                          cudaStream_t st);
 

@@ -180,8 +180,8 @@ __device__ __forceinline__ void kron_stencil_row(const float* __restrict__ xj, c
 
 // One thread per (node, Radau node a): both velocity rows (a, 0), (a, 1).
 template <int NT>
-__global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const int* __restrict__ rowptr,
-                                                        const float* __restrict__ Mk, const float* __restrict__ Ak,
+__global__ void __launch_bounds__(256) op_vel_rows_kron(Geom g, TimeF tf, const float* __restrict__ Mk,
+                                                        const float* __restrict__ Ak,
                                                         const float* __restrict__ vp, const float* __restrict__ x,
                                                         const float* __restrict__ b, float* __restrict__ out) {
   pdl_wait();
@@ -1466,7 +1466,7 @@ void kron_split(const Geom& g, long long nnzb, const double* vv, const TimeData&
   STG_LAUNCH_OK();
 }
 
-void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, const float* Mk, const float* Ak,
+void apply_operator_kron(const Geom& g, const TimeData& td, const float* Mk, const float* Ak,
                          const float* vp, const float* pv, const float* x, const float* b, float* out,
                          cudaStream_t st) {
   if (g.n_nodes * g.nt >= (1LL << 31)) throw Error{STG_EINVAL, "level too large for 32-bit row indices"};
@@ -1475,10 +1475,10 @@ void apply_operator_kron(const Geom& g, const TimeData& td, const int* rowptr, c
     for (int c = 0; c < 5; ++c) tf.T[a][c] = (float)td.T[a][c];
   const unsigned grid = grid_for(g.n_nodes * g.nt, 256);
   switch (g.nt) {
-    case 2: launch_k(op_vel_rows_kron<2>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
-    case 3: launch_k(op_vel_rows_kron<3>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
-    case 4: launch_k(op_vel_rows_kron<4>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
-    default: launch_k(op_vel_rows_kron<5>, grid, 256, 0, st, g, tf, rowptr, Mk, Ak, vp, x, b, out); break;
+    case 2: launch_k(op_vel_rows_kron<2>, grid, 256, 0, st, g, tf, Mk, Ak, vp, x, b, out); break;
+    case 3: launch_k(op_vel_rows_kron<3>, grid, 256, 0, st, g, tf, Mk, Ak, vp, x, b, out); break;
+    case 4: launch_k(op_vel_rows_kron<4>, grid, 256, 0, st, g, tf, Mk, Ak, vp, x, b, out); break;
+    default: launch_k(op_vel_rows_kron<5>, grid, 256, 0, st, g, tf, Mk, Ak, vp, x, b, out); break;
   }
   launch_k(op_pres_rows<2, float, float>, grid_for(g.npres, 256), 256, 0, st, g, pv, x, b, out);
 }
