@@ -765,8 +765,8 @@ def setup_profile(args) -> None:
     spec = cfg["spec"]
     if args.scale > 1 or args.levels:
         spec = si.scaled(spec, args.scale, args.levels or None)
-    k = cfg["k"]
-    w = torch.from_numpy(si.make_w(dict(cfg, spec=spec)).ravel()).cuda()
+    k = cfg["k"] if args.k is None else args.k
+    w = torch.from_numpy(si.make_w(dict(cfg, spec=spec, k=k)).ravel()).cuda()
     s = Solver(spec, k, cfg["nu"], cfg["tau"], w, nu1=cfg["nu1"], nu2=cfg["nu2"],
                linearisation="newton" if cfg["newton"] else "oseen", **FORMS["f32"])
     s.update_linearisation(w)
@@ -778,7 +778,7 @@ def setup_profile(args) -> None:
     e1.record(s.stream)
     torch.cuda.profiler.stop()
     torch.cuda.synchronize()
-    print(json.dumps({"workload": args.setup_profile, "cells": list(spec.n), "levels": spec.n_levels,
+    print(json.dumps({"workload": args.setup_profile, "cells": list(spec.n), "levels": spec.n_levels, "k": k,
                       "setup_ms": e0.elapsed_time(e1)}), flush=True)
     s.close()
 
@@ -861,6 +861,8 @@ def main():
     ap.add_argument("--setup-profile", default=None, metavar="WORKLOAD",
                     help="profiler case: one untimed and one profiled re-linearisation (FP32 form) of a "
                          "workload of stg_inputs.WORKLOADS (with --scale/--levels), then exit")
+    ap.add_argument("--k", type=int, default=None,
+                    help="with --setup-profile: the time degree (default: the workload's)")
     ap.add_argument("--vcycle-profile", default=None, choices=["f32", "f64", "bf16"],
                     help="profiler case: one V-cycle of the headline channel (with --scale/--levels) in "
                          "this form inside the profiler range, after three untimed ones, then exit")
