@@ -33,3 +33,26 @@ def test_sweep_bytes_parts():
     assert b32["total"] == b32["residual"] + b32["colour"] + b32["update"]
     # the FP32 Kronecker operator is smaller than the dense FP64 blocks
     assert b32["residual"] < b64["residual"] / 2
+
+
+def test_every_colour_variant_has_a_kernel_name():
+    """The bench names the kernel behind any of the 17 variants the autotuner may pick (warp form
+    0..8, staged 9..16 with one or two rows per thread); the staged names carry the stage count
+    of the shape table and the rows per thread."""
+    import bench
+    names = [bench.colour_kernel_name(v) for v in range(17)]
+    assert all("vanka_colour" in n for n in names)
+    assert names[11].startswith("vanka_colour_bulk_kernel<float,float,2,1>")
+    assert names[15].startswith("vanka_colour_bulk_kernel<float,float,2,2>")
+    assert names[10].startswith("vanka_colour_bulk_kernel<float,float,3,1>")
+
+
+def test_colour_fraction_reports_the_fp64_pipe_and_measured_traffic():
+    import bench
+    # one full-size FP64 launch: 22 528 patches of 42 in 0.114 ms
+    f = bench.colour_fraction(1, "f64", 0.114, 1, 22528, 6779.4, 11)
+    flops = 2.0 * 42 * 42 * 22528
+    assert abs(f["fp64"]["tflops"] - flops / 0.114e-3 / 1e12) < 1e-9
+    assert f["traffic"] == bench.MEASURED_TRAFFIC_PER_PATCH[("f64", 11)] * 22528
+    g = bench.colour_fraction(1, "bf16", 0.028, 1, 22528, 6779.4, 12)
+    assert "traffic" not in g and "fp64" not in g
