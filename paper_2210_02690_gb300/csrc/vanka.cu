@@ -1528,7 +1528,7 @@ void invert_patches(const Geom& g, const int* rowptr, const double* vv, const do
     only = flags;
   } else if (compute_f32 && flags &&
              (n == 63 || n == 84 || n == 105 || n == 85 || n == 170 || n == 60 || n == 120 || n == 180 ||
-              n == 255)) {
+              (n == 255 && g.dim == 3))) {  // the cluster kernel has no removed-cell path (3D only)
     // larger patches: register tiles, pivot-free, then the pivoting kernel for flagged patches
     STG_CUDA_OK(cudaMemsetAsync(flags, 0, sizeof(int) * g.n_cells, st));
     auto tiles = [&](auto kern, int threads_t, auto* V, auto* VP, auto* PV) {
